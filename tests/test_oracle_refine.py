@@ -1,0 +1,119 @@
+"""Oracle pins for the Hilbert-curve refinement (Sec. "Adaptive refinements"),
+driven by analytic length maps so that only the refinement logic is tested."""
+import numpy as np
+import pytest
+
+
+def circle_map(x):
+    r = np.hypot(x[:, 0] - 0.1, x[:, 1] + 0.05)
+    return np.ones(len(x)), np.where(r < 0.5, 1.0, 0.0)
+
+
+def smooth_map(x):
+    return 2.0 + np.sin(3 * x[:, 0]) * np.cos(2 * x[:, 1]), x[:, 0] ** 2 + x[:, 1]
+
+
+def _coarse_key_range(oracle_mod, ndim, p0, p, extent):
+    R = 1 << (p - p0)
+    keys = []
+    for k in range(extent[2] // R if ndim == 3 else 1):
+        for j in range(extent[1] // R):
+            for i in range(extent[0] // R):
+                c = (i * R + R // 2, j * R + R // 2, k * R + R // 2)[:ndim]
+                keys.append(oracle_mod.hilbert_key(c, ndim, p))
+    return min(keys), max(keys)
+
+
+def test_negative_tau_gives_dense_lattice_2d(oracle_mod):
+    """tau < 0 flags every pair: refinement fills every cell between the first
+    and the last coarse sample along the curve (it only inserts between
+    samples)."""
+    k0, k1 = _coarse_key_range(oracle_mod, 2, 2, 4, (16, 16))
+    for shift in (0, 1):
+        sp = oracle_mod.refine_spec(ndim=2, coarse_order=2, max_order=4, center=(0, 0, 0), u=(2, 0, 0),
+                                    v=(0, 2, 0), tau=-1.0, shift=shift)
+        r = oracle_mod.refine_fn(smooth_map, sp)
+        if shift == 0:
+            assert list(r["key"]) == list(range(k0, k1 + 1))
+        else:  # the shifted pass also reaches cells beyond the ends of the coarse range
+            assert set(range(k0, k1 + 1)) <= set(int(k) for k in r["key"])
+
+
+def test_negative_tau_gives_dense_lattice_3d_clipped(oracle_mod):
+    """A 2:1 box: the order-3 curve is clipped to 8 x 8 x 4 cells."""
+    sp = oracle_mod.refine_spec(ndim=3, coarse_order=1, max_order=3, extent=(8, 8, 4), lo=(-1, -1, 0),
+                                hi=(1, 1, 1), tau=-1.0, shift=0)
+    r = oracle_mod.refine_fn(lambda x: (np.ones(len(x)), x[:, 0] + 2 * x[:, 2]), sp)
+    k0, k1 = _coarse_key_range(oracle_mod, 3, 1, 3, (8, 8, 4))
+    want = sorted(k for k in range(k0, k1 + 1) if oracle_mod.hilbert_coords(k, 3, 3)[2] < 4)
+    assert list(r["key"]) == want
+
+
+def test_large_tau_keeps_coarse_samples_only(oracle_mod):
+    sp = oracle_mod.refine_spec(ndim=2, coarse_order=3, max_order=6, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0),
+                                tau=10.0)
+    r = oracle_mod.refine_fn(smooth_map, sp)
+    cells = [oracle_mod.hilbert_coords(k, 2, 6) for k in r["key"]]
+    assert len(cells) == 64
+    assert all(c[0] % 8 == 4 and c[1] % 8 == 4 for c in cells)  # index R/2 modulo R, R = 8
+    assert r["iters"] == 0
+
+
+def test_step_map_refines_only_along_the_step(oracle_mod):
+    p0, p = 3, 7
+    n = 1 << p
+    sp = oracle_mod.refine_spec(ndim=2, coarse_order=p0, max_order=p, center=(0, 0, 0), u=(2, 0, 0),
+                                v=(0, 2, 0), tau=0.5)
+    r = oracle_mod.refine_fn(circle_map, sp)
+    keys = r["key"].astype(np.int64)
+    assert np.all(np.diff(keys) > 0)  # unique, sorted
+    cells = np.array([oracle_mod.hilbert_coords(k, 2, p) for k in r["key"]])
+    R = 1 << (p - p0)
+    coarse = (cells[:, 0] % R == R // 2) & (cells[:, 1] % R == R // 2)
+    assert coarse.sum() == (n // R) ** 2  # every coarse sample is kept
+    # termination: no pair adjacent along the curve straddles the step with key gap > 1
+    L = r["L"]
+    straddle = np.abs(np.diff(L)) > 0.5
+    assert np.all(np.diff(keys)[straddle] == 1)
+    # every refined sample lies near the step: within sqrt(6 x coarse key gap) cells
+    xy = -1 + (cells + 0.5) * 2.0 / n
+    d = np.abs(np.hypot(xy[:, 0] - 0.1, xy[:, 1] + 0.05) - 0.5) * n / 2
+    assert np.all(d[~coarse] <= np.sqrt(6 * R * R) + 1)
+
+
+def test_shifted_curve_reduces_misses(oracle_mod):
+    """The shifted-curve pass must find substantially more of the step's
+    boundary cells than refinement along one curve (the misses the paper's
+    shift is meant to remove)."""
+    p0, p = 3, 7
+    n = 1 << p
+    cov = {}
+    for shift in (0, 1):
+        sp = oracle_mod.refine_spec(ndim=2, coarse_order=p0, max_order=p, center=(0, 0, 0), u=(2, 0, 0),
+                                    v=(0, 2, 0), tau=0.5, shift=shift)
+        r = oracle_mod.refine_fn(circle_map, sp)
+        S = {oracle_mod.hilbert_coords(k, 2, p) for k in r["key"]}
+        hit = tot = 0
+        for i in range(n):
+            for j in range(n):
+                x, y = -1 + (i + 0.5) * 2 / n, -1 + (j + 0.5) * 2 / n
+                if abs(np.hypot(x - 0.1, y + 0.05) - 0.5) < 1.0 / n:
+                    tot += 1
+                    hit += (i, j) in S
+        cov[shift] = hit / tot
+    assert cov[1] > 3 * cov[0]
+    assert cov[1] > 0.7
+
+
+def test_converter_on_refined_samples_keeps_sampled_values(oracle_mod):
+    p0, p = 2, 5
+    sp = oracle_mod.refine_spec(ndim=2, coarse_order=p0, max_order=p, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0),
+                                tau=0.3)
+    r = oracle_mod.refine_fn(smooth_map, sp)
+    grid = oracle_mod.convert(r["key"], r["q"], 2, p, (32, 32, 0), p, True)
+    for k, q in zip(r["key"], r["q"]):
+        x, y = oracle_mod.hilbert_coords(k, 2, p)
+        assert grid[y, x] == q
+    assert np.all(np.isfinite(grid))
+    lo, hi = r["q"].min(), r["q"].max()
+    assert np.all((grid >= lo * (1 - 1e-12)) & (grid <= hi * (1 + 1e-12)))
