@@ -1,0 +1,360 @@
+"""Benchmark: Q-points/s of a complete refined Q map (the QSL Squasher hot path).
+
+Workload (one step): the potential field of 4 sub-photospheric point charges
+(|q| ~ U(0.5, 1.5), alternating signs, depths ~ U(0.05, 0.2), (x, y) ~
+U[-0.5, 0.5]^2, seed 2) sampled in FP32 on a 256^3 grid over [-1,1]^2 x [0,1];
+field packing, the 1024 x 1024 photospheric (z = 0) coarse Q/FLL map, the
+FLEDGE map of its lengths, FLL-jump refinement along the Hilbert curve (with
+the shifted-curve pass) to 4096 x 4096 effective resolution, FP64 retrace of
+lines with Q > 1e6, and the Hilbert -> rectilinear conversion of Q and FLL to
+4096 x 4096. value = Q-points traced per step (coarse + refined) / step time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica (its own field
+seed); value sums all ranks' Q-points over the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Q-points/s (refined 4096^2-effective Q map, Q rel.err <= 1e-3 vs FP64 oracle)"
+UNIT = "Q-points/s"
+GRID_N = 256
+COARSE = 1024
+P0, P = 10, 12
+TAU = 0.05
+TOL = 1e-7
+FIELD_SEED = 2
+
+# Algorithmic FP32 work of one RK stage evaluation in the tangent tracer
+# (paper mode): trilinear value + gradient of 3 components (99 FLOP), cell
+# location (9), gradient scaling (9), deviation right-hand sides (30), the
+# stage's share of the Cash-Karp combinations, error norm and controller
+# (99); an FMA counts as 2 FLOP.
+FLOP_PER_STAGE = 246.0
+# FP32 peak of the FMA pipe: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=GRID_N)
+    ap.add_argument("--coarse", type=int, default=COARSE)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_field(seed, device, n):
+    import torch
+
+    from paper_1609_00724_gb300 import inputs
+    ch = inputs.random_charges(4, seed)
+    return inputs.charge_field(ch, n, dtype=torch.float32, device=device, slab=64)
+
+
+def opts(qsl):
+    return qsl.qsl_opts_default(tol_abs=TOL, tol_rel=TOL, q_form=qsl.QSL_Q_PERP)
+
+
+def spec(qsl, coarse):
+    p0 = int(np.log2(coarse))
+    return qsl.refine_spec(ndim=2, coarse_order=p0, max_order=p0 + (P - P0), center=(0, 0, 0), u=(2, 0, 0),
+                           v=(0, 2, 0), tau=TAU, shift=1, max_iters=64)
+
+
+def gpu_step(qsl, gf, bufs, coarse, stream_sync=True):
+    """One full step on device-resident inputs. Returns (q_points, stats dict)."""
+    import torch
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
+    o = opts(qsl)
+    sp = spec(qsl, coarse)
+    n, iters, traced, rc = qsl.qsl_refine(F, sp, o, bufs["key"], bufs["q"], bufs["L"], bufs["faces"], bufs["st"],
+                                          0, bufs["qg"], bufs["lg"])
+    # FLEDGE of the converted length map
+    qsl.qsl_fledge(bufs["lg"].view(bufs["eff"], bufs["eff"]), bufs["sg"])
+    if stream_sync:
+        torch.cuda.synchronize()
+    return traced, {"samples": n, "iters": iters, "rc": rc}
+
+
+def alloc(torch, coarse, device):
+    eff = coarse << (P - P0)
+    cap = eff * eff
+    return {"key": torch.empty(cap, dtype=torch.int64, device=device),
+            "q": torch.empty(cap, dtype=torch.float32, device=device),
+            "L": torch.empty(cap, dtype=torch.float32, device=device),
+            "faces": torch.empty(2 * cap, dtype=torch.uint8, device=device),
+            "st": torch.empty(cap, dtype=torch.uint8, device=device),
+            "qg": torch.empty(cap, dtype=torch.float32, device=device),
+            "lg": torch.empty(cap, dtype=torch.float32, device=device),
+            "sg": torch.empty((eff, eff), dtype=torch.float32, device=device), "eff": eff}
+
+
+def oracle_sample_rate(gf_cpu, coarse, budget_s=15.0, seed=99):
+    """The FP64 oracle, as it stands, on a seeded subsample of the coarse map's
+    seeds at the bench tolerance, on all host cores. Returns (Q-points/s,
+    seeds, cores, seconds)."""
+    import oracle
+    from paper_1609_00724_gb300 import inputs
+    g = inputs.to_numpy64(gf_cpu)
+    F = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
+    seeds = oracle.plane_seeds([0, 0, 0], [2, 0, 0], [0, 2, 0], coarse, coarse)
+    cores = os.cpu_count() or 1
+    o = oracle.default_opts(tol_abs=TOL, tol_rel=TOL, nthreads=cores)
+    done, t_used, m = 0, 0.0, 64 * cores
+    rng_seed = seed
+    while t_used < budget_s and done < len(seeds):
+        idx = inputs.subsample(len(seeds), m, rng_seed)
+        t0 = time.perf_counter()
+        oracle.trace_seeds(F, seeds[idx], o)
+        t_used += time.perf_counter() - t0
+        done += len(idx)
+        rng_seed += 1
+        m = min(4 * m, max(64, int(m * budget_s / max(t_used, 1e-3))))
+    return done / t_used, done, cores, t_used
+
+
+def parity_sample(qsl, gf, gf_cpu, coarse, n=200):
+    """Coarse-map Q/FLL of the GPU path at the bench tolerance against the FP64
+    oracle at tol 1e-11 on `n` seeded pixels."""
+    import torch
+
+    import oracle
+    from paper_1609_00724_gb300 import inputs
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
+    N = coarse * coarse
+    q = torch.empty(N, device="cuda")
+    L = torch.empty(N, device="cuda")
+    fc = torch.empty(2 * N, dtype=torch.uint8, device="cuda")
+    qsl.qsl_q_map_2d(F, (0, 0, 0), (2, 0, 0), (0, 2, 0), coarse, coarse, opts(qsl), q=q, length=L, faces=fc)
+    torch.cuda.synchronize()
+    idx = inputs.subsample(N, n, 7)
+    g = inputs.to_numpy64(gf_cpu)
+    Fo = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
+    seeds = oracle.plane_seeds([0, 0, 0], [2, 0, 0], [0, 2, 0], coarse, coarse)[idx]
+    ref = oracle.trace_seeds(Fo, seeds, oracle.default_opts(tol_abs=1e-11, tol_rel=1e-11, nthreads=os.cpu_count()))
+    qg, lg = q.cpu().numpy()[idx], L.cpu().numpy()[idx]
+    fg = fc.cpu().numpy().reshape(-1, 2)[idx]
+    ok = np.isfinite(ref["q_perp"]) & (ref["q_perp"] < 1e6)
+    qe = np.abs(qg[ok] / ref["q_perp"][ok] - 1)
+    le = np.abs(lg / ref["L"] - 1)[ref["L"] > 0]
+    faces_eq = float(np.mean((fg[:, 0] == ref["face_f"]) & (fg[:, 1] == ref["face_b"])))
+    return {"n": int(n), "q_max_rel": float(qe.max()), "q_p99_rel": float(np.quantile(qe, 0.99)),
+            "l_max_rel": float(le.max()), "faces_equal": faces_eq}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle (as it stands) on host cores, one
+    bounded sample of the workload per step."""
+    if rank != 0:
+        return
+    import torch
+
+    import oracle
+    from paper_1609_00724_gb300 import inputs
+    gf = make_field(FIELD_SEED, "cpu", args.grid)
+    g = inputs.to_numpy64(gf)
+    F = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
+    seeds = oracle.plane_seeds([0, 0, 0], [2, 0, 0], [0, 2, 0], args.coarse, args.coarse)
+    cores = os.cpu_count() or 1
+    o = oracle.default_opts(tol_abs=TOL, tol_rel=TOL, nthreads=cores)
+    per_step = 24 * cores
+    for w in range(args.warmup):
+        oracle.trace_seeds(F, seeds[inputs.subsample(len(seeds), per_step, 1000 + w)], o)
+    t = 0.0
+    for s in range(args.steps):
+        idx = inputs.subsample(len(seeds), per_step, 2000 + s)
+        t0 = time.perf_counter()
+        oracle.trace_seeds(F, seeds[idx], o)
+        t += time.perf_counter() - t0
+    value = per_step * args.steps / t
+    sample = "%d seeded coarse-map seeds per step of the 1024^2 z=0 map, tol %g" % (per_step, TOL)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "4-charge potential field 256^3 FP32, 1024^2 z=0 map refined to 4096^2",
+                       "oracle": "FP64 C++ (oracle/qslref.cpp)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    del torch
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1609_00724_gb300 import qsl
+    qsl.lib()
+    field_seed = FIELD_SEED + 1000 * rank
+    gf = make_field(field_seed, dev, args.grid)
+    bufs = alloc(torch, args.coarse, dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        gpu_step(qsl, gf, bufs, args.coarse)
+    # --- timed region: device-resident inputs (the field is 268 MB, larger than L2)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    traced_total = 0
+    kernel_ms = []
+    stage_evals = 0
+    info = {}
+    barrier()
+    with ClockSampler(local) as clk:
+        start.record()
+        for _ in range(args.steps):
+            tr, info = gpu_step(qsl, gf, bufs, args.coarse, stream_sync=False)
+            traced_total += tr
+        end.record()
+        barrier()
+    ms = start.elapsed_time(end)
+    t = torch.tensor([ms], device=dev)
+    n_units = torch.tensor([float(traced_total)], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(n_units, op=torch.distributed.ReduceOp.SUM)
+    ms_max = float(t.item())
+    value = float(n_units.item()) / (ms_max / 1000.0)
+
+    # --- dominant kernel (tracer) timing over one more step: CUDA events recorded
+    # by the library around each tracer launch on the launching stream
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
+    N = args.coarse * args.coarse
+    qm = torch.empty(N, device=dev)
+    Lm = torch.empty(N, device=dev)
+    for _ in range(2):
+        qsl.qsl_q_map_2d(F, (0, 0, 0), (2, 0, 0), (0, 2, 0), args.coarse, args.coarse, opts(qsl), q=qm, length=Lm)
+    st = qsl.qsl_last_stats()
+    kms = st["kernel_ms"]
+    achieved_tflops = st["stage_evals"] * FLOP_PER_STAGE / (kms / 1000.0) / 1e12
+
+    # --- end to end through the C ABI with host buffers (pinned), copies inside
+    eff = args.coarse << (P - P0)
+    host = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in bufs.items() if k != "eff"}
+    hb = [a.cpu().pin_memory() for a in (gf.bx, gf.by, gf.bz)]
+    e2e_t = []
+    for it in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Fh = qsl.qsl_load_field(hb[0].numpy(), hb[1].numpy(), hb[2].numpy(), gf.xc, gf.yc, gf.zc,
+                                qsl.QSL_PAPER_NORMALIZE_FIRST)
+        n_h, _, traced_h, _ = qsl.qsl_refine(Fh, spec(qsl, args.coarse), opts(qsl), host["key"].numpy(),
+                                             host["q"].numpy(), host["L"].numpy(), host["faces"].numpy(),
+                                             host["st"].numpy(), 0, host["qg"].numpy(), host["lg"].numpy())
+        e2e_t.append(time.perf_counter() - t0)
+        del Fh
+    e2e_value = traced_h / min(e2e_t)
+    h2d = sum(a.numel() * a.element_size() for a in hb)
+    d2h = n_h * (8 + 4 + 4 + 2 + 1) + 2 * eff * eff * 4
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "4-charge potential field %d^3 FP32, %d^2 z=0 Q map refined to %d^2 effective"
+                                   % (args.grid, args.coarse, eff),
+                       "tol": TOL, "tau": TAU, "coarse_order": int(np.log2(args.coarse)), "max_order":
+                           int(np.log2(eff)), "interp": "paper (normalise first)", "precision": "FP32 trace, FP64 Q",
+                       "l2": "inputs larger than L2 (268 MB packed field)", "parallelism": "replicas x%d" % world,
+                       "samples_per_step": info.get("samples"), "refine_iters": info.get("iters"),
+                       "q_points_per_step": traced_total // max(args.steps, 1)},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": None,
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "trace_kernel<float,9> (1024^2 coarse map)", "kernel_ms": kms,
+                         "stage_evals": st["stage_evals"], "peak_note": "FP32 FMA pipe at 2.07 GHz (derived)"}}
+    if rank == 0 and not args.no_cpu_baseline:
+        gf_cpu = make_field(field_seed, "cpu", args.grid)
+        rate, nseeds, cores, secs = oracle_sample_rate(gf_cpu, args.coarse)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d seeded seeds of the %d^2 coarse map, tol %g, %.1f s"
+                                          % (nseeds, args.coarse, TOL, secs)}
+        line["parity"] = parity_sample(qsl, gf, gf_cpu, args.coarse)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,252 @@
+/*
+ * qsl.h — C ABI of the GB300 QSL engine: squashing factor Q, field-line length
+ * (FLL) and FLEDGE maps of a gridded 3D magnetic field, after the method of
+ * Tassev & Savcheva, "QSL Squasher: A Fast Quasi-Separatrix Layer Map
+ * Calculator" (arXiv:1609.00724).
+ *
+ * Conventions shared by every call:
+ *  - Return value: QSL_OK (0) or a negative QSL_E* code; qsl_last_error()
+ *    gives a message (thread-local). Problems of single lines are status
+ *    codes in the outputs, not call failures.
+ *  - `mem` says where the caller's array arguments live: QSL_MEM_HOST or
+ *    QSL_MEM_DEVICE (CUDA device memory of the current device). Small
+ *    parameter arrays (axis coordinates, centre/axis vectors, shapes) are
+ *    always host memory.
+ *  - All outputs are caller-owned. Output pointers documented as optional may
+ *    be NULL.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). With device
+ *    memory, calls are asynchronous on that stream; with host memory they
+ *    return after the results are in host memory. qsl_refine synchronises
+ *    the stream once per refinement iteration (it reads a sample count).
+ *  - Library scratch memory comes from the stream-ordered allocator
+ *    (cudaMallocAsync) on `stream`; QSL_ENOMEM when it fails.
+ *  - Every computation runs in this library's CUDA kernels on the current
+ *    device; there is no CPU fallback.
+ */
+#ifndef QSL_H
+#define QSL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------- */
+#define QSL_OK 0
+#define QSL_EINVAL (-1)     /* bad argument (message says which)                   */
+#define QSL_ENOMEM (-2)     /* device or host allocation failed                     */
+#define QSL_ECUDA (-3)      /* a CUDA runtime call or kernel launch failed          */
+#define QSL_ETIMEOUT (-4)   /* the device watchdog (qsl_opts.timeout_s) expired     */
+#define QSL_ENONFINITE (-5) /* non-finite field values were given                   */
+#define QSL_ECAPACITY (-6)  /* qsl_refine: sample capacity exhausted (partial result) */
+
+/* ---- enumerations ----------------------------------------------------------- */
+#define QSL_MEM_HOST 0
+#define QSL_MEM_DEVICE 1
+
+#define QSL_F32 0
+#define QSL_F64 1
+
+/* Interpolation of the field (Sec. "Interpolation schemes" and the footnote of
+ * Sec. "Squashing factor calculation"): the paper normalises the field cubes
+ * first and interpolates the unit vectors (the interpolant is then not unit);
+ * RAW interpolates B and normalises at the point. */
+#define QSL_PAPER_NORMALIZE_FIRST 0
+#define QSL_RAW_B 1
+
+/* Integrators (Sec. "Integration methods"). */
+#define QSL_RKCK54 0 /* adaptive Cash-Karp 5(4), the paper's default          */
+#define QSL_EULER 1  /* fixed-step explicit Euler, step qsl_opts.euler_h cells */
+
+/* Which Q the map calls return (qsl_line records hold all three). */
+#define QSL_Q_PERP 0 /* Eq. finalQ with dx_perp = dx - b (b.dx)                   */
+#define QSL_Q_FOOT 1 /* Eq. finalQ with deviations projected onto the end faces    */
+#define QSL_Q_DET 2  /* Eq. finalQ's bracket over the true Gram determinants (>= 2) */
+
+/* Precision policy. */
+#define QSL_FP32_MIXED 0 /* FP32 tracing, FP64 Q assembly, FP64 retrace above retrace_q */
+#define QSL_FP64 1       /* FP64 tracing and assembly everywhere                        */
+
+/* Per-direction line status (3 bits). */
+#define QSL_LINE_OK 0        /* reached a face of the domain                     */
+#define QSL_LINE_MAXLEN 1    /* stopped at qsl_opts.max_length ("local" Q)         */
+#define QSL_LINE_MAXSTEPS 2  /* qsl_opts.max_steps step attempts used up          */
+#define QSL_LINE_STALL 3     /* step size fell below qsl_opts.h_min               */
+#define QSL_LINE_OUTSIDE 4   /* the seed lies outside the domain                  */
+#define QSL_LINE_NONFINITE 5 /* the state became non-finite                       */
+#define QSL_LINE_NULL 6      /* the interpolated field vanishes at the seed       */
+#define QSL_LINE_TIMEOUT 7   /* the device watchdog stopped the launch            */
+
+/* Map status byte: status_F | status_B << 3 | flags. */
+#define QSL_FLAG_OPEN_SKIPPED 0x40 /* open line with skip_open: Q = NaN           */
+#define QSL_FLAG_RETRACED 0x80     /* Q above retrace_q: traced again in FP64     */
+
+/* Faces: 0..5 = x-, x+, y-, y+, z-, z+ of the domain; QSL_NO_FACE otherwise. */
+#define QSL_NO_FACE 255
+
+/* ---- options ----------------------------------------------------------------- */
+typedef struct qsl_opts {
+  int32_t integrator;  /* QSL_RKCK54 | QSL_EULER                                    */
+  int32_t q_form;      /* QSL_Q_PERP | QSL_Q_FOOT | QSL_Q_DET (map outputs)          */
+  int32_t precision;   /* QSL_FP32_MIXED | QSL_FP64                                  */
+  int32_t skip_open;   /* 1: lines not closed on z- get Q = NaN (Sec. "Squashing factor calculation") */
+  int32_t length_only; /* 1: integrate x only; Q outputs are NaN (FLEDGE fast path)   */
+  int32_t warps_per_block; /* tracer launch shape; 0 = autotuned                        */
+  int32_t blocks_per_sm;   /* tracer launch shape; 0 = autotuned                        */
+  int32_t refill_min;      /* lanes idle before a warp refills from the queue; 0 = auto */
+  double tol_abs, tol_rel; /* step error tolerances (paper: 1e-2)                       */
+  double h_init, h_max, h_min; /* step bounds in units of the smallest grid spacing      */
+  double max_length;       /* per direction, domain units; <= 0: 20 x domain diagonal  */
+  int64_t max_steps;       /* step attempts per direction                               */
+  double euler_h;          /* Euler step in cells (paper: about 1/5)                    */
+  double retrace_q;        /* FP64 retrace threshold for QSL_FP32_MIXED; <= 0: never    */
+  double domain_lo[3], domain_hi[3]; /* tracing box; lo >= hi on any axis: grid extent */
+  double land_tol;         /* face landing tolerance in cells (FP32 stops at its resolution of the step) */
+  double timeout_s;        /* device watchdog per launch; <= 0: none                    */
+} qsl_opts;
+
+/* Fills the defaults: RKCK54, Q_PERP, FP32_MIXED, tol 1e-2/1e-2, h_init 0.1,
+ * h_max 2, h_min 1e-15 cells, max_length 20 x diagonal, max_steps 1e6,
+ * euler_h 0.2, retrace_q 1e6, land_tol 1e-12, no watchdog. */
+void qsl_opts_default(qsl_opts* opts);
+
+/* ---- per-line record (qsl_trace_seeds) --------------------------------------- */
+typedef struct qsl_line {
+  double q_perp;  /* Eq. finalQ                                               */
+  double q_foot;  /* Eq. finalQ with face-projected deviations and |B_n|      */
+  double q_det;   /* bracket of Eq. finalQ / sqrt(det G_F det G_B)            */
+  double b0, bf, bb;       /* |B| at the seed and at the two ends               */
+  double flux_f, flux_b;   /* (B_e/B_0)|a_e x b_e| - 1 at each end               */
+  float length;            /* lambda_F - lambda_B                                */
+  float lam_f, lam_b;      /* lambda_F >= 0, lambda_B <= 0                       */
+  float pad0;
+  float x_f[3], x_b[3];    /* end points                                         */
+  int32_t steps;           /* step attempts, both directions                     */
+  uint8_t face_f, face_b;  /* end faces (QSL_NO_FACE at a cutoff)                */
+  uint8_t status_f, status_b; /* QSL_LINE_* per direction                        */
+} qsl_line; /* 112 bytes */
+
+/* ---- statistics of the last tracing call on this thread ------------------------ */
+typedef struct qsl_stats {
+  int64_t lines;        /* seeds traced (both directions each)                 */
+  int64_t stage_evals;  /* interpolations of B and grad B inside the tracer    */
+  int64_t accepted, rejected, landing; /* step attempts by kind              */
+  int64_t retraced;     /* seeds traced again in FP64                           */
+  double kernel_ms;     /* device time of the tracer launches (CUDA events)     */
+  int32_t warps_per_block, blocks_per_sm, refill_min, pad;
+} qsl_stats;
+
+/* Synchronises the stream of the last tracing call on this thread and copies
+ * its counters. */
+int qsl_last_stats(qsl_stats* out);
+
+/* ---- field ------------------------------------------------------------------- */
+typedef struct qsl_field qsl_field; /* opaque; library-owned device copy */
+
+/* Loads B (three arrays nz x ny x nx, x fastest, dtype QSL_F32|QSL_F64, in
+ * `mem`) sampled at the vertices of a rectilinear grid with strictly
+ * increasing host coordinates xc[nx], yc[ny], zc[nz] (Sec. "Code Overview":
+ * input cubes on a rectilinear grid), and packs it per vertex as float4:
+ * (B/|B|, |B|) for QSL_PAPER_NORMALIZE_FIRST, (B, |B|) for QSL_RAW_B. A zero
+ * vertex packs as (0,0,0,0). Every n >= 2. QSL_ENONFINITE if any component
+ * is not finite. The handle owns its device memory until qsl_free_field. */
+int qsl_load_field(const void* bx, const void* by, const void* bz, int dtype, int mem, int nx, int ny, int nz,
+                   const double* xc, const double* yc, const double* zc, int interp_mode, void* stream,
+                   qsl_field** out);
+void qsl_free_field(qsl_field* field);
+
+/* ---- tracing ----------------------------------------------------------------- */
+/* Traces one field line per seed (seeds: S x 3 doubles in `mem`) forwards and
+ * backwards to the domain faces (Sec. "Squashing factor calculation"),
+ * integrating the field-line equation (Eq. fl) and the linearised deviation
+ * equation (Eq. dev) for two orthonormal initial deviations (Eq. ic), and
+ * writes one qsl_line per seed (`out`, S records in `mem`). S may be 0. */
+int qsl_trace_seeds(const qsl_field* field, const double* seeds, int64_t S, const qsl_opts* opts, qsl_line* out,
+                    int mem, void* stream);
+
+/* Q / FLL map on a planar slice (Sec. "Code Overview": centre, orientation and
+ * axes span): pixel (i, j), i < nu fastest, is seeded at
+ *   center + ((i + 0.5)/nu - 0.5) u + ((j + 0.5)/nv - 0.5) v.
+ * Outputs (each optional, nu*nv entries in `mem`): q (float, opts.q_form),
+ * length (float), faces (2 bytes per pixel: face_F, face_B), status (byte). */
+int qsl_q_map_2d(const qsl_field* field, const double center[3], const double u[3], const double v[3], int nu,
+                 int nv, const qsl_opts* opts, float* q, float* length, uint8_t* faces, uint8_t* status, int mem,
+                 void* stream);
+
+/* Q / FLL volume: seeds at the cell centres of an nx x ny x nz lattice over the
+ * box [lo, hi] (x fastest). Outputs as qsl_q_map_2d. */
+int qsl_q_volume_3d(const qsl_field* field, const double lo[3], const double hi[3], int nx, int ny, int nz,
+                    const qsl_opts* opts, float* q, float* length, uint8_t* faces, uint8_t* status, int mem,
+                    void* stream);
+
+/* FLEDGE map (Sec. "Adaptive refinements"): gradient magnitude of the Sobel
+ * operator applied to a 2D or 3D length map `length` (shape[0] slowest, in
+ * `mem`). Unnormalised separable Sobel ([-1,0,1] derivative, [1,2,1]
+ * smoothing), half-sample-symmetric boundary, index units; non-finite lengths
+ * count as the largest finite length of the map. s_out has the same shape. */
+int qsl_fledge(const float* length, int ndim, const int64_t* shape, float* s_out, int mem, void* stream);
+
+/* ---- Hilbert-curve refinement (Sec. "Adaptive refinements") ------------------- */
+typedef struct qsl_refine_spec {
+  int32_t ndim;          /* 2: planar slice (center, u, v); 3: volume (lo, hi)         */
+  int32_t coarse_order;  /* p0: the coarse pass samples every 2^(p-p0)-th cell          */
+  int32_t max_order;     /* p: effective lattice 2^p cells per axis (p <= 20 in 3D, 30 in 2D) */
+  int32_t max_iters;     /* refinement iterations (each: curve pass + shifted pass)       */
+  int32_t extent[3];     /* effective lattice extent per axis, <= 2^p, multiple of 2^(p-p0); 0: 2^p */
+  int32_t shift;         /* 1: shifted-curve pass after each refinement pass                */
+  int32_t out_order;     /* converter output order (<= p); 0: p                             */
+  int32_t pad;
+  double center[3], u[3], v[3]; /* planar slice, as in qsl_q_map_2d                     */
+  double lo[3], hi[3];          /* volume box                                             */
+  double tau;                   /* refine a pair when |L_i - L_i+1| > tau; tau < 0: every pair */
+  const uint8_t* proposal;      /* optional (device or host per `mem`): one byte per coarse
+                                   cell, x fastest; nonzero cells are sampled at every
+                                   effective cell before the first iteration          */
+} qsl_refine_spec;
+
+typedef struct qsl_samples {
+  int64_t capacity;  /* entries the arrays below can hold                           */
+  int64_t count;     /* in: samples already present (resume); out: samples now       */
+  uint64_t* key;     /* Hilbert keys at max_order, sorted ascending                    */
+  float* q;          /* opts.q_form per sample                                         */
+  float* length;
+  uint8_t* faces;    /* 2 per sample (optional)                                        */
+  uint8_t* status;   /* 1 per sample (optional)                                        */
+  int32_t iters;     /* out: iterations run                                            */
+  int32_t traced;    /* out: samples traced by this call (low 31 bits)                 */
+} qsl_samples;
+
+/* Refines seeds along a Hilbert curve wherever the field-line length jumps by
+ * more than tau between samples adjacent along the curve, then converts the
+ * samples to the rectilinear output lattice (extent >> (p - out_order) per
+ * axis, x fastest): a cell takes the maximum of its samples, an empty cell the
+ * value interpolated along the curve (log10 for Q). q_grid / l_grid optional.
+ * Samples sit at effective-cell centres; positions as in qsl_q_map_2d /
+ * qsl_q_volume_3d over the effective lattice. With samples->count > 0 the
+ * call resumes from those (sorted) samples instead of the coarse pass.
+ * QSL_ECAPACITY when the capacity is reached (samples so far are valid). */
+int qsl_refine(const qsl_field* field, const qsl_refine_spec* spec, const qsl_opts* opts, qsl_samples* samples,
+               float* q_grid, float* l_grid, int mem, void* stream);
+
+/* Hilbert keys (Skilling's transpose method, curve starting at the origin) of
+ * n cells with coords (n x ndim uint32, axis 0 first) at `bits` per axis
+ * (ndim * bits <= 63), and the inverse. */
+int qsl_hilbert_encode(const uint32_t* coords, int64_t n, int ndim, int bits, uint64_t* keys, int mem,
+                       void* stream);
+int qsl_hilbert_decode(const uint64_t* keys, int64_t n, int ndim, int bits, uint32_t* coords, int mem,
+                       void* stream);
+
+/* Hilbert -> rectilinear converter alone (the last step of qsl_refine): keys
+ * sorted ascending at max_order, vals per key. */
+int qsl_convert(const uint64_t* keys, const float* vals, int64_t n, int ndim, int max_order, const int32_t* extent,
+                int out_order, int log_interp, float* out, int mem, void* stream);
+
+/* Human-readable message of the last failing call on this thread. */
+const char* qsl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSL_H */

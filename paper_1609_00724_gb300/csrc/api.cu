@@ -1,0 +1,501 @@
+// C ABI of the GB300 QSL library: argument checking, device memory for host
+// arguments, field packing and the tracing calls (see include/qsl.h).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "qsl_internal.cuh"
+
+namespace qsl {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+#define QSL_FAIL(code, ...)        \
+  do {                             \
+    qsl::set_error(__VA_ARGS__);   \
+    return code;                   \
+  } while (0)
+
+// Per-thread record of the last tracing call (for qsl_last_stats).
+struct LastCall {
+  DeviceStats* host = nullptr;  // pinned
+  DeviceStats* dev = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int n_ev = 0;
+  cudaStream_t stream = nullptr;
+  int64_t lines = 0, retraced = 0;
+  int64_t* retraced_host = nullptr;  // pinned
+  LaunchShape shape{0, 0, 0};
+  bool valid = false;
+  int device = -1;
+};
+static thread_local LastCall g_last;
+
+static int last_call_begin(cudaStream_t stream) {
+  int dev = 0;
+  QSL_CHECK_CUDA(cudaGetDevice(&dev));
+  if (g_last.device != dev) {
+    // per-thread, per-device bookkeeping buffers (small, kept until exit)
+    QSL_CHECK_CUDA(cudaMallocHost((void**)&g_last.host, sizeof(DeviceStats)));
+    QSL_CHECK_CUDA(cudaMallocHost((void**)&g_last.retraced_host, sizeof(int64_t)));
+    QSL_CHECK_CUDA(cudaMalloc((void**)&g_last.dev, sizeof(DeviceStats)));
+    for (int i = 0; i < 4; ++i) QSL_CHECK_CUDA(cudaEventCreate(&g_last.ev[i]));
+    g_last.device = dev;
+  }
+  QSL_CHECK_CUDA(cudaMemsetAsync(g_last.dev, 0, sizeof(DeviceStats), stream));
+  *g_last.retraced_host = 0;
+  g_last.stream = stream;
+  g_last.n_ev = 0;
+  g_last.valid = true;
+  return QSL_OK;
+}
+
+// ------------------------------------------------------------ options
+void resolve_config(const qsl_field* f, const qsl_opts* o, TraceConfig* c) {
+  bool use = true;
+  for (int a = 0; a < 3; ++a)
+    if (!(o->domain_lo[a] < o->domain_hi[a])) use = false;
+  for (int a = 0; a < 3; ++a) {
+    c->lo[a] = use ? o->domain_lo[a] : f->glo[a];
+    c->hi[a] = use ? o->domain_hi[a] : f->ghi[a];
+  }
+  double d2 = 0;
+  for (int a = 0; a < 3; ++a) d2 += (c->hi[a] - c->lo[a]) * (c->hi[a] - c->lo[a]);
+  c->max_len = o->max_length > 0 ? o->max_length : 20.0 * std::sqrt(d2);
+  c->cell = f->cell;
+  c->tol_abs = o->tol_abs;
+  c->tol_rel = o->tol_rel;
+  c->h_init = o->h_init;
+  c->h_max = o->h_max;
+  c->h_min = o->h_min;
+  c->euler_h = o->euler_h;
+  c->land_tol = o->land_tol * f->cell;
+  c->max_steps = o->max_steps;
+  c->integrator = o->integrator;
+  c->length_only = o->length_only;
+  c->timeout_ns = o->timeout_s > 0 ? (unsigned long long)(o->timeout_s * 1e9) : 0ull;
+}
+
+static int validate_opts(const qsl_field* f, const qsl_opts* o) {
+  if (!f) QSL_FAIL(QSL_EINVAL, "field is NULL");
+  if (!o) QSL_FAIL(QSL_EINVAL, "opts is NULL");
+  if (o->integrator != QSL_RKCK54 && o->integrator != QSL_EULER) QSL_FAIL(QSL_EINVAL, "bad integrator %d", o->integrator);
+  if (o->q_form < 0 || o->q_form > 2) QSL_FAIL(QSL_EINVAL, "bad q_form %d", o->q_form);
+  if (o->precision != QSL_FP32_MIXED && o->precision != QSL_FP64) QSL_FAIL(QSL_EINVAL, "bad precision %d", o->precision);
+  if (!(o->tol_abs > 0) || !(o->tol_rel >= 0)) QSL_FAIL(QSL_EINVAL, "tolerances must be tol_abs > 0, tol_rel >= 0");
+  if (!(o->h_init > 0) || !(o->h_max > 0) || !(o->h_min >= 0)) QSL_FAIL(QSL_EINVAL, "step bounds must be positive");
+  if (o->integrator == QSL_EULER && !(o->euler_h > 0)) QSL_FAIL(QSL_EINVAL, "euler_h must be positive");
+  if (o->max_steps < 1) QSL_FAIL(QSL_EINVAL, "max_steps must be >= 1");
+  if (o->warps_per_block < 0 || o->warps_per_block > 8) QSL_FAIL(QSL_EINVAL, "warps_per_block must be 0..8");
+  if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32) QSL_FAIL(QSL_EINVAL, "blocks_per_sm must be 0..32");
+  if (o->refill_min < 0 || o->refill_min > 32) QSL_FAIL(QSL_EINVAL, "refill_min must be 0..32");
+  return QSL_OK;
+}
+
+int default_shape(const qsl_opts* o, int tangent, int precision, LaunchShape* s) {
+  s->warps_per_block = o->warps_per_block > 0 ? o->warps_per_block : 4;
+  if (o->blocks_per_sm > 0) {
+    s->blocks_per_sm = o->blocks_per_sm;
+  } else {
+    // enough resident warps to hide the gathers; registers set the ceiling
+    int w = tangent ? (precision == QSL_FP64 ? 8 : 16) : 32;
+    s->blocks_per_sm = w / s->warps_per_block;
+    if (s->blocks_per_sm < 1) s->blocks_per_sm = 1;
+  }
+  s->refill_min = o->refill_min > 0 ? o->refill_min : 1;
+  return QSL_OK;
+}
+
+// ------------------------------------------------------------ field packing
+template <class T>
+__global__ void pack_kernel(const T* bx, const T* by, const T* bz, size_t n, int raw, float4* v32, double4_32a* v64,
+                            int* bad) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double B[3] = {(double)bx[i], (double)by[i], (double)bz[i]};
+    if (!isfinite(B[0]) || !isfinite(B[1]) || !isfinite(B[2])) {
+      atomicExch(bad, 1);
+      B[0] = B[1] = B[2] = 0;
+    }
+    double m = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    double o[3];
+    for (int a = 0; a < 3; ++a) o[a] = raw ? B[a] : (m > 0 ? B[a] / m : 0.0);
+    v32[i] = make_float4((float)o[0], (float)o[1], (float)o[2], (float)m);
+    v64[i] = make_double4_32a(o[0], o[1], o[2], m);
+  }
+}
+
+}  // namespace qsl
+
+using namespace qsl;
+
+extern "C" {
+
+const char* qsl_last_error(void) { return g_err.c_str(); }
+
+void qsl_opts_default(qsl_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->integrator = QSL_RKCK54;
+  o->q_form = QSL_Q_PERP;
+  o->precision = QSL_FP32_MIXED;
+  o->tol_abs = 1e-2;
+  o->tol_rel = 1e-2;
+  o->h_init = 0.1;
+  o->h_max = 2.0;
+  o->h_min = 1e-15;
+  o->max_length = 0;
+  o->max_steps = 1000000;
+  o->euler_h = 0.2;
+  o->retrace_q = 1e6;
+  o->land_tol = 1e-12;
+  o->timeout_s = 0;
+}
+
+int qsl_load_field(const void* bx, const void* by, const void* bz, int dtype, int mem, int nx, int ny, int nz,
+                   const double* xc, const double* yc, const double* zc, int interp_mode, void* stream_,
+                   qsl_field** out) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (!out) QSL_FAIL(QSL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!bx || !by || !bz || !xc || !yc || !zc) QSL_FAIL(QSL_EINVAL, "NULL array argument");
+  if (dtype != QSL_F32 && dtype != QSL_F64) QSL_FAIL(QSL_EINVAL, "bad dtype %d", dtype);
+  if (mem != QSL_MEM_HOST && mem != QSL_MEM_DEVICE) QSL_FAIL(QSL_EINVAL, "bad mem %d", mem);
+  if (interp_mode != QSL_PAPER_NORMALIZE_FIRST && interp_mode != QSL_RAW_B)
+    QSL_FAIL(QSL_EINVAL, "bad interp_mode %d", interp_mode);
+  if (nx < 2 || ny < 2 || nz < 2) QSL_FAIL(QSL_EINVAL, "grid must have at least 2 vertices per axis");
+  int n[3] = {nx, ny, nz};
+  const double* ax[3] = {xc, yc, zc};
+  qsl_field* f = new qsl_field();
+  memset(f, 0, sizeof(*f));
+  f->cell = INFINITY;
+  f->uniform = 1;
+  for (int a = 0; a < 3; ++a) {
+    f->n[a] = n[a];
+    double h0 = ax[a][1] - ax[a][0];
+    for (int i = 0; i + 1 < n[a]; ++i) {
+      double h = ax[a][i + 1] - ax[a][i];
+      if (!(h > 0) || !std::isfinite(h)) {
+        delete f;
+        QSL_FAIL(QSL_EINVAL, "axis %d coordinates must be finite and strictly increasing", a);
+      }
+      f->cell = fmin(f->cell, h);
+      // uniform when every vertex sits on org + i*h to 1e-12 of the span
+      double span = ax[a][n[a] - 1] - ax[a][0];
+      double pred = ax[a][0] + (ax[a][n[a] - 1] - ax[a][0]) * (double)(i + 1) / (n[a] - 1);
+      if (fabs(ax[a][i + 1] - pred) > 1e-12 * span) f->uniform = 0;
+      (void)h0;
+    }
+    f->glo[a] = ax[a][0];
+    f->ghi[a] = ax[a][n[a] - 1];
+    f->org[a] = ax[a][0];
+    f->h[a] = (ax[a][n[a] - 1] - ax[a][0]) / (n[a] - 1);
+  }
+  f->mode = interp_mode;
+  cudaGetDevice(&f->device);
+  size_t N = (size_t)nx * ny * nz;
+  size_t esz = dtype == QSL_F32 ? 4 : 8;
+  const void* src[3] = {bx, by, bz};
+  void* staged[3] = {nullptr, nullptr, nullptr};
+  int* bad = nullptr;
+  int bad_h = 0;
+  auto fail = [&](int code) {
+    for (int a = 0; a < 3; ++a) {
+      if (staged[a]) cudaFree(staged[a]);
+      if (f->axis64[a]) cudaFree(f->axis64[a]);
+      if (f->axis32[a]) cudaFree(f->axis32[a]);
+    }
+    if (bad) cudaFree(bad);
+    if (f->v32) cudaFree(f->v32);
+    if (f->v64) cudaFree(f->v64);
+    delete f;
+    return code;
+  };
+#define TRY(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      set_error("%s failed: %s", #call, cudaGetErrorString(e_));                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? QSL_ENOMEM : QSL_ECUDA);                   \
+    }                                                                                          \
+  } while (0)
+  TRY(cudaMalloc((void**)&f->v32, N * sizeof(float4)));
+  TRY(cudaMalloc((void**)&f->v64, N * sizeof(double4_32a)));
+  TRY(cudaMalloc((void**)&bad, sizeof(int)));
+  TRY(cudaMemsetAsync(bad, 0, sizeof(int), stream));
+  for (int a = 0; a < 3; ++a) {
+    TRY(cudaMalloc((void**)&f->axis64[a], n[a] * sizeof(double)));
+    TRY(cudaMalloc((void**)&f->axis32[a], n[a] * sizeof(float)));
+    TRY(cudaMemcpyAsync(f->axis64[a], ax[a], n[a] * sizeof(double), cudaMemcpyHostToDevice, stream));
+    float* tmp = new float[n[a]];
+    for (int i = 0; i < n[a]; ++i) tmp[i] = (float)ax[a][i];
+    cudaError_t e = cudaMemcpy(f->axis32[a], tmp, n[a] * sizeof(float), cudaMemcpyHostToDevice);
+    delete[] tmp;
+    TRY(e);
+    if (mem == QSL_MEM_HOST) {
+      TRY(cudaMalloc(&staged[a], N * esz));
+      TRY(cudaMemcpyAsync(staged[a], src[a], N * esz, cudaMemcpyHostToDevice, stream));
+    }
+  }
+  const void* p[3];
+  for (int a = 0; a < 3; ++a) p[a] = mem == QSL_MEM_HOST ? staged[a] : src[a];
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int blocks = (int)std::min<size_t>((N + 255) / 256, (size_t)sms * 32);
+  if (dtype == QSL_F32)
+    pack_kernel<float><<<blocks, 256, 0, stream>>>((const float*)p[0], (const float*)p[1], (const float*)p[2], N,
+                                                   interp_mode == QSL_RAW_B, f->v32, f->v64, bad);
+  else
+    pack_kernel<double><<<blocks, 256, 0, stream>>>((const double*)p[0], (const double*)p[1],
+                                                    (const double*)p[2], N, interp_mode == QSL_RAW_B, f->v32,
+                                                    f->v64, bad);
+  TRY(cudaGetLastError());
+  TRY(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  TRY(cudaStreamSynchronize(stream));
+  for (int a = 0; a < 3; ++a)
+    if (staged[a]) {
+      cudaFree(staged[a]);
+      staged[a] = nullptr;
+    }
+  cudaFree(bad);
+  bad = nullptr;
+  if (bad_h) {
+    set_error("field contains non-finite values");
+    return fail(QSL_ENONFINITE);
+  }
+#undef TRY
+  *out = f;
+  return QSL_OK;
+}
+
+void qsl_free_field(qsl_field* f) {
+  if (!f) return;
+  cudaFree(f->v32);
+  cudaFree(f->v64);
+  for (int a = 0; a < 3; ++a) {
+    cudaFree(f->axis64[a]);
+    cudaFree(f->axis32[a]);
+  }
+  delete f;
+}
+
+}  // extern "C"
+
+namespace qsl {
+
+// Common driver of qsl_trace_seeds / qsl_q_map_2d / qsl_q_volume_3d: the
+// FP32 (or FP64) trace, then the FP64 retrace of lines above retrace_q.
+int run_lines(const qsl_field* f, const SeedSource& src, int64_t S, const qsl_opts* o, const LineOutputs& out,
+              cudaStream_t stream) {
+  TraceConfig cfg;
+  resolve_config(f, o, &cfg);
+  int rc = last_call_begin(stream);
+  if (rc) return rc;
+  LaunchShape shape;
+  default_shape(o, !o->length_only, o->precision, &shape);
+  g_last.shape = shape;
+  g_last.lines = S;
+  rc = trace_and_assemble(f, src, S, nullptr, cfg, o->precision, shape, out, stream, g_last.dev, &g_last.ev[0]);
+  if (rc) return rc;
+  g_last.n_ev = 2;
+  if (o->precision == QSL_FP32_MIXED && o->retrace_q > 0 && !o->length_only && S > 0) {
+    int64_t* index = nullptr;
+    int64_t* count = nullptr;
+    QSL_CHECK_CUDA(cudaMallocAsync((void**)&index, sizeof(int64_t) * S, stream));
+    QSL_CHECK_CUDA(cudaMallocAsync((void**)&count, sizeof(int64_t), stream));
+    rc = select_retrace(src, S, out, o->retrace_q, index, count, stream);
+    if (rc) return rc;
+    SeedSource s2 = src;
+    s2.index = index;
+    LineOutputs o2 = out;
+    o2.retraced = 1;
+    LaunchShape sh2;
+    default_shape(o, 1, QSL_FP64, &sh2);
+    rc = trace_and_assemble(f, s2, S, count, cfg, QSL_FP64, sh2, o2, stream, g_last.dev, &g_last.ev[2]);
+    if (rc) return rc;
+    g_last.n_ev = 4;
+    QSL_CHECK_CUDA(cudaMemcpyAsync(g_last.retraced_host, count, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+    QSL_CHECK_CUDA(cudaFreeAsync(index, stream));
+    QSL_CHECK_CUDA(cudaFreeAsync(count, stream));
+  }
+  QSL_CHECK_CUDA(cudaMemcpyAsync(g_last.host, g_last.dev, sizeof(DeviceStats), cudaMemcpyDeviceToHost, stream));
+  return QSL_OK;
+}
+
+// Device buffer that is either the caller's (device memory) or a staging copy.
+struct Staged {
+  void* dev = nullptr;
+  void* user = nullptr;
+  size_t bytes = 0;
+  bool owned = false;
+};
+
+static int stage_out(void* user, size_t bytes, int mem, cudaStream_t s, Staged* st) {
+  st->user = user;
+  st->bytes = bytes;
+  if (!user || mem == QSL_MEM_DEVICE) {
+    st->dev = user;
+    return QSL_OK;
+  }
+  QSL_CHECK_CUDA(cudaMallocAsync(&st->dev, bytes ? bytes : 1, s));
+  st->owned = true;
+  return QSL_OK;
+}
+
+static int stage_in(const void* user, size_t bytes, int mem, cudaStream_t s, Staged* st) {
+  st->user = (void*)user;
+  st->bytes = bytes;
+  if (!user || mem == QSL_MEM_DEVICE) {
+    st->dev = (void*)user;
+    return QSL_OK;
+  }
+  QSL_CHECK_CUDA(cudaMallocAsync(&st->dev, bytes ? bytes : 1, s));
+  st->owned = true;
+  if (bytes) QSL_CHECK_CUDA(cudaMemcpyAsync(st->dev, user, bytes, cudaMemcpyHostToDevice, s));
+  return QSL_OK;
+}
+
+static int unstage(Staged* st, bool copy_back, cudaStream_t s) {
+  if (!st->owned) return QSL_OK;
+  if (copy_back && st->bytes)
+    QSL_CHECK_CUDA(cudaMemcpyAsync(st->user, st->dev, st->bytes, cudaMemcpyDeviceToHost, s));
+  QSL_CHECK_CUDA(cudaFreeAsync(st->dev, s));
+  st->owned = false;
+  return QSL_OK;
+}
+
+static int map_common(const qsl_field* f, const SeedSource& src, int64_t S, const qsl_opts* o, float* q,
+                      float* length, uint8_t* faces, uint8_t* status, int mem, cudaStream_t stream) {
+  int rc = validate_opts(f, o);
+  if (rc) return rc;
+  if (mem != QSL_MEM_HOST && mem != QSL_MEM_DEVICE) QSL_FAIL(QSL_EINVAL, "bad mem %d", mem);
+  Staged sq, sl, sf, ss;
+  if ((rc = stage_out(q, S * sizeof(float), mem, stream, &sq))) return rc;
+  if ((rc = stage_out(length, S * sizeof(float), mem, stream, &sl))) return rc;
+  if ((rc = stage_out(faces, S * 2, mem, stream, &sf))) return rc;
+  if ((rc = stage_out(status, S, mem, stream, &ss))) return rc;
+  LineOutputs out{};
+  out.q = (float*)sq.dev;
+  out.length = (float*)sl.dev;
+  out.faces = (uint8_t*)sf.dev;
+  out.status = (uint8_t*)ss.dev;
+  out.q_form = o->q_form;
+  out.skip_open = o->skip_open;
+  // the FP64 retrace selects from the q output; give it a scratch one if absent
+  Staged sq2;
+  if (!out.q && o->precision == QSL_FP32_MIXED && o->retrace_q > 0 && !o->length_only) {
+    QSL_CHECK_CUDA(cudaMallocAsync(&sq2.dev, S * sizeof(float) + 4, stream));
+    sq2.owned = true;
+    sq2.bytes = 0;
+    out.q = (float*)sq2.dev;
+  }
+  rc = run_lines(f, src, S, o, out, stream);
+  if (rc) return rc;
+  if ((rc = unstage(&sq, true, stream)) || (rc = unstage(&sl, true, stream)) || (rc = unstage(&sf, true, stream)) ||
+      (rc = unstage(&ss, true, stream)) || (rc = unstage(&sq2, false, stream)))
+    return rc;
+  if (mem == QSL_MEM_HOST) QSL_CHECK_CUDA(cudaStreamSynchronize(stream));
+  return QSL_OK;
+}
+
+}  // namespace qsl
+
+extern "C" {
+
+int qsl_trace_seeds(const qsl_field* f, const double* seeds, int64_t S, const qsl_opts* o, qsl_line* out, int mem,
+                    void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  int rc = validate_opts(f, o);
+  if (rc) return rc;
+  if (S < 0) QSL_FAIL(QSL_EINVAL, "S must be >= 0");
+  if (S > 0 && (!seeds || !out)) QSL_FAIL(QSL_EINVAL, "seeds/out is NULL");
+  if (mem != QSL_MEM_HOST && mem != QSL_MEM_DEVICE) QSL_FAIL(QSL_EINVAL, "bad mem %d", mem);
+  Staged si, so;
+  if ((rc = stage_in(seeds, S * 3 * sizeof(double), mem, stream, &si))) return rc;
+  if ((rc = stage_out(out, S * sizeof(qsl_line), mem, stream, &so))) return rc;
+  SeedSource src{};
+  src.kind = SEEDS_ARRAY;
+  src.xyz = (const double*)si.dev;
+  LineOutputs lo{};
+  lo.lines = (qsl_line*)so.dev;
+  lo.q_form = QSL_Q_PERP;
+  lo.skip_open = o->skip_open;
+  rc = run_lines(f, src, S, o, lo, stream);
+  if (rc) return rc;
+  if ((rc = unstage(&so, true, stream)) || (rc = unstage(&si, false, stream))) return rc;
+  if (mem == QSL_MEM_HOST) QSL_CHECK_CUDA(cudaStreamSynchronize(stream));
+  return QSL_OK;
+}
+
+int qsl_q_map_2d(const qsl_field* f, const double center[3], const double u[3], const double v[3], int nu, int nv,
+                 const qsl_opts* o, float* q, float* length, uint8_t* faces, uint8_t* status, int mem,
+                 void* stream) {
+  if (!center || !u || !v) QSL_FAIL(QSL_EINVAL, "center/u/v is NULL");
+  if (nu < 0 || nv < 0) QSL_FAIL(QSL_EINVAL, "nu, nv must be >= 0");
+  SeedSource src{};
+  src.kind = SEEDS_PLANE;
+  src.n[0] = nu;
+  src.n[1] = nv;
+  src.n[2] = 1;
+  for (int k = 0; k < 3; ++k) {
+    src.c[k] = center[k];
+    src.u[k] = u[k];
+    src.v[k] = v[k];
+  }
+  return map_common(f, src, (int64_t)nu * nv, o, q, length, faces, status, mem, (cudaStream_t)stream);
+}
+
+int qsl_q_volume_3d(const qsl_field* f, const double lo[3], const double hi[3], int nx, int ny, int nz,
+                    const qsl_opts* o, float* q, float* length, uint8_t* faces, uint8_t* status, int mem,
+                    void* stream) {
+  if (!lo || !hi) QSL_FAIL(QSL_EINVAL, "lo/hi is NULL");
+  if (nx < 0 || ny < 0 || nz < 0) QSL_FAIL(QSL_EINVAL, "lattice sizes must be >= 0");
+  SeedSource src{};
+  src.kind = SEEDS_VOLUME;
+  src.n[0] = nx;
+  src.n[1] = ny;
+  src.n[2] = nz;
+  for (int k = 0; k < 3; ++k) {
+    src.c[k] = lo[k];
+    src.u[k] = hi[k];
+  }
+  return map_common(f, src, (int64_t)nx * ny * nz, o, q, length, faces, status, mem, (cudaStream_t)stream);
+}
+
+int qsl_last_stats(qsl_stats* s) {
+  if (!s) QSL_FAIL(QSL_EINVAL, "out is NULL");
+  memset(s, 0, sizeof(*s));
+  if (!g_last.valid) QSL_FAIL(QSL_EINVAL, "no tracing call on this thread yet");
+  QSL_CHECK_CUDA(cudaStreamSynchronize(g_last.stream));
+  s->lines = g_last.lines;
+  s->stage_evals = (int64_t)g_last.host->stage_evals;
+  s->accepted = (int64_t)g_last.host->accepted;
+  s->rejected = (int64_t)g_last.host->rejected;
+  s->landing = (int64_t)g_last.host->landing;
+  s->retraced = *g_last.retraced_host;
+  double ms = 0;
+  for (int i = 0; i + 1 < g_last.n_ev; i += 2) {
+    float t = 0;
+    QSL_CHECK_CUDA(cudaEventElapsedTime(&t, g_last.ev[i], g_last.ev[i + 1]));
+    ms += t;
+  }
+  s->kernel_ms = ms;
+  s->warps_per_block = g_last.shape.warps_per_block;
+  s->blocks_per_sm = g_last.shape.blocks_per_sm;
+  s->refill_min = g_last.shape.refill_min;
+  if (g_last.host->timeouts) QSL_FAIL(QSL_ETIMEOUT, "device watchdog expired in %llu warps", g_last.host->timeouts);
+  return QSL_OK;
+}
+
+}  // extern "C"

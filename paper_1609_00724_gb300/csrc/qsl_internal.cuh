@@ -1,0 +1,131 @@
+// Internal declarations of the GB300 QSL library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/qsl.h"
+
+namespace qsl {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+#define QSL_CHECK_CUDA(call)                                                             \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      qsl::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? QSL_ENOMEM : QSL_ECUDA;                   \
+    }                                                                                    \
+  } while (0)
+
+// ---------------------------------------------------------------- field
+// Device view of a packed field. Vertex (i, j, k) is v[(k*ny + j)*nx + i].
+template <class R>
+struct V4;
+template <>
+struct V4<float> {
+  typedef float4 type;
+};
+template <>
+struct V4<double> {
+  typedef double4_32a type;
+};
+
+template <class R>
+struct FieldView {
+  const typename V4<R>::type* v;
+  const R* axis[3];   // vertex coordinates per axis (rectilinear grids)
+  R org[3];           // first vertex per axis (uniform grids)
+  R inv_h[3];         // 1 / spacing per axis (uniform grids)
+  int n[3];
+  int uniform;        // 1: all axes uniform (fast cell location)
+  int raw;            // 1: QSL_RAW_B packing, 0: paper packing
+};
+
+}  // namespace qsl
+
+struct qsl_field {
+  int n[3];
+  int mode;
+  int uniform;
+  double cell;                 // smallest spacing over all axes
+  double glo[3], ghi[3];       // grid extent
+  double org[3], h[3];         // uniform spacing (valid when uniform)
+  float4* v32;                 // packed vertices, FP32
+  double4_32a* v64;                // packed vertices, FP64 (for FP64 tracing)
+  double* axis64[3];           // device axis coordinates
+  float* axis32[3];
+  int device;
+};
+
+namespace qsl {
+
+// Where the seeds of a tracing launch come from.
+enum SeedKind { SEEDS_ARRAY = 0, SEEDS_PLANE = 1, SEEDS_VOLUME = 2, SEEDS_KEYS2 = 3, SEEDS_KEYS3 = 4 };
+
+struct SeedSource {
+  int kind;
+  int bits;                 // Hilbert bits per axis (SEEDS_KEYS*)
+  int n[3];                 // plane: (nu, nv, 1); volume and keys: lattice extent
+  double c[3], u[3], v[3];  // plane: centre + axes; volume/keys3: lo (c) and hi (u)
+  const double* xyz;        // SEEDS_ARRAY: S x 3
+  const uint64_t* keys;     // SEEDS_KEYS*: Hilbert keys
+  const int64_t* index;     // optional: local seed j -> global seed index[j]
+};
+
+// Outputs of the assembly step (each optional).
+struct LineOutputs {
+  qsl_line* lines;
+  float* q;
+  float* length;
+  uint8_t* faces;
+  uint8_t* status;
+  int q_form;
+  int skip_open;
+  int retraced;          // set QSL_FLAG_RETRACED on written seeds
+};
+
+struct DeviceStats {
+  unsigned long long stage_evals, accepted, rejected, landing, lines, timeouts;
+};
+
+// Resolved tracing parameters (domain units).
+struct TraceConfig {
+  double lo[3], hi[3];
+  double max_len;
+  double cell;
+  double tol_abs, tol_rel;
+  double h_init, h_max, h_min, euler_h;
+  double land_tol;       // domain units
+  long long max_steps;
+  int integrator;
+  int length_only;
+  unsigned long long timeout_ns;  // device watchdog per warp (%globaltimer), 0 = none
+};
+
+struct LaunchShape {
+  int warps_per_block;
+  int blocks_per_sm;
+  int refill_min;
+};
+
+// Runs the tracer over `n_seeds` seeds of `src` (n_seeds may live on the
+// device: `n_seeds_dev` != nullptr overrides n_seeds as an upper bound), then
+// assembles Q/FLL into `out`. Precision: 0 = FP32 trace, 1 = FP64 trace.
+// ev (optional): two events recorded around the tracer kernel.
+int trace_and_assemble(const qsl_field* f, const SeedSource& src, int64_t n_seeds, const int64_t* n_seeds_dev,
+                       const TraceConfig& cfg, int precision, const LaunchShape& shape, const LineOutputs& out,
+                       cudaStream_t stream, DeviceStats* stats_dev, cudaEvent_t* ev);
+
+// Selects seeds whose chosen Q exceeds `threshold` (or is not finite while
+// L is) into `index` (device), count into count_dev (device).
+int select_retrace(const SeedSource& src, int64_t n_seeds, const LineOutputs& out, double threshold,
+                   int64_t* index, int64_t* count_dev, cudaStream_t stream);
+
+void resolve_config(const qsl_field* f, const qsl_opts* o, TraceConfig* cfg);
+int default_shape(const qsl_opts* o, int tangent, int precision, LaunchShape* s);
+
+}  // namespace qsl

@@ -1,0 +1,763 @@
+// Hilbert-curve refinement and the Hilbert -> rectilinear converter
+// (Sec. "Adaptive refinements" of arXiv:1609.00724) for sm_103a.
+//
+// Samples live as structure-of-arrays sorted by Hilbert key (key, q, length,
+// faces, status). One refinement iteration:
+//   (A) flag every pair adjacent along the curve with key gap > 1 and
+//       |L_i - L_i+1| > tau; the new sample is the in-region cell nearest the
+//       mean key (the region is the effective lattice; skipping whole
+//       out-of-region blocks of the curve when it leaves a clipped box);
+//   (B) shifted-curve pass: keys of the lattice shifted by S = 2^(p-1) +- the
+//       half coarse spacing (alternating) on a curve of order p+1, sorted, the
+//       same flag rule, new cells mapped back by -S;
+// after each pass the new samples are traced and merged (radix sort by key).
+// The host loop reads one count per pass.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+#include <cstring>
+#include <vector>
+
+#include "hilbert_dev.cuh"
+#include "qsl_internal.cuh"
+
+namespace qsl {
+int run_lines(const qsl_field* f, const SeedSource& src, int64_t S, const qsl_opts* o, const LineOutputs& out,
+              cudaStream_t stream);
+}
+
+namespace qsl {
+namespace {
+
+const uint64_t NONE = ~0ull;
+
+__global__ void encode_kernel(const uint32_t* __restrict__ c, int64_t n, int nd, int bits, uint64_t* keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t cc[3] = {c[nd * i], c[nd * i + 1], nd == 3 ? c[nd * i + 2] : 0u};
+    keys[i] = hilbert_key_dev(cc, nd, bits);
+  }
+}
+
+__global__ void decode_kernel(const uint64_t* __restrict__ keys, int64_t n, int nd, int bits, uint32_t* c) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t cc[3];
+    hilbert_coords_dev(keys[i], nd, bits, cc);
+    for (int a = 0; a < nd; ++a) c[nd * i + a] = cc[a];
+  }
+}
+
+struct Region {
+  uint64_t lo[3], hi[3];  // lo <= c < hi per axis
+};
+
+__device__ __forceinline__ bool in_region(const uint32_t* c, int nd, const Region& r) {
+  for (int a = 0; a < nd; ++a)
+    if (c[a] < r.lo[a] || c[a] >= r.hi[a]) return false;
+  return true;
+}
+
+// In-region cell nearest to key m strictly between k_lo and k_hi along the
+// curve (lower one on ties); skips whole aligned out-of-region blocks.
+__device__ bool nearest_in_region(uint64_t m, uint64_t k_lo, uint64_t k_hi, int nd, int bits, const Region& r,
+                                  uint64_t* out) {
+  uint64_t found[2];
+  bool have[2] = {false, false};
+  for (int d = 0; d < 2; ++d) {
+    uint64_t k = m;
+    for (int guard = 0; guard < 4096; ++guard) {
+      if (k <= k_lo || k >= k_hi) break;
+      uint32_t c[3] = {0, 0, 0};
+      hilbert_coords_dev(k, nd, bits, c);
+      if (in_region(c, nd, r)) {
+        found[d] = k;
+        have[d] = true;
+        break;
+      }
+      int lev = 0;
+      while (lev < bits) {
+        int l = lev + 1;
+        bool outside = false;
+        for (int a = 0; a < nd; ++a) {
+          uint64_t b0 = ((uint64_t)c[a] >> l) << l;
+          uint64_t b1 = b0 + (1ull << l);
+          if (b1 <= r.lo[a] || b0 >= r.hi[a]) outside = true;
+        }
+        if (!outside) break;
+        lev = l;
+      }
+      uint64_t blk = 1ull << (nd * lev);
+      uint64_t start = (k / blk) * blk;
+      if (d == 0) {
+        if (start == 0) break;
+        k = start - 1;
+      } else {
+        k = start + blk;
+      }
+    }
+  }
+  if (have[0] && have[1]) {
+    *out = (m - found[0] <= found[1] - m) ? found[0] : found[1];
+    return true;
+  }
+  if (have[0]) {
+    *out = found[0];
+    return true;
+  }
+  if (have[1]) {
+    *out = found[1];
+    return true;
+  }
+  return false;
+}
+
+// Coarse pass keys: cell (i*R + R/2, ...) of the effective lattice.
+__global__ void coarse_keys_kernel(int64_t n, int nd, int bits, int R, int nc0, int nc1, uint64_t* keys) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = g % nc0, rem = g / nc0;
+    int64_t j = rem % nc1, k = rem / nc1;
+    uint32_t c[3] = {(uint32_t)(i * R + R / 2), (uint32_t)(j * R + R / 2), (uint32_t)(k * R + R / 2)};
+    keys[g] = hilbert_key_dev(c, nd, bits);
+  }
+}
+
+// Proposal: every effective cell of the flagged coarse cells except the coarse
+// sample itself (it already exists). One thread per (flagged cell, sub-cell).
+__global__ void proposal_keys_kernel(const int64_t* __restrict__ cells, const int64_t* ncells_dev, int nd, int bits,
+                                     int R, int nc0, int nc1, uint64_t* keys, int64_t* count) {
+  int64_t ncells = *ncells_dev;
+  int64_t per = 1;
+  for (int a = 0; a < nd; ++a) per *= R;
+  int64_t total = ncells * per;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t cell = cells[t / per], sub = t % per;
+    int64_t i = cell % nc0, rem = cell / nc0;
+    int64_t j = rem % nc1, k = rem / nc1;
+    int64_t s0 = sub % R, s1 = (sub / R) % R, s2 = nd == 3 ? sub / (R * R) : 0;
+    if (s0 == R / 2 && s1 == R / 2 && (nd == 2 || s2 == R / 2)) continue;
+    uint32_t c[3] = {(uint32_t)(i * R + s0), (uint32_t)(j * R + s1), (uint32_t)(k * R + s2)};
+    unsigned long long pos = atomicAdd((unsigned long long*)count, 1ull);
+    keys[pos] = hilbert_key_dev(c, nd, bits);
+  }
+}
+
+__global__ void mask_cells_kernel(const uint8_t* __restrict__ mask, int64_t n, int64_t* cells, int64_t* count) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    if (mask[g]) {
+      unsigned long long pos = atomicAdd((unsigned long long*)count, 1ull);
+      cells[pos] = g;
+    }
+  }
+}
+
+// Pass A flags: candidate key per pair, NONE when not refined.
+__global__ void flag_pairs_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ L, int64_t n,
+                                  double tau, int nd, int bits, Region reg, uint64_t* cand) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + 1 < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t a = keys[i], b = keys[i + 1];
+    uint64_t out = NONE;
+    if (b - a > 1 && fabs((double)L[i + 1] - (double)L[i]) > tau) {
+      uint64_t got;
+      if (nearest_in_region(a + (b - a) / 2, a, b, nd, bits, reg, &got)) out = got;
+    }
+    cand[i] = out;
+  }
+}
+
+// Shifted keys of all samples (curve of order p+1).
+__global__ void shift_keys_kernel(const uint64_t* __restrict__ keys, int64_t n, int nd, int bits, uint32_t S,
+                                  uint64_t* skeys, int64_t* perm) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c[3] = {0, 0, 0};
+    hilbert_coords_dev(keys[i], nd, bits, c);
+    for (int a = 0; a < nd; ++a) c[a] += S;
+    skeys[i] = hilbert_key_dev(c, nd, bits + 1);
+    perm[i] = i;
+  }
+}
+
+// Pass B flags along the shifted curve; candidates are keys on the original curve.
+__global__ void flag_shifted_kernel(const uint64_t* __restrict__ skeys, const int64_t* __restrict__ perm,
+                                    const float* __restrict__ L, int64_t n, double tau, int nd, int bits, uint32_t S,
+                                    Region sreg, uint64_t* cand) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + 1 < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t a = skeys[i], b = skeys[i + 1];
+    uint64_t out = NONE;
+    if (b - a > 1 && fabs((double)L[perm[i + 1]] - (double)L[perm[i]]) > tau) {
+      uint64_t got;
+      if (nearest_in_region(a + (b - a) / 2, a, b, nd, bits + 1, sreg, &got)) {
+        uint32_t c[3] = {0, 0, 0};
+        hilbert_coords_dev(got, nd, bits + 1, c);
+        for (int a2 = 0; a2 < nd; ++a2) c[a2] -= S;
+        out = hilbert_key_dev(c, nd, bits);
+      }
+    }
+    cand[i] = out;
+  }
+}
+
+// Stream compaction of candidates != NONE (exclusive scan of flags).
+__global__ void cand_flags_kernel(const uint64_t* __restrict__ cand, int64_t n, int64_t* flags) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    flags[i] = cand[i] != NONE;
+}
+
+__global__ void cand_scatter_kernel(const uint64_t* __restrict__ cand, const int64_t* __restrict__ pos, int64_t n,
+                                    int64_t limit, uint64_t* out, int64_t* count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (cand[i] != NONE && pos[i] < limit) out[pos[i]] = cand[i];
+    if (i == n - 1) *count = pos[i] + (cand[i] != NONE ? 1 : 0);
+  }
+}
+
+__global__ void iota_kernel(int64_t* p, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = i;
+}
+
+__global__ void gather_kernel(const int64_t* __restrict__ perm, int64_t n, const float* q, const float* L,
+                              const uint8_t* fa, const uint8_t* st, float* q2, float* L2, uint8_t* fa2,
+                              uint8_t* st2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s = perm[i];
+    q2[i] = q[s];
+    L2[i] = L[s];
+    fa2[2 * i] = fa[2 * s];
+    fa2[2 * i + 1] = fa[2 * s + 1];
+    st2[i] = st[s];
+  }
+}
+
+// Converter: one thread per output cell.
+__global__ void convert_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ vals, int64_t n, int nd,
+                               int bits, int d, int eo0, int eo1, int eo2, int log_interp, float* out) {
+  int64_t N = (int64_t)eo0 * eo1 * eo2;
+  uint64_t blk = 1ull << (nd * d);
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < N; o += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = o % eo0, rem = o / eo0;
+    int64_t j = rem % eo1, k = rem / eo1;
+    uint32_t c[3] = {(uint32_t)(i << d), (uint32_t)(j << d), (uint32_t)(k << d)};
+    uint64_t k0 = (hilbert_key_dev(c, nd, bits) / blk) * blk;
+    uint64_t k1 = k0 + blk;
+    // lower bound of k0
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if (keys[mid] < k0) lo = mid + 1; else hi = mid;
+    }
+    float res = __int_as_float(0x7fc00000);
+    if (lo < n && keys[lo] < k1) {
+      // maximum over the samples of the cell (NaNs ignored unless all NaN)
+      for (int64_t s = lo; s < n && keys[s] < k1; ++s) {
+        float v = vals[s];
+        if (isnan(res) || v > res) res = isnan(v) ? res : v;
+      }
+    } else if (n > 0) {
+      int64_t succ = lo, pred = lo - 1;
+      if (succ >= n) {
+        res = vals[pred];
+      } else if (pred < 0) {
+        res = vals[succ];
+      } else {
+        double kc = (double)k0 + 0.5 * (double)(blk - 1);
+        double t = (kc - (double)keys[pred]) / ((double)keys[succ] - (double)keys[pred]);
+        double a = vals[pred], b = vals[succ];
+        if (log_interp)
+          res = (float)exp10((1 - t) * log10(a) + t * log10(b));
+        else
+          res = (float)((1 - t) * a + t * b);
+      }
+    }
+    out[o] = res;
+  }
+}
+
+int grid_for(int64_t n) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t b = (n + 255) / 256;
+  if (b > (int64_t)sms * 16) b = (int64_t)sms * 16;
+  return b < 1 ? 1 : (int)b;
+}
+
+// Scratch buffers of one refine call (stream-ordered allocations).
+struct Scratch {
+  std::vector<void*> bufs;
+  cudaStream_t s;
+  template <class T>
+  int alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, count * sizeof(T) + 16, s);
+    if (e != cudaSuccess) {
+      set_error("cudaMallocAsync of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      return QSL_ENOMEM;
+    }
+    bufs.push_back(q);
+    *p = (T*)q;
+    return QSL_OK;
+  }
+  ~Scratch() {
+    for (void* b : bufs) cudaFreeAsync(b, s);
+  }
+};
+
+// Radix sort of (key, value) pairs on the low `bits` bits.
+int sort_pairs(const uint64_t* kin, uint64_t* kout, const int64_t* vin, int64_t* vout, int64_t n, int bits,
+               cudaStream_t s) {
+  if (n <= 0) return QSL_OK;
+  size_t tmp = 0;
+  QSL_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, kin, kout, vin, vout, n, 0, bits, s));
+  void* t = nullptr;
+  QSL_CHECK_CUDA(cudaMallocAsync(&t, tmp + 16, s));
+  QSL_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(t, tmp, kin, kout, vin, vout, n, 0, bits, s));
+  QSL_CHECK_CUDA(cudaFreeAsync(t, s));
+  return QSL_OK;
+}
+
+int exclusive_sum(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return QSL_OK;
+  size_t tmp = 0;
+  QSL_CHECK_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, in, out, n, s));
+  void* t = nullptr;
+  QSL_CHECK_CUDA(cudaMallocAsync(&t, tmp + 16, s));
+  QSL_CHECK_CUDA(cub::DeviceScan::ExclusiveSum(t, tmp, in, out, n, s));
+  QSL_CHECK_CUDA(cudaFreeAsync(t, s));
+  return QSL_OK;
+}
+
+}  // namespace
+
+int convert_device(const uint64_t* keys, const float* vals, int64_t n, int nd, int p, const int32_t* extent,
+                   int out_order, int log_interp, float* out, cudaStream_t s) {
+  int d = p - out_order;
+  int eo[3] = {1, 1, 1};
+  for (int a = 0; a < nd; ++a) eo[a] = extent[a] >> d;
+  int64_t N = (int64_t)eo[0] * eo[1] * eo[2];
+  if (N > 0) {
+    convert_kernel<<<grid_for(N), 256, 0, s>>>(keys, vals, n, nd, p, d, eo[0], eo[1], eo[2], log_interp, out);
+    QSL_CHECK_CUDA(cudaGetLastError());
+  }
+  return QSL_OK;
+}
+
+// The refinement driver (device arrays). `smp` arrays are device pointers.
+int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o, qsl_samples* smp,
+                  float* q_grid, float* l_grid, int mem_proposal, cudaStream_t s) {
+  const int nd = sp->ndim, p = sp->max_order, p0 = sp->coarse_order;
+  const int R = 1 << (p - p0);
+  int ext[3] = {1, 1, 1};
+  for (int a = 0; a < nd; ++a) ext[a] = sp->extent[a] > 0 ? sp->extent[a] : (1 << p);
+  Region reg;
+  for (int a = 0; a < 3; ++a) {
+    reg.lo[a] = 0;
+    reg.hi[a] = a < nd ? (uint64_t)ext[a] : 1;
+  }
+  SeedSource src{};
+  src.kind = nd == 2 ? SEEDS_KEYS2 : SEEDS_KEYS3;
+  src.bits = p;
+  for (int a = 0; a < 3; ++a) src.n[a] = ext[a];
+  for (int k = 0; k < 3; ++k) {
+    if (nd == 2) {
+      src.c[k] = sp->center[k];
+      src.u[k] = sp->u[k];
+      src.v[k] = sp->v[k];
+    } else {
+      src.c[k] = sp->lo[k];
+      src.u[k] = sp->hi[k];
+    }
+  }
+  Scratch sc;
+  sc.s = s;
+  int64_t cap = smp->capacity;
+  int64_t n = smp->count;
+  int rc;
+  int64_t* cnt = nullptr;  // device counter
+  int64_t* cnt_h = nullptr;
+  QSL_CHECK_CUDA(cudaMallocHost((void**)&cnt_h, sizeof(int64_t)));
+  struct HostFree {
+    int64_t* p;
+    ~HostFree() { cudaFreeHost(p); }
+  } hf{cnt_h};
+  if ((rc = sc.alloc(&cnt, 1))) return rc;
+  int64_t traced = 0;
+  bool cap_hit = false;
+
+  // temporaries sized to the capacity
+  uint64_t *kA = nullptr, *cand = nullptr, *sk = nullptr, *sk2 = nullptr;
+  int64_t *perm = nullptr, *perm2 = nullptr, *flags = nullptr, *pos = nullptr;
+  float *q2 = nullptr, *L2 = nullptr;
+  uint8_t *fa2 = nullptr, *st2 = nullptr;
+  if ((rc = sc.alloc(&kA, cap)) || (rc = sc.alloc(&cand, cap)) || (rc = sc.alloc(&sk, cap)) ||
+      (rc = sc.alloc(&sk2, cap)) || (rc = sc.alloc(&perm, cap)) || (rc = sc.alloc(&perm2, cap)) ||
+      (rc = sc.alloc(&flags, cap)) || (rc = sc.alloc(&pos, cap)) || (rc = sc.alloc(&q2, cap)) ||
+      (rc = sc.alloc(&L2, cap)) || (rc = sc.alloc(&fa2, 2 * cap)) || (rc = sc.alloc(&st2, cap)))
+    return rc;
+
+  // trace samples [off, off + m) (keys already written) and merge everything
+  auto trace_and_merge = [&](int64_t off, int64_t m) -> int {
+    if (m <= 0) return QSL_OK;
+    SeedSource s2 = src;
+    s2.keys = smp->key + off;
+    LineOutputs lo{};
+    lo.q = smp->q + off;
+    lo.length = smp->length + off;
+    lo.faces = smp->faces + 2 * off;
+    lo.status = smp->status + off;
+    lo.q_form = o->q_form;
+    lo.skip_open = o->skip_open;
+    int r = run_lines(f, s2, m, o, lo, s);
+    if (r) return r;
+    traced += m;
+    int64_t tot = off + m;
+    iota_kernel<<<grid_for(tot), 256, 0, s>>>(perm, tot);
+    QSL_CHECK_CUDA(cudaGetLastError());
+    if ((r = sort_pairs(smp->key, kA, perm, perm2, tot, nd * p, s))) return r;
+    gather_kernel<<<grid_for(tot), 256, 0, s>>>(perm2, tot, smp->q, smp->length, smp->faces, smp->status, q2, L2,
+                                                fa2, st2);
+    QSL_CHECK_CUDA(cudaGetLastError());
+    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, kA, tot * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->q, q2, tot * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->length, L2, tot * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->faces, fa2, 2 * tot, cudaMemcpyDeviceToDevice, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->status, st2, tot, cudaMemcpyDeviceToDevice, s));
+    return QSL_OK;
+  };
+
+  // compact candidates cand[0..m) into smp->key[n..), returns the number added
+  auto compact = [&](int64_t m, int64_t* added) -> int {
+    *added = 0;
+    if (m <= 0) return QSL_OK;
+    cand_flags_kernel<<<grid_for(m), 256, 0, s>>>(cand, m, flags);
+    QSL_CHECK_CUDA(cudaGetLastError());
+    int r = exclusive_sum(flags, pos, m, s);
+    if (r) return r;
+    cand_scatter_kernel<<<grid_for(m), 256, 0, s>>>(cand, pos, m, cap - n, smp->key + n, cnt);
+    QSL_CHECK_CUDA(cudaGetLastError());
+    QSL_CHECK_CUDA(cudaMemcpyAsync(cnt_h, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    QSL_CHECK_CUDA(cudaStreamSynchronize(s));
+    int64_t a = *cnt_h;
+    if (a > cap - n) {
+      a = cap - n;
+      cap_hit = true;
+    }
+    *added = a;
+    return QSL_OK;
+  };
+
+  if (n == 0) {
+    // coarse pass
+    int nc[3] = {1, 1, 1};
+    for (int a = 0; a < nd; ++a) nc[a] = ext[a] / R;
+    int64_t m = (int64_t)nc[0] * nc[1] * nc[2];
+    if (m > cap) {
+      set_error("capacity %lld below the %lld coarse samples", (long long)cap, (long long)m);
+      return QSL_ECAPACITY;
+    }
+    coarse_keys_kernel<<<grid_for(m), 256, 0, s>>>(m, nd, p, R, nc[0], nc[1], smp->key);
+    QSL_CHECK_CUDA(cudaGetLastError());
+    // trace in curve order (neighbouring seeds on neighbouring lanes)
+    iota_kernel<<<grid_for(m), 256, 0, s>>>(perm, m);
+    if ((rc = sort_pairs(smp->key, kA, perm, perm2, m, nd * p, s))) return rc;
+    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, kA, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    if ((rc = trace_and_merge(0, m))) return rc;
+    n = m;
+    // optional proposal: flagged coarse cells are sampled densely
+    if (sp->proposal) {
+      const uint8_t* mask = sp->proposal;
+      uint8_t* mask_dev = nullptr;
+      if (mem_proposal == QSL_MEM_HOST) {
+        if ((rc = sc.alloc(&mask_dev, m))) return rc;
+        QSL_CHECK_CUDA(cudaMemcpyAsync(mask_dev, mask, m, cudaMemcpyHostToDevice, s));
+        mask = mask_dev;
+      }
+      int64_t* cells = nullptr;
+      if ((rc = sc.alloc(&cells, m))) return rc;
+      QSL_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t), s));
+      mask_cells_kernel<<<grid_for(m), 256, 0, s>>>(mask, m, cells, cnt);
+      QSL_CHECK_CUDA(cudaMemcpyAsync(cnt_h, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      QSL_CHECK_CUDA(cudaStreamSynchronize(s));
+      int64_t ncells = *cnt_h;
+      int64_t per = 1;
+      for (int a = 0; a < nd; ++a) per *= R;
+      int64_t want = ncells * (per - 1);
+      if (want > cap - n) {
+        set_error("capacity too small for the proposal (%lld more samples)", (long long)want);
+        return QSL_ECAPACITY;
+      }
+      int64_t* ncd = nullptr;
+      if ((rc = sc.alloc(&ncd, 1))) return rc;
+      QSL_CHECK_CUDA(cudaMemcpyAsync(ncd, cnt, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+      QSL_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t), s));
+      if (want > 0) {
+        proposal_keys_kernel<<<grid_for(want), 256, 0, s>>>(cells, ncd, nd, p, R, nc[0], nc[1], smp->key + n, cnt);
+        QSL_CHECK_CUDA(cudaGetLastError());
+        if ((rc = trace_and_merge(n, want))) return rc;
+        n += want;
+      }
+    }
+  }
+
+  int it = 0;
+  for (; it < sp->max_iters && !cap_hit; ++it) {
+    int64_t added_total = 0, added = 0;
+    // (A) along the curve
+    if (n > 1) {
+      flag_pairs_kernel<<<grid_for(n - 1), 256, 0, s>>>(smp->key, smp->length, n, sp->tau, nd, p, reg, cand);
+      QSL_CHECK_CUDA(cudaGetLastError());
+      if ((rc = compact(n - 1, &added))) return rc;
+      if ((rc = trace_and_merge(n, added))) return rc;
+      n += added;
+      added_total += added;
+    }
+    // (B) along the shifted curve
+    if (sp->shift && n > 1 && !cap_hit) {
+      uint32_t half = 1u << (p - 1 >= 0 ? p - 1 : 0);
+      uint32_t dsh = (uint32_t)(R / 2 > 1 ? R / 2 : 1);
+      uint32_t S = (it % 2 == 0) ? half + dsh : half - (dsh < half ? dsh : half);
+      shift_keys_kernel<<<grid_for(n), 256, 0, s>>>(smp->key, n, nd, p, S, sk, perm);
+      QSL_CHECK_CUDA(cudaGetLastError());
+      if ((rc = sort_pairs(sk, sk2, perm, perm2, n, nd * (p + 1), s))) return rc;
+      Region sreg;
+      for (int a = 0; a < 3; ++a) {
+        sreg.lo[a] = reg.lo[a] + (a < nd ? S : 0);
+        sreg.hi[a] = reg.hi[a] + (a < nd ? S : 0);
+      }
+      flag_shifted_kernel<<<grid_for(n - 1), 256, 0, s>>>(sk2, perm2, smp->length, n, sp->tau, nd, p, S, sreg, cand);
+      QSL_CHECK_CUDA(cudaGetLastError());
+      if ((rc = compact(n - 1, &added))) return rc;
+      if ((rc = trace_and_merge(n, added))) return rc;
+      n += added;
+      added_total += added;
+    }
+    if (added_total == 0) break;
+  }
+  smp->count = n;
+  smp->iters = it;
+  smp->traced = (int32_t)(traced & 0x7fffffff);
+  int out_order = sp->out_order > 0 ? sp->out_order : p;
+  if (q_grid && (rc = convert_device(smp->key, smp->q, n, nd, p, ext, out_order, 1, q_grid, s))) return rc;
+  if (l_grid && (rc = convert_device(smp->key, smp->length, n, nd, p, ext, out_order, 0, l_grid, s))) return rc;
+  if (cap_hit) {
+    set_error("sample capacity %lld reached", (long long)cap);
+    return QSL_ECAPACITY;
+  }
+  return QSL_OK;
+}
+
+}  // namespace qsl
+
+using namespace qsl;
+
+extern "C" {
+
+int qsl_hilbert_encode(const uint32_t* coords, int64_t n, int ndim, int bits, uint64_t* keys, int mem,
+                       void* stream_) {
+  cudaStream_t s = (cudaStream_t)stream_;
+  if ((ndim != 2 && ndim != 3) || bits < 0 || ndim * bits > 63 || n < 0) {
+    set_error("bad ndim/bits/n");
+    return QSL_EINVAL;
+  }
+  if (n == 0) return QSL_OK;
+  if (!coords || !keys) {
+    set_error("NULL array");
+    return QSL_EINVAL;
+  }
+  const uint32_t* c = coords;
+  uint64_t* k = keys;
+  if (mem == QSL_MEM_HOST) {
+    QSL_CHECK_CUDA(cudaMallocAsync((void**)&c, n * ndim * 4, s));
+    QSL_CHECK_CUDA(cudaMallocAsync((void**)&k, n * 8, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync((void*)c, coords, n * ndim * 4, cudaMemcpyHostToDevice, s));
+  }
+  encode_kernel<<<grid_for(n), 256, 0, s>>>(c, n, ndim, bits, k);
+  QSL_CHECK_CUDA(cudaGetLastError());
+  if (mem == QSL_MEM_HOST) {
+    QSL_CHECK_CUDA(cudaMemcpyAsync(keys, k, n * 8, cudaMemcpyDeviceToHost, s));
+    QSL_CHECK_CUDA(cudaFreeAsync((void*)c, s));
+    QSL_CHECK_CUDA(cudaFreeAsync(k, s));
+    QSL_CHECK_CUDA(cudaStreamSynchronize(s));
+  }
+  return QSL_OK;
+}
+
+int qsl_hilbert_decode(const uint64_t* keys, int64_t n, int ndim, int bits, uint32_t* coords, int mem,
+                       void* stream_) {
+  cudaStream_t s = (cudaStream_t)stream_;
+  if ((ndim != 2 && ndim != 3) || bits < 0 || ndim * bits > 63 || n < 0) {
+    set_error("bad ndim/bits/n");
+    return QSL_EINVAL;
+  }
+  if (n == 0) return QSL_OK;
+  if (!coords || !keys) {
+    set_error("NULL array");
+    return QSL_EINVAL;
+  }
+  const uint64_t* k = keys;
+  uint32_t* c = coords;
+  if (mem == QSL_MEM_HOST) {
+    QSL_CHECK_CUDA(cudaMallocAsync((void**)&k, n * 8, s));
+    QSL_CHECK_CUDA(cudaMallocAsync((void**)&c, n * ndim * 4, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync((void*)k, keys, n * 8, cudaMemcpyHostToDevice, s));
+  }
+  decode_kernel<<<grid_for(n), 256, 0, s>>>(k, n, ndim, bits, c);
+  QSL_CHECK_CUDA(cudaGetLastError());
+  if (mem == QSL_MEM_HOST) {
+    QSL_CHECK_CUDA(cudaMemcpyAsync(coords, c, n * ndim * 4, cudaMemcpyDeviceToHost, s));
+    QSL_CHECK_CUDA(cudaFreeAsync((void*)k, s));
+    QSL_CHECK_CUDA(cudaFreeAsync(c, s));
+    QSL_CHECK_CUDA(cudaStreamSynchronize(s));
+  }
+  return QSL_OK;
+}
+
+int qsl_convert(const uint64_t* keys, const float* vals, int64_t n, int ndim, int max_order, const int32_t* extent,
+                int out_order, int log_interp, float* out, int mem, void* stream_) {
+  cudaStream_t s = (cudaStream_t)stream_;
+  if ((ndim != 2 && ndim != 3) || max_order < 0 || ndim * max_order > 63 || out_order < 0 ||
+      out_order > max_order || n < 0 || !extent || !out || (n > 0 && (!keys || !vals))) {
+    set_error("bad converter arguments");
+    return QSL_EINVAL;
+  }
+  int d = max_order - out_order;
+  int64_t N = 1;
+  for (int a = 0; a < ndim; ++a) {
+    if (extent[a] < 1 || extent[a] > (1 << max_order) || (extent[a] & ((1 << d) - 1))) {
+      set_error("extent[%d] must be in 1..2^max_order and a multiple of 2^(max_order-out_order)", a);
+      return QSL_EINVAL;
+    }
+    N *= extent[a] >> d;
+  }
+  if (mem == QSL_MEM_DEVICE) return convert_device(keys, vals, n, ndim, max_order, extent, out_order, log_interp, out, s);
+  uint64_t* k = nullptr;
+  float *v = nullptr, *o = nullptr;
+  QSL_CHECK_CUDA(cudaMallocAsync((void**)&k, n * 8 + 8, s));
+  QSL_CHECK_CUDA(cudaMallocAsync((void**)&v, n * 4 + 4, s));
+  QSL_CHECK_CUDA(cudaMallocAsync((void**)&o, N * 4, s));
+  if (n) {
+    QSL_CHECK_CUDA(cudaMemcpyAsync(k, keys, n * 8, cudaMemcpyHostToDevice, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync(v, vals, n * 4, cudaMemcpyHostToDevice, s));
+  }
+  int rc = convert_device(k, v, n, ndim, max_order, extent, out_order, log_interp, o, s);
+  if (rc) return rc;
+  QSL_CHECK_CUDA(cudaMemcpyAsync(out, o, N * 4, cudaMemcpyDeviceToHost, s));
+  QSL_CHECK_CUDA(cudaFreeAsync(k, s));
+  QSL_CHECK_CUDA(cudaFreeAsync(v, s));
+  QSL_CHECK_CUDA(cudaFreeAsync(o, s));
+  QSL_CHECK_CUDA(cudaStreamSynchronize(s));
+  return QSL_OK;
+}
+
+int qsl_refine(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o, qsl_samples* smp, float* q_grid,
+               float* l_grid, int mem, void* stream_) {
+  cudaStream_t s = (cudaStream_t)stream_;
+  if (!f || !sp || !o || !smp) {
+    set_error("NULL argument");
+    return QSL_EINVAL;
+  }
+  if (sp->ndim != 2 && sp->ndim != 3) {
+    set_error("ndim must be 2 or 3");
+    return QSL_EINVAL;
+  }
+  int nd = sp->ndim, p = sp->max_order, p0 = sp->coarse_order;
+  if (p0 < 0 || p < p0 || nd * (p + 1) > 63 || p > 30) {
+    set_error("need 0 <= coarse_order <= max_order and ndim * (max_order + 1) <= 63");
+    return QSL_EINVAL;
+  }
+  int R = 1 << (p - p0);
+  for (int a = 0; a < nd; ++a) {
+    int e = sp->extent[a] > 0 ? sp->extent[a] : (1 << p);
+    if (e > (1 << p) || e % R) {
+      set_error("extent[%d] = %d must be <= 2^max_order and a multiple of 2^(max_order - coarse_order)", a, e);
+      return QSL_EINVAL;
+    }
+  }
+  int oo = sp->out_order > 0 ? sp->out_order : p;
+  if (oo > p) {
+    set_error("out_order above max_order");
+    return QSL_EINVAL;
+  }
+  if (smp->capacity < 1 || smp->count < 0 || smp->count > smp->capacity || !smp->key || !smp->q || !smp->length) {
+    set_error("bad samples (capacity/count/arrays)");
+    return QSL_EINVAL;
+  }
+  if (sp->max_iters < 0) {
+    set_error("max_iters must be >= 0");
+    return QSL_EINVAL;
+  }
+  if (mem == QSL_MEM_DEVICE) {
+    // faces/status are optional: give the driver scratch ones
+    qsl_samples d = *smp;
+    void* sf = nullptr;
+    void* ss = nullptr;
+    if (!d.faces) {
+      QSL_CHECK_CUDA(cudaMallocAsync(&sf, 2 * d.capacity, s));
+      d.faces = (uint8_t*)sf;
+    }
+    if (!d.status) {
+      QSL_CHECK_CUDA(cudaMallocAsync(&ss, d.capacity, s));
+      d.status = (uint8_t*)ss;
+    }
+    int rc = refine_device(f, sp, o, &d, q_grid, l_grid, QSL_MEM_DEVICE, s);
+    smp->count = d.count;
+    smp->iters = d.iters;
+    smp->traced = d.traced;
+    if (sf) cudaFreeAsync(sf, s);
+    if (ss) cudaFreeAsync(ss, s);
+    return rc;
+  }
+  if (mem != QSL_MEM_HOST) {
+    set_error("bad mem %d", mem);
+    return QSL_EINVAL;
+  }
+  int64_t cap = smp->capacity;
+  qsl_samples d = *smp;
+  QSL_CHECK_CUDA(cudaMallocAsync((void**)&d.key, cap * 8, s));
+  QSL_CHECK_CUDA(cudaMallocAsync((void**)&d.q, cap * 4, s));
+  QSL_CHECK_CUDA(cudaMallocAsync((void**)&d.length, cap * 4, s));
+  QSL_CHECK_CUDA(cudaMallocAsync((void**)&d.faces, cap * 2, s));
+  QSL_CHECK_CUDA(cudaMallocAsync((void**)&d.status, cap, s));
+  int64_t c0 = smp->count;
+  if (c0) {
+    QSL_CHECK_CUDA(cudaMemcpyAsync(d.key, smp->key, c0 * 8, cudaMemcpyHostToDevice, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync(d.q, smp->q, c0 * 4, cudaMemcpyHostToDevice, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync(d.length, smp->length, c0 * 4, cudaMemcpyHostToDevice, s));
+    if (smp->faces) QSL_CHECK_CUDA(cudaMemcpyAsync(d.faces, smp->faces, c0 * 2, cudaMemcpyHostToDevice, s));
+    else QSL_CHECK_CUDA(cudaMemsetAsync(d.faces, 255, c0 * 2, s));
+    if (smp->status) QSL_CHECK_CUDA(cudaMemcpyAsync(d.status, smp->status, c0, cudaMemcpyHostToDevice, s));
+    else QSL_CHECK_CUDA(cudaMemsetAsync(d.status, 0, c0, s));
+  }
+  int ext[3] = {1, 1, 1};
+  for (int a = 0; a < nd; ++a) ext[a] = sp->extent[a] > 0 ? sp->extent[a] : (1 << p);
+  int dd = p - oo;
+  int64_t N = 1;
+  for (int a = 0; a < nd; ++a) N *= ext[a] >> dd;
+  float *qg = nullptr, *lg = nullptr;
+  if (q_grid) QSL_CHECK_CUDA(cudaMallocAsync((void**)&qg, N * 4, s));
+  if (l_grid) QSL_CHECK_CUDA(cudaMallocAsync((void**)&lg, N * 4, s));
+  int rc = refine_device(f, sp, o, &d, qg, lg, QSL_MEM_HOST, s);
+  if (rc == QSL_OK || rc == QSL_ECAPACITY) {
+    int64_t n = d.count;
+    if (n) {
+      QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, d.key, n * 8, cudaMemcpyDeviceToHost, s));
+      QSL_CHECK_CUDA(cudaMemcpyAsync(smp->q, d.q, n * 4, cudaMemcpyDeviceToHost, s));
+      QSL_CHECK_CUDA(cudaMemcpyAsync(smp->length, d.length, n * 4, cudaMemcpyDeviceToHost, s));
+      if (smp->faces) QSL_CHECK_CUDA(cudaMemcpyAsync(smp->faces, d.faces, n * 2, cudaMemcpyDeviceToHost, s));
+      if (smp->status) QSL_CHECK_CUDA(cudaMemcpyAsync(smp->status, d.status, n, cudaMemcpyDeviceToHost, s));
+    }
+    if (qg) QSL_CHECK_CUDA(cudaMemcpyAsync(q_grid, qg, N * 4, cudaMemcpyDeviceToHost, s));
+    if (lg) QSL_CHECK_CUDA(cudaMemcpyAsync(l_grid, lg, N * 4, cudaMemcpyDeviceToHost, s));
+    smp->count = d.count;
+    smp->iters = d.iters;
+    smp->traced = d.traced;
+  }
+  cudaFreeAsync(d.key, s);
+  cudaFreeAsync(d.q, s);
+  cudaFreeAsync(d.length, s);
+  cudaFreeAsync(d.faces, s);
+  cudaFreeAsync(d.status, s);
+  if (qg) cudaFreeAsync(qg, s);
+  if (lg) cudaFreeAsync(lg, s);
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,1035 @@
+// Field-line and tangent-space tracer (Sec. "Algorithm" of arXiv:1609.00724)
+// for sm_103a.
+//
+// Work unit = one direction of one seed (unit 2j: forward to lambda_F, unit
+// 2j+1: backward to lambda_B), so the two halves of a line are load-balanced
+// independently. Each warp is persistent: its 32 lanes trace 32 units, and
+// lanes whose unit ends take the next units from a global queue (one atomic
+// per warp refill), so uneven line lengths do not idle the warp. Every loop
+// iteration performs exactly one Cash-Karp step evaluation (6 interpolations
+// of B and grad B) per busy lane; accepting/rejecting, face landing and
+// queue refill are per-lane bookkeeping around that common step.
+//
+// The field is a packed float4 (double4 for FP64) vertex array read through
+// the read-only cache; consecutive units are spatially adjacent seeds, so the
+// lanes of a warp start on neighbouring cells.
+//
+// After the trace, one thread per seed reads both ends and assembles Q in
+// FP64 (Eq. finalQ and its footpoint/determinant forms).
+#include <cstdio>
+#include <type_traits>
+
+#include "hilbert_dev.cuh"
+#include "qsl_internal.cuh"
+
+namespace qsl {
+namespace {
+
+constexpr int NO_FACE = 255;
+constexpr int ST_RUNNING = -1;
+
+// Cash & Karp (1990) embedded 5(4) coefficients (the stepper of Sec.
+// "Integration methods").
+constexpr double A21 = 1.0 / 5.0;
+constexpr double A31 = 3.0 / 40.0, A32 = 9.0 / 40.0;
+constexpr double A41 = 3.0 / 10.0, A42 = -9.0 / 10.0, A43 = 6.0 / 5.0;
+constexpr double A51 = -11.0 / 54.0, A52 = 5.0 / 2.0, A53 = -70.0 / 27.0, A54 = 35.0 / 27.0;
+constexpr double A61 = 1631.0 / 55296.0, A62 = 175.0 / 512.0, A63 = 575.0 / 13824.0, A64 = 44275.0 / 110592.0,
+                 A65 = 253.0 / 4096.0;
+constexpr double B1 = 37.0 / 378.0, B3 = 250.0 / 621.0, B4 = 125.0 / 594.0, B6 = 512.0 / 1771.0;
+constexpr double E1 = 37.0 / 378.0 - 2825.0 / 27648.0, E3 = 250.0 / 621.0 - 18575.0 / 48384.0,
+                 E4 = 125.0 / 594.0 - 13525.0 / 55296.0, E5 = -277.0 / 14336.0, E6 = 512.0 / 1771.0 - 0.25;
+
+__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ double4_32a ldg4(const double4_32a* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  double2 a = __ldg(q), b = __ldg(q + 1);
+  double4_32a r;
+  r.x = a.x;
+  r.y = a.y;
+  r.z = b.x;
+  r.w = b.y;
+  return r;
+}
+
+// ------------------------------------------------------------ interpolation
+template <class R>
+struct Interp {
+  R b[3];     // interpolated rhs of Eq. fl
+  R g[3][3];  // g[i][j] = d b_i / d x_j (Eq. dev)
+  R m;        // |B|
+};
+
+template <class R>
+__device__ __forceinline__ void locate_uniform(R x, R org, R inv_h, int n, int& i, R& u) {
+  R f = (x - org) * inv_h;
+  R fc = fmin(fmax(f, R(0)), R(n - 2));
+  i = (int)floor(fc);
+  if (i > n - 2) i = n - 2;
+  u = f - R(i);
+}
+
+template <class R, class S>
+__device__ __forceinline__ void locate_axis(const S* __restrict__ c, R x, int n, int& i, R& u, R& inv_h) {
+  if (!(x > R(c[0]))) {
+    i = 0;
+  } else if (x >= R(c[n - 1])) {
+    i = n - 2;
+  } else {
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (R(c[mid]) <= x) lo = mid; else hi = mid;
+    }
+    i = lo;
+  }
+  R c0 = R(c[i]), c1 = R(c[i + 1]);
+  inv_h = R(1) / (c1 - c0);
+  u = (x - c0) * inv_h;
+}
+
+// Fast power and division for the step-size controller (FP32 uses the
+// hardware approximations; the controller is a heuristic either way).
+__device__ __forceinline__ float cpow(float a, float e) { return __powf(a, e); }
+__device__ __forceinline__ double cpow(double a, double e) { return pow(a, e); }
+__device__ __forceinline__ float cdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double cdiv(double a, double b) { return a / b; }
+
+// One component of the trilinear interpolant (Eq. interp with the trilinear
+// kernels) and its derivatives in the local coordinates (u, v, w).
+template <class R>
+__device__ __forceinline__ void tri1(R v000, R v100, R v010, R v110, R v001, R v101, R v011, R v111, R u, R v,
+                                     R w, R& val, R& du, R& dv, R& dw) {
+  R e00 = v100 - v000, e10 = v110 - v010, e01 = v101 - v001, e11 = v111 - v011;
+  R a00 = fma(u, e00, v000), a10 = fma(u, e10, v010), a01 = fma(u, e01, v001), a11 = fma(u, e11, v011);
+  R d0 = fma(v, e10 - e00, e00), d1 = fma(v, e11 - e01, e01);
+  du = fma(w, d1 - d0, d0);
+  R f0 = a10 - a00, f1 = a11 - a01;
+  R b0 = fma(v, f0, a00), b1 = fma(v, f1, a01);
+  dv = fma(w, f1 - f0, f0);
+  dw = b1 - b0;
+  val = fma(w, dw, b0);
+}
+
+template <class R>
+__device__ __forceinline__ R tri0(R v000, R v100, R v010, R v110, R v001, R v101, R v011, R v111, R u, R v, R w) {
+  R a00 = fma(u, v100 - v000, v000), a10 = fma(u, v110 - v010, v010), a01 = fma(u, v101 - v001, v001),
+    a11 = fma(u, v111 - v011, v011);
+  R b0 = fma(v, a10 - a00, a00), b1 = fma(v, a11 - a01, a01);
+  return fma(w, b1 - b0, b0);
+}
+
+// Interpolated b, grad b and |B| at a point. Storage type S (float/double),
+// arithmetic R. Global frame (LOC = false): (x0, x1, x2) in domain units.
+// Local frame (LOC = true, uniform grids): the point is vertex `ic` plus
+// (x0, x1, x2) in cell units, so the cell and its local coordinates come from
+// small exact numbers instead of a subtraction of nearly equal coordinates.
+template <class R, class S, bool GRAD, bool MAG, bool LOC = false>
+__device__ __forceinline__ void interp(const FieldView<S>& F, R x0, R x1, R x2, Interp<R>& I,
+                                       const int* ic = nullptr) {
+  int ci[3];
+  R uu[3], sc[3];
+  R xs[3] = {x0, x1, x2};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (LOC) {
+      R lim = R(F.n[a]);
+      R fl = floor(fmin(fmax(xs[a], -lim), lim));
+      int i = ic[a] + (int)fl;
+      i = min(max(i, 0), F.n[a] - 2);
+      uu[a] = xs[a] - R(i - ic[a]);
+      ci[a] = i;
+      sc[a] = R(F.inv_h[a]);
+    } else if (F.uniform) {
+      locate_uniform<R>(xs[a], R(F.org[a]), R(F.inv_h[a]), F.n[a], ci[a], uu[a]);
+      sc[a] = R(F.inv_h[a]);
+    } else {
+      locate_axis<R, S>(F.axis[a], xs[a], F.n[a], ci[a], uu[a], sc[a]);
+    }
+  }
+  typedef typename V4<S>::type V;
+  const size_t sy = (size_t)F.n[0], sz = (size_t)F.n[0] * (size_t)F.n[1];
+  const V* p = F.v + (size_t)ci[2] * sz + (size_t)ci[1] * sy + (size_t)ci[0];
+  V q000 = ldg4(p), q100 = ldg4(p + 1), q010 = ldg4(p + sy), q110 = ldg4(p + sy + 1);
+  V q001 = ldg4(p + sz), q101 = ldg4(p + sz + 1), q011 = ldg4(p + sz + sy), q111 = ldg4(p + sz + sy + 1);
+  R u = uu[0], v = uu[1], w = uu[2];
+  R val[3], d[3][3];
+#define QSL_TRI(C, K)                                                                                    \
+  if (GRAD) {                                                                                            \
+    tri1<R>(R(q000.C), R(q100.C), R(q010.C), R(q110.C), R(q001.C), R(q101.C), R(q011.C), R(q111.C), u, v, \
+            w, val[K], d[K][0], d[K][1], d[K][2]);                                                       \
+  } else {                                                                                               \
+    val[K] = tri0<R>(R(q000.C), R(q100.C), R(q010.C), R(q110.C), R(q001.C), R(q101.C), R(q011.C),        \
+                     R(q111.C), u, v, w);                                                                \
+  }
+  QSL_TRI(x, 0)
+  QSL_TRI(y, 1)
+  QSL_TRI(z, 2)
+#undef QSL_TRI
+  if (MAG || F.raw) {
+    I.m = tri0<R>(R(q000.w), R(q100.w), R(q010.w), R(q110.w), R(q001.w), R(q101.w), R(q011.w), R(q111.w), u,
+                  v, w);
+  }
+  if (GRAD) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) d[i][j] *= sc[j];
+  }
+  if (!F.raw) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      I.b[i] = val[i];
+      if (GRAD)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) I.g[i][j] = d[i][j];
+    }
+  } else {
+    // interpolate B, normalise at the point: b = B/|B|,
+    // d b_i/d x_j = (dB_i/dx_j - b_i sum_k b_k dB_k/dx_j)/|B|
+    R m2 = val[0] * val[0] + val[1] * val[1] + val[2] * val[2];
+    R m = sqrt(m2);
+    if (MAG) I.m = m;
+    R rm = (m > R(0)) ? R(1) / m : R(0);
+    R bh[3] = {val[0] * rm, val[1] * rm, val[2] * rm};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) I.b[i] = bh[i];
+    if (GRAD) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        R t = bh[0] * d[0][j] + bh[1] * d[1][j] + bh[2] * d[2][j];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) I.g[i][j] = (d[i][j] - bh[i] * t) * rm;
+      }
+    }
+  }
+}
+
+template <class R, class S, int NC, bool LOC>
+__device__ __forceinline__ void rhs(const FieldView<S>& F, const R* y, R* k, const int* ic) {
+  Interp<R> I;
+  interp<R, S, NC == 9, false, LOC>(F, y[0], y[1], y[2], I, ic);
+  if (LOC) {
+    k[0] = I.b[0] * R(F.inv_h[0]);
+    k[1] = I.b[1] * R(F.inv_h[1]);
+    k[2] = I.b[2] * R(F.inv_h[2]);
+  } else {
+    k[0] = I.b[0];
+    k[1] = I.b[1];
+    k[2] = I.b[2];
+  }
+  if (NC == 9) {
+#pragma unroll
+    for (int v = 0; v < 2; ++v)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        k[3 + 3 * v + i] = I.g[i][0] * y[3 + 3 * v] + I.g[i][1] * y[4 + 3 * v] + I.g[i][2] * y[5 + 3 * v];
+  }
+}
+
+// One Cash-Karp step of signed size hh from y: the 5th-order increment dy
+// (y_new = y + dy) and the embedded error estimate yerr.
+template <class R, class S, int NC, bool LOC>
+__device__ __forceinline__ void ck_step(const FieldView<S>& F, const R* y, R hh, R* dy, R* yerr, const int* ic) {
+  R k1[NC], k2[NC], k3[NC], k4[NC], k5[NC], k6[NC], t[NC];
+  rhs<R, S, NC, LOC>(F, y, k1, ic);
+#pragma unroll
+  for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(A21) * k1[i], y[i]);
+  rhs<R, S, NC, LOC>(F, t, k2, ic);
+#pragma unroll
+  for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(A31) * k1[i] + R(A32) * k2[i], y[i]);
+  rhs<R, S, NC, LOC>(F, t, k3, ic);
+#pragma unroll
+  for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(A41) * k1[i] + R(A42) * k2[i] + R(A43) * k3[i], y[i]);
+  rhs<R, S, NC, LOC>(F, t, k4, ic);
+#pragma unroll
+  for (int i = 0; i < NC; ++i)
+    t[i] = fma(hh, R(A51) * k1[i] + R(A52) * k2[i] + R(A53) * k3[i] + R(A54) * k4[i], y[i]);
+  rhs<R, S, NC, LOC>(F, t, k5, ic);
+#pragma unroll
+  for (int i = 0; i < NC; ++i)
+    t[i] = fma(hh, R(A61) * k1[i] + R(A62) * k2[i] + R(A63) * k3[i] + R(A64) * k4[i] + R(A65) * k5[i], y[i]);
+  rhs<R, S, NC, LOC>(F, t, k6, ic);
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    dy[i] = hh * (R(B1) * k1[i] + R(B3) * k3[i] + R(B4) * k4[i] + R(B6) * k6[i]);
+    yerr[i] = hh * (R(E1) * k1[i] + R(E3) * k3[i] + R(E4) * k4[i] + R(E5) * k5[i] + R(E6) * k6[i]);
+  }
+}
+
+template <class R, class S, int NC, bool LOC>
+__device__ __forceinline__ void euler_step(const FieldView<S>& F, const R* y, R hh, R* dy, R* yerr,
+                                           const int* ic) {
+  R k[NC];
+  rhs<R, S, NC, LOC>(F, y, k, ic);
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    dy[i] = hh * k[i];
+    yerr[i] = R(0);
+  }
+}
+
+// ------------------------------------------------------------ seeds
+__device__ __forceinline__ void seed_position(const SeedSource& s, int64_t g, double* x) {
+  switch (s.kind) {
+    case SEEDS_ARRAY:
+      x[0] = s.xyz[3 * g];
+      x[1] = s.xyz[3 * g + 1];
+      x[2] = s.xyz[3 * g + 2];
+      break;
+    case SEEDS_PLANE: {
+      int64_t i = g % s.n[0], j = g / s.n[0];
+      double a = (i + 0.5) / s.n[0] - 0.5, b = (j + 0.5) / s.n[1] - 0.5;
+      for (int k = 0; k < 3; ++k) x[k] = s.c[k] + a * s.u[k] + b * s.v[k];
+      break;
+    }
+    case SEEDS_VOLUME: {
+      int64_t i = g % s.n[0], r = g / s.n[0];
+      int64_t j = r % s.n[1], k = r / s.n[1];
+      int64_t id[3] = {i, j, k};
+      for (int a = 0; a < 3; ++a) x[a] = s.c[a] + (id[a] + 0.5) / s.n[a] * (s.u[a] - s.c[a]);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+__device__ __forceinline__ void seed_of(const SeedSource& s, int64_t j, int64_t* g, double* x) {
+  int64_t gi = s.index ? s.index[j] : j;
+  *g = gi;
+  if (s.kind == SEEDS_KEYS2 || s.kind == SEEDS_KEYS3) {
+    int nd = (s.kind == SEEDS_KEYS2) ? 2 : 3;
+    uint32_t c[3] = {0, 0, 0};
+    hilbert_coords_dev(s.keys[gi], nd, s.bits, c);
+    if (nd == 2) {
+      double a = (c[0] + 0.5) / s.n[0] - 0.5, b = (c[1] + 0.5) / s.n[1] - 0.5;
+      for (int k = 0; k < 3; ++k) x[k] = s.c[k] + a * s.u[k] + b * s.v[k];
+    } else {
+      for (int a = 0; a < 3; ++a) x[a] = s.c[a] + (c[a] + 0.5) / s.n[a] * (s.u[a] - s.c[a]);
+    }
+    return;
+  }
+  seed_position(s, gi, x);
+}
+
+// ------------------------------------------------------------ tracer kernel
+template <class R>
+struct EndRec {
+  R x[3], d1[3], d2[3];
+  R mu;
+  int32_t face, status, steps, pad;
+};
+
+template <class R>
+struct TraceParams {
+  FieldView<R> F;
+  SeedSource src;
+  int64_t n_units;             // 2 x seeds
+  const int64_t* n_seeds_dev;  // optional device count of seeds
+  EndRec<R>* ends;
+  unsigned long long* head;
+  DeviceStats* stats;
+  R lo[3], hi[3];              // domain bounds: domain units (global frame) or grid-index units (local frame)
+  double lo_d[3], hi_d[3];     // domain bounds in domain units
+  R max_len, tol_abs, tol_rel, h_init, h_max, h_min, euler_h, land_tol;
+  long long max_steps;
+  int euler;
+  int refill_min;
+  unsigned long long timeout_ns;  // per-warp watchdog, 0 = none
+  int* timeout_flag;
+};
+
+// Outward signed distance of the point from face f: global frame, x in domain
+// units; local frame, the point is vertex ic + x in cell units and lo/hi are
+// grid-index coordinates (bound - ic is exact for grid-aligned domains).
+// The distance is evaluated in "delta form" for the point y + d:
+// (bound - y) - d, where bound - y is exact near the face, so its precision
+// follows the step increment d rather than the coordinate (this keeps the
+// landed lambda accurate for lines that graze the face).
+template <class R, bool LOC>
+__device__ __forceinline__ R face_g(const R* lo, const R* hi, const int* ic, int f, const R* y, const R* d) {
+  int a = f >> 1;
+  R bound = (f & 1) ? hi[a] : lo[a];
+  if (LOC) bound -= R(ic[a]);
+  R r = bound - y[a];
+  R dd = d ? d[a] : R(0);
+  return (f & 1) ? (dd - r) : (r - dd);
+}
+
+// Exit face along the chord y -> y + d: the smallest crossing fraction,
+// lowest face id on ties.
+template <class R, bool LOC>
+__device__ __forceinline__ int chord_face(const R* lo, const R* hi, const int* ic, const R* y, const R* d) {
+  int face = -1;
+  R tb = R(0);
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    R g1 = face_g<R, LOC>(lo, hi, ic, f, y, d);
+    if (g1 > R(0)) {
+      R g0 = face_g<R, LOC>(lo, hi, ic, f, y, (const R*)nullptr);
+      R t = g0 / (g0 - g1);
+      if (face < 0 || t < tb) {
+        face = f;
+        tb = t;
+      }
+    }
+  }
+  return face < 0 ? 0 : face;
+}
+
+template <class R>
+__device__ __forceinline__ R eps_of();
+template <>
+__device__ __forceinline__ float eps_of<float>() { return 1.1920928955078125e-07f; }
+template <>
+__device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <class R, int NC, bool LOC>
+__device__ __forceinline__ void write_end(const TraceParams<R>& P, int64_t unit, const R* y, const int* ic, R mu,
+                                          int face, int status, int steps) {
+  EndRec<R>& e = P.ends[unit];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (LOC)
+      e.x[a] = (R)((double)P.F.org[a] + ((double)ic[a] + (double)y[a]) / (double)P.F.inv_h[a]);
+    else
+      e.x[a] = y[a];
+  }
+  if (status == QSL_LINE_OK && face != NO_FACE) {
+    int a = face >> 1;
+    e.x[a] = (R)((face & 1) ? P.hi_d[a] : P.lo_d[a]);  // exactly on the face
+  }
+  if (NC == 9)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      e.d1[i] = y[3 + i];
+      e.d2[i] = y[6 + i];
+    }
+  e.mu = mu;
+  e.face = (status == QSL_LINE_OK) ? face : NO_FACE;
+  e.status = status;
+  e.steps = steps;
+}
+
+template <class R, int NC, bool LOC>
+__global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  int64_t total = P.n_units;
+  if (P.n_seeds_dev) {
+    int64_t c = 2 * (*P.n_seeds_dev);
+    total = c < total ? c : total;
+  }
+  const FieldView<R>& F = P.F;
+
+  bool active = false;
+  bool exhausted = false;  // warp-uniform
+  int64_t unit = 0;
+  R y[NC];
+  int ic[3] = {0, 0, 0};   // reference vertex of the local frame
+  R mu = 0, muc = 0, h = 0, sgn = 1;
+  int steps = 0, phase = 0;
+  bool capped = false;
+  // face landing state
+  R la = 0, lb = 0, lga = 0, lgb = 0, lhm = 0, yh[3] = {0, 0, 0};
+  int lface = 0, lside = 0, lit = 0, lround = 0;
+  unsigned long long c_stage = 0, c_acc = 0, c_rej = 0, c_land = 0, c_lines = 0;
+  int iter = 0;
+  bool timed_out = false;
+  const unsigned long long t_start = P.timeout_ns ? globaltimer() : 0ull;
+
+  for (;;) {
+    // ---- refill idle lanes from the global queue (one atomic per warp)
+    if (!exhausted) {
+      unsigned need = __ballot_sync(FULL, !active);
+      int nneed = __popc(need);
+      if (nneed > 0 && (nneed >= P.refill_min || need == FULL)) {
+        int leader = __ffs(need) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(P.head, (unsigned long long)nneed);
+        base = __shfl_sync(FULL, base, leader);
+        if ((int64_t)(base + nneed) >= total) exhausted = true;
+        if (!active) {
+          int64_t myu = (int64_t)base + __popc(need & lt_mask);
+          if (myu < total) {
+            unit = myu;
+            active = true;
+            c_lines += (myu & 1) == 0;
+            // ---- initialise this unit
+            int64_t g;
+            double xd[3];
+            seed_of(P.src, unit >> 1, &g, xd);
+            sgn = (unit & 1) ? R(-1) : R(1);
+            if (LOC) {
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                double fa = (xd[a] - (double)F.org[a]) * (double)F.inv_h[a];
+                double fl = floor(fmin(fmax(fa, 0.0), (double)(F.n[a] - 2)));
+                ic[a] = (int)fl;
+                y[a] = (R)(fa - fl);
+              }
+            } else {
+              y[0] = R(xd[0]);
+              y[1] = R(xd[1]);
+              y[2] = R(xd[2]);
+            }
+            mu = 0;
+            muc = 0;
+            steps = 0;
+            phase = 0;
+            lface = NO_FACE;
+            int status = ST_RUNNING;
+            bool outside = false;
+#pragma unroll
+            for (int f = 0; f < 6; ++f)
+              if (face_g<R, LOC>(P.lo, P.hi, ic, f, y, (const R*)nullptr) > R(0)) outside = true;
+            if (outside || !isfinite(xd[0]) || !isfinite(xd[1]) || !isfinite(xd[2])) {
+              status = QSL_LINE_OUTSIDE;
+            } else {
+              Interp<R> I0;
+              interp<R, R, false, false, LOC>(F, y[0], y[1], y[2], I0, ic);
+              R m0 = sqrt(I0.b[0] * I0.b[0] + I0.b[1] * I0.b[1] + I0.b[2] * I0.b[2]);
+              if (!(m0 > R(0))) {
+                status = QSL_LINE_NULL;
+              } else {
+                if (NC == 9) {
+                  // Eq. ic: a, b orthonormal and orthogonal to B(x0); reading:
+                  // e = axis of the smallest |b0| component (lowest on ties),
+                  // a = normalise(e x b0), b = b0 x a.
+                  R u0[3] = {I0.b[0] / m0, I0.b[1] / m0, I0.b[2] / m0};
+                  int ax = 0;
+                  if (fabs(u0[1]) < fabs(u0[ax])) ax = 1;
+                  if (fabs(u0[2]) < fabs(u0[ax])) ax = 2;
+                  R av[3];
+                  if (ax == 0) { av[0] = 0; av[1] = -u0[2]; av[2] = u0[1]; }
+                  else if (ax == 1) { av[0] = u0[2]; av[1] = 0; av[2] = -u0[0]; }
+                  else { av[0] = -u0[1]; av[1] = u0[0]; av[2] = 0; }
+                  R an = sqrt(av[0] * av[0] + av[1] * av[1] + av[2] * av[2]);
+                  av[0] /= an;
+                  av[1] /= an;
+                  av[2] /= an;
+                  y[3] = av[0];
+                  y[4] = av[1];
+                  y[5] = av[2];
+                  y[6] = u0[1] * av[2] - u0[2] * av[1];
+                  y[7] = u0[2] * av[0] - u0[0] * av[2];
+                  y[8] = u0[0] * av[1] - u0[1] * av[0];
+                }
+                // a seed on a face whose field points out of the domain ends
+                // this side at once with zero length
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                  if (status == ST_RUNNING && face_g<R, LOC>(P.lo, P.hi, ic, f, y, (const R*)nullptr) == R(0)) {
+                    R bn = I0.b[f >> 1] * sgn;
+                    R outw = (f & 1) ? bn : -bn;
+                    if (outw > R(0)) {
+                      status = QSL_LINE_OK;
+                      lface = f;
+                    }
+                  }
+                }
+              }
+            }
+            h = P.euler ? P.euler_h : P.h_init;
+            if (status != ST_RUNNING) {
+              write_end<R, NC, LOC>(P, unit, y, ic, R(0), lface, status, 0);
+              active = false;
+            }
+          }
+        }
+      }
+    }
+    if (!__any_sync(FULL, active)) {
+      if (exhausted) break;
+      continue;
+    }
+    // ---- device watchdog
+    if (P.timeout_ns && ((++iter & 63) == 0)) {
+      if (globaltimer() - t_start > P.timeout_ns) timed_out = true;
+    }
+    if (!active) continue;
+
+    int status = ST_RUNNING;
+    if (timed_out) status = QSL_LINE_TIMEOUT;
+    R hs = lhm;
+    if (status == ST_RUNNING && phase == 0) {
+      if (steps >= P.max_steps) status = QSL_LINE_MAXSTEPS;
+      R room = P.max_len - mu;
+      if (status == ST_RUNNING && !(room > R(0))) status = QSL_LINE_MAXLEN;
+      R hcap = P.euler ? P.euler_h : P.h_max;
+      hs = fmin(h, hcap);
+      capped = false;
+      if (room <= hs) {
+        hs = room;
+        capped = true;
+      }
+    }
+    if (status == ST_RUNNING) {
+      R dy[NC], yerr[NC];
+      if (P.euler) {
+        euler_step<R, R, NC, LOC>(F, y, sgn * hs, dy, yerr, ic);
+        c_stage += 1;
+      } else {
+        ck_step<R, R, NC, LOC>(F, y, sgn * hs, dy, yerr, ic);
+        c_stage += 6;
+      }
+      steps += 1;
+      if (phase == 0) {
+        R err = 0;
+        bool finite = true;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+          R yn = y[i] + dy[i];
+          if (!isfinite(yn)) finite = false;
+          R e = fabs(yerr[i]), ya = fabs(y[i]), yb = fabs(yn);
+          if (LOC && i < 3) {
+            // position error in domain units, scaled by |x| in domain units
+            R hh = R(1) / R(F.inv_h[i]);
+            R base = R(F.org[i]) + R(ic[i]) * hh;
+            e *= hh;
+            ya = fabs(base + y[i] * hh);
+            yb = fabs(base + yn * hh);
+          }
+          R sc = P.tol_abs + P.tol_rel * fmax(ya, yb);
+          err = fmax(err, cdiv(e, sc));
+        }
+        if (!finite) {
+          status = QSL_LINE_NONFINITE;
+        } else if (!P.euler && err > R(1)) {
+          c_rej += 1;
+          h = hs * fmax(R(0.2), R(0.9) * cpow(err, R(-0.25)));
+          if (h < P.h_min) status = QSL_LINE_STALL;
+        } else {
+          c_acc += 1;
+          bool inside = true;
+#pragma unroll
+          for (int f = 0; f < 6; ++f)
+            if (face_g<R, LOC>(P.lo, P.hi, ic, f, y, dy) > R(0)) inside = false;
+          if (inside) {
+#pragma unroll
+            for (int i = 0; i < NC; ++i) y[i] += dy[i];
+            if (LOC) {
+              // move the reference vertex with the line (exact shifts)
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                R fl = floor(y[a]);
+                int ni = min(max(ic[a] + (int)fl, 0), F.n[a] - 2);
+                y[a] -= R(ni - ic[a]);
+                ic[a] = ni;
+              }
+            }
+            R t1 = hs - muc, t2 = mu + t1;  // compensated sum of the step lengths
+            muc = (t2 - mu) - t1;
+            mu = t2;
+            if (capped) status = QSL_LINE_MAXLEN;
+            else if (!P.euler) h = hs * ((err == R(0)) ? R(5) : fmin(R(5), R(0.9) * cpow(err, R(-0.2))));
+          } else {
+            // leave the domain: land exactly on the exit face
+            phase = 1;
+            yh[0] = dy[0];
+            yh[1] = dy[1];
+            yh[2] = dy[2];
+            lface = chord_face<R, LOC>(P.lo, P.hi, ic, y, yh);
+            la = 0;
+            lb = hs;
+            lga = face_g<R, LOC>(P.lo, P.hi, ic, lface, y, (const R*)nullptr);
+            lgb = face_g<R, LOC>(P.lo, P.hi, ic, lface, y, yh);
+            lside = 0;
+            lit = 0;
+            lround = 0;
+            lhm = la + (lb - la) * lga / (lga - lgb);
+          }
+        }
+      } else {
+        c_land += 1;
+        lit += 1;
+        R gm = face_g<R, LOC>(P.lo, P.hi, ic, lface, y, dy);
+        // converged when within the landing tolerance or at the resolution of
+        // the step increment along the face normal
+        R dn = fabs(lface >> 1 == 0 ? dy[0] : (lface >> 1 == 1 ? dy[1] : dy[2]));
+        R gtol = fmax(P.land_tol, R(4) * eps_of<R>() * dn);
+        if (fabs(gm) <= gtol || lit >= 60 || !isfinite(gm) || !(lb - la > eps_of<R>() * lb)) {
+          R worst = R(-1);
+#pragma unroll
+          for (int f = 0; f < 6; ++f)
+            if (f != lface) worst = fmax(worst, face_g<R, LOC>(P.lo, P.hi, ic, f, y, dy));
+          if (worst > gtol && lround < 8) {
+            // the landed point is outside another face: that face was crossed first
+            lround += 1;
+            yh[0] = dy[0];
+            yh[1] = dy[1];
+            yh[2] = dy[2];
+            R hi_h = lhm;
+            lface = chord_face<R, LOC>(P.lo, P.hi, ic, y, yh);
+            la = 0;
+            lb = hi_h;
+            lga = face_g<R, LOC>(P.lo, P.hi, ic, lface, y, (const R*)nullptr);
+            lgb = face_g<R, LOC>(P.lo, P.hi, ic, lface, y, yh);
+            lside = 0;
+            lit = 0;
+            lhm = la + (lb - la) * lga / (lga - lgb);
+          } else {
+#pragma unroll
+            for (int i = 0; i < NC; ++i) y[i] += dy[i];
+            R t1 = lhm - muc, t2 = mu + t1;
+            muc = (t2 - mu) - t1;
+            mu = t2;
+            status = QSL_LINE_OK;
+          }
+        } else {
+          if (gm > R(0)) {
+            lb = lhm;
+            lgb = gm;
+            if (lside == 1) lga *= R(0.5);
+            lside = 1;
+          } else {
+            la = lhm;
+            lga = gm;
+            if (lside == -1) lgb *= R(0.5);
+            lside = -1;
+          }
+          lhm = la + (lb - la) * lga / (lga - lgb);
+        }
+      }
+    }
+    if (status != ST_RUNNING) {
+      write_end<R, NC, LOC>(P, unit, y, ic, mu, lface, status, steps);
+      active = false;
+    }
+  }
+  // ---- statistics: one atomic per warp and counter
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c_stage += __shfl_down_sync(FULL, c_stage, o);
+    c_acc += __shfl_down_sync(FULL, c_acc, o);
+    c_rej += __shfl_down_sync(FULL, c_rej, o);
+    c_land += __shfl_down_sync(FULL, c_land, o);
+    c_lines += __shfl_down_sync(FULL, c_lines, o);
+  }
+  unsigned any_to = __ballot_sync(FULL, timed_out);
+  if (lane == 0 && P.stats) {
+    atomicAdd(&P.stats->stage_evals, c_stage);
+    atomicAdd(&P.stats->accepted, c_acc);
+    atomicAdd(&P.stats->rejected, c_rej);
+    atomicAdd(&P.stats->landing, c_land);
+    atomicAdd(&P.stats->lines, c_lines);
+    if (any_to) atomicAdd(&P.stats->timeouts, 1ull);
+  }
+  if (lane == 0 && any_to && P.timeout_flag) atomicExch(P.timeout_flag, 1);
+}
+
+// ------------------------------------------------------------ assembly (FP64)
+__device__ __forceinline__ double dot3(const double* a, const double* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+struct EndTerms {
+  double bmag, A, B, C, cross, Af, Bf, Cf, bn;
+  bool foot_ok;
+};
+
+template <class S>
+__device__ void end_terms(const FieldView<S>& F, const double* x, const double* d1, const double* d2, int face,
+                          bool have_face, EndTerms& r) {
+  Interp<double> I;
+  interp<double, S, false, true>(F, x[0], x[1], x[2], I);
+  r.bmag = I.m;
+  double m = sqrt(dot3(I.b, I.b));
+  double u[3] = {I.b[0] / m, I.b[1] / m, I.b[2] / m};
+  // Sec. "Squashing factor calculation": dx_perp = dx - b (b.dx), b normalised
+  double ud1 = dot3(u, d1), ud2 = dot3(u, d2);
+  double ap[3], bp[3];
+  for (int i = 0; i < 3; ++i) {
+    ap[i] = d1[i] - u[i] * ud1;
+    bp[i] = d2[i] - u[i] * ud2;
+  }
+  r.A = dot3(ap, ap);
+  r.B = dot3(bp, bp);
+  r.C = dot3(ap, bp);
+  double cr[3] = {ap[1] * bp[2] - ap[2] * bp[1], ap[2] * bp[0] - ap[0] * bp[2], ap[0] * bp[1] - ap[1] * bp[0]};
+  r.cross = sqrt(dot3(cr, cr));
+  r.foot_ok = false;
+  r.Af = r.Bf = r.Cf = r.bn = __longlong_as_double(0x7ff8000000000000ll);
+  if (have_face && face != NO_FACE) {
+    int a = face >> 1;
+    if (u[a] != 0.0) {
+      double af[3], bf[3];
+      for (int i = 0; i < 3; ++i) {
+        af[i] = d1[i] - u[i] * (d1[a] / u[a]);
+        bf[i] = d2[i] - u[i] * (d2[a] / u[a]);
+      }
+      r.Af = dot3(af, af);
+      r.Bf = dot3(bf, bf);
+      r.Cf = dot3(af, bf);
+      r.bn = I.m * fabs(u[a]);
+      r.foot_ok = true;
+    }
+  }
+}
+
+template <class R, class S>
+struct AssembleParams {
+  FieldView<S> F;
+  SeedSource src;
+  int64_t n_seeds;
+  const int64_t* n_seeds_dev;
+  const EndRec<R>* ends;
+  LineOutputs out;
+  int tangent;
+};
+
+template <class R, class S>
+__global__ void __launch_bounds__(128) assemble_kernel(const AssembleParams<R, S> P) {
+  int64_t n = P.n_seeds;
+  if (P.n_seeds_dev) n = min(n, *P.n_seeds_dev);
+  const double NaN = __longlong_as_double(0x7ff8000000000000ll);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    int64_t g;
+    double x0[3];
+    seed_of(P.src, j, &g, x0);
+    const EndRec<R>& ef = P.ends[2 * j];
+    const EndRec<R>& eb = P.ends[2 * j + 1];
+    double q_perp = NaN, q_foot = NaN, q_det = NaN, b0 = NaN, bf = NaN, bb = NaN, ff = NaN, fb = NaN;
+    int sf = ef.status, sb = eb.status;
+    double L = NaN;
+    if (sf != QSL_LINE_OUTSIDE) L = (double)ef.mu + (double)eb.mu;
+    if (sf != QSL_LINE_OUTSIDE && sf != QSL_LINE_NULL) {
+      Interp<double> I0;
+      interp<double, S, false, true>(P.F, x0[0], x0[1], x0[2], I0);
+      b0 = I0.m;
+    }
+    bool okf = (sf == QSL_LINE_OK || sf == QSL_LINE_MAXLEN);
+    bool okb = (sb == QSL_LINE_OK || sb == QSL_LINE_MAXLEN);
+    bool open = !(sf == QSL_LINE_OK && sb == QSL_LINE_OK && ef.face == 4 && eb.face == 4);
+    if (P.tangent && okf && okb) {
+      double xf[3], xb[3], d1f[3], d2f[3], d1b[3], d2b[3];
+      for (int i = 0; i < 3; ++i) {
+        xf[i] = ef.x[i];
+        xb[i] = eb.x[i];
+        d1f[i] = ef.d1[i];
+        d2f[i] = ef.d2[i];
+        d1b[i] = eb.d1[i];
+        d2b[i] = eb.d2[i];
+      }
+      EndTerms tf, tb;
+      end_terms<S>(P.F, xf, d1f, d2f, ef.face, sf == QSL_LINE_OK, tf);
+      end_terms<S>(P.F, xb, d1b, d2b, eb.face, sb == QSL_LINE_OK, tb);
+      bf = tf.bmag;
+      bb = tb.bmag;
+      double br = tf.A * tb.B + tb.A * tf.B - 2.0 * tb.C * tf.C;
+      q_perp = bf * bb / (b0 * b0) * br;  // Eq. finalQ
+      q_det = br / sqrt((tf.A * tf.B - tf.C * tf.C) * (tb.A * tb.B - tb.C * tb.C));
+      ff = bf / b0 * tf.cross - 1.0;
+      fb = bb / b0 * tb.cross - 1.0;
+      if (tf.foot_ok && tb.foot_ok) {
+        double brf = tf.Af * tb.Bf + tb.Af * tf.Bf - 2.0 * tb.Cf * tf.Cf;
+        q_foot = tf.bn * tb.bn / (b0 * b0) * brf;
+      }
+      if (P.out.skip_open && open) q_perp = q_foot = q_det = NaN;
+    }
+    uint8_t flags = (P.out.skip_open && open && P.tangent && okf && okb) ? QSL_FLAG_OPEN_SKIPPED : 0;
+    if (P.out.retraced) flags |= QSL_FLAG_RETRACED;
+    if (P.out.lines) {
+      qsl_line& o = P.out.lines[g];
+      o.q_perp = q_perp;
+      o.q_foot = q_foot;
+      o.q_det = q_det;
+      o.b0 = b0;
+      o.bf = bf;
+      o.bb = bb;
+      o.flux_f = ff;
+      o.flux_b = fb;
+      o.length = (float)L;
+      o.lam_f = (float)ef.mu;
+      o.lam_b = -(float)eb.mu;
+      o.pad0 = 0;
+      for (int i = 0; i < 3; ++i) {
+        o.x_f[i] = (float)ef.x[i];
+        o.x_b[i] = (float)eb.x[i];
+      }
+      o.steps = ef.steps + eb.steps;
+      o.face_f = (uint8_t)ef.face;
+      o.face_b = (uint8_t)eb.face;
+      o.status_f = (uint8_t)sf;
+      o.status_b = (uint8_t)sb;
+    }
+    double qsel = (P.out.q_form == QSL_Q_FOOT) ? q_foot : (P.out.q_form == QSL_Q_DET ? q_det : q_perp);
+    if (P.out.q) P.out.q[g] = (float)qsel;
+    if (P.out.length) P.out.length[g] = (float)L;
+    if (P.out.faces) {
+      P.out.faces[2 * g] = (uint8_t)ef.face;
+      P.out.faces[2 * g + 1] = (uint8_t)eb.face;
+    }
+    if (P.out.status) P.out.status[g] = (uint8_t)((sf & 7) | ((sb & 7) << 3) | flags);
+  }
+}
+
+// Seeds whose selected Q exceeds the threshold (or whose Q is not finite for
+// a finite length) go to the FP64 retrace list.
+__global__ void select_kernel(int64_t n, const float* q, const qsl_line* lines, int q_form, double thr,
+                              int64_t* index, int64_t* count) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    double qv;
+    if (q) {
+      qv = q[j];
+    } else {
+      qv = (q_form == QSL_Q_FOOT) ? lines[j].q_foot : (q_form == QSL_Q_DET ? lines[j].q_det : lines[j].q_perp);
+    }
+    if (qv > thr) {
+      unsigned long long k = atomicAdd((unsigned long long*)count, 1ull);
+      index[k] = j;
+    }
+  }
+}
+
+template <class R>
+FieldView<R> make_view(const qsl_field* f);
+template <>
+FieldView<float> make_view<float>(const qsl_field* f) {
+  FieldView<float> v;
+  v.v = f->v32;
+  for (int a = 0; a < 3; ++a) {
+    v.axis[a] = f->axis32[a];
+    v.org[a] = (float)f->org[a];
+    v.inv_h[a] = (float)(1.0 / f->h[a]);
+    v.n[a] = f->n[a];
+  }
+  v.uniform = f->uniform;
+  v.raw = f->mode == QSL_RAW_B;
+  return v;
+}
+template <>
+FieldView<double> make_view<double>(const qsl_field* f) {
+  FieldView<double> v;
+  v.v = f->v64;
+  for (int a = 0; a < 3; ++a) {
+    v.axis[a] = f->axis64[a];
+    v.org[a] = f->org[a];
+    v.inv_h[a] = 1.0 / f->h[a];
+    v.n[a] = f->n[a];
+  }
+  v.uniform = f->uniform;
+  v.raw = f->mode == QSL_RAW_B;
+  return v;
+}
+
+template <class R, int NC>
+int launch_trace(const qsl_field* f, const SeedSource& src, int64_t n_seeds, const int64_t* n_seeds_dev,
+                 const TraceConfig& cfg, const LaunchShape& shape, const LineOutputs& out, cudaStream_t stream,
+                 DeviceStats* stats_dev, cudaEvent_t* ev) {
+  int dev = 0, sms = 0;
+  QSL_CHECK_CUDA(cudaGetDevice(&dev));
+  QSL_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  EndRec<R>* ends = nullptr;
+  unsigned long long* head = nullptr;
+  int* tflag = nullptr;
+  size_t n_units = (size_t)(2 * n_seeds);
+  QSL_CHECK_CUDA(cudaMallocAsync((void**)&ends, sizeof(EndRec<R>) * (n_units ? n_units : 1), stream));
+  QSL_CHECK_CUDA(cudaMallocAsync((void**)&head, 16, stream));
+  QSL_CHECK_CUDA(cudaMemsetAsync(head, 0, 16, stream));
+  tflag = (int*)(head + 1);
+  TraceParams<R> P;
+  P.F = make_view<R>(f);
+  P.src = src;
+  P.n_units = 2 * n_seeds;
+  P.n_seeds_dev = n_seeds_dev;
+  P.ends = ends;
+  P.head = head;
+  P.stats = stats_dev;
+  const bool loc = f->uniform != 0;
+  for (int a = 0; a < 3; ++a) {
+    P.lo_d[a] = cfg.lo[a];
+    P.hi_d[a] = cfg.hi[a];
+    // the local frame measures positions in grid-index units
+    P.lo[a] = loc ? (R)((cfg.lo[a] - f->org[a]) / f->h[a]) : (R)cfg.lo[a];
+    P.hi[a] = loc ? (R)((cfg.hi[a] - f->org[a]) / f->h[a]) : (R)cfg.hi[a];
+  }
+  P.max_len = (R)cfg.max_len;
+  P.tol_abs = (R)cfg.tol_abs;
+  P.tol_rel = (R)cfg.tol_rel;
+  P.h_init = (R)(cfg.h_init * cfg.cell);
+  P.h_max = (R)(cfg.h_max * cfg.cell);
+  P.h_min = (R)(cfg.h_min * cfg.cell);
+  P.euler_h = (R)(cfg.euler_h * cfg.cell);
+  // landing tolerance in the frame's units (cell units of the coarsest axis
+  // in the local frame); the kernel also stops at the resolution of the step
+  double lt = loc ? cfg.land_tol / fmax(fmax(f->h[0], f->h[1]), f->h[2]) : cfg.land_tol;
+  P.land_tol = (R)lt;
+  P.max_steps = cfg.max_steps;
+  P.euler = cfg.integrator == QSL_EULER;
+  P.refill_min = shape.refill_min > 0 ? shape.refill_min : 1;
+  P.timeout_ns = cfg.timeout_ns;
+  P.timeout_flag = tflag;
+  int threads = 32 * shape.warps_per_block;
+  int blocks = sms * shape.blocks_per_sm;
+  int64_t max_warps_needed = (2 * n_seeds + 31) / 32;
+  if ((int64_t)blocks * shape.warps_per_block > max_warps_needed && !n_seeds_dev)
+    blocks = (int)((max_warps_needed + shape.warps_per_block - 1) / shape.warps_per_block);
+  if (blocks < 1) blocks = 1;
+  if (ev) QSL_CHECK_CUDA(cudaEventRecord(ev[0], stream));
+  if (n_seeds > 0) {
+    if (loc)
+      trace_kernel<R, NC, true><<<blocks, threads, 0, stream>>>(P);
+    else
+      trace_kernel<R, NC, false><<<blocks, threads, 0, stream>>>(P);
+    QSL_CHECK_CUDA(cudaGetLastError());
+  }
+  if (ev) QSL_CHECK_CUDA(cudaEventRecord(ev[1], stream));
+  // assembly
+  typedef typename std::conditional<sizeof(R) == 4, float, double>::type S;
+  AssembleParams<R, S> A;
+  A.F = make_view<S>(f);
+  A.src = src;
+  A.n_seeds = n_seeds;
+  A.n_seeds_dev = n_seeds_dev;
+  A.ends = ends;
+  A.out = out;
+  A.tangent = NC == 9;
+  if (n_seeds > 0) {
+    int ab = (int)((n_seeds + 127) / 128);
+    if (ab > sms * 16) ab = sms * 16;
+    assemble_kernel<R, S><<<ab, 128, 0, stream>>>(A);
+    QSL_CHECK_CUDA(cudaGetLastError());
+  }
+  QSL_CHECK_CUDA(cudaFreeAsync(ends, stream));
+  QSL_CHECK_CUDA(cudaFreeAsync(head, stream));
+  return QSL_OK;
+}
+
+}  // namespace
+
+int trace_and_assemble(const qsl_field* f, const SeedSource& src, int64_t n_seeds, const int64_t* n_seeds_dev,
+                       const TraceConfig& cfg, int precision, const LaunchShape& shape, const LineOutputs& out,
+                       cudaStream_t stream, DeviceStats* stats_dev, cudaEvent_t* ev) {
+  bool tangent = !cfg.length_only;
+  if (precision == QSL_FP64) {
+    if (tangent)
+      return launch_trace<double, 9>(f, src, n_seeds, n_seeds_dev, cfg, shape, out, stream, stats_dev, ev);
+    return launch_trace<double, 3>(f, src, n_seeds, n_seeds_dev, cfg, shape, out, stream, stats_dev, ev);
+  }
+  if (tangent)
+    return launch_trace<float, 9>(f, src, n_seeds, n_seeds_dev, cfg, shape, out, stream, stats_dev, ev);
+  return launch_trace<float, 3>(f, src, n_seeds, n_seeds_dev, cfg, shape, out, stream, stats_dev, ev);
+}
+
+int select_retrace(const SeedSource& src, int64_t n_seeds, const LineOutputs& out, double threshold,
+                   int64_t* index, int64_t* count_dev, cudaStream_t stream) {
+  (void)src;
+  QSL_CHECK_CUDA(cudaMemsetAsync(count_dev, 0, sizeof(int64_t), stream));
+  if (n_seeds == 0) return QSL_OK;
+  int blocks = (int)((n_seeds + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  select_kernel<<<blocks, 256, 0, stream>>>(n_seeds, out.q, out.lines, out.q_form, threshold, index, count_dev);
+  QSL_CHECK_CUDA(cudaGetLastError());
+  return QSL_OK;
+}
+
+}  // namespace qsl

@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libqsl.so (include/qsl.h), same names as the C ABI.
+
+Argument marshalling only: arrays are torch tensors (device memory, current
+stream) or numpy arrays (host memory); every step of the computation runs in
+the library's CUDA kernels. Loading fails loudly when libqsl.so is missing.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqsl.so")
+
+QSL_OK, QSL_EINVAL, QSL_ENOMEM, QSL_ECUDA, QSL_ETIMEOUT, QSL_ENONFINITE, QSL_ECAPACITY = 0, -1, -2, -3, -4, -5, -6
+QSL_MEM_HOST, QSL_MEM_DEVICE = 0, 1
+QSL_F32, QSL_F64 = 0, 1
+QSL_PAPER_NORMALIZE_FIRST, QSL_RAW_B = 0, 1
+QSL_RKCK54, QSL_EULER = 0, 1
+QSL_Q_PERP, QSL_Q_FOOT, QSL_Q_DET = 0, 1, 2
+QSL_FP32_MIXED, QSL_FP64 = 0, 1
+(QSL_LINE_OK, QSL_LINE_MAXLEN, QSL_LINE_MAXSTEPS, QSL_LINE_STALL, QSL_LINE_OUTSIDE, QSL_LINE_NONFINITE,
+ QSL_LINE_NULL, QSL_LINE_TIMEOUT) = range(8)
+QSL_FLAG_OPEN_SKIPPED, QSL_FLAG_RETRACED = 0x40, 0x80
+QSL_NO_FACE = 255
+
+
+class QslError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("qsl error %d: %s" % (code, msg))
+        self.code = code
+
+
+class qsl_opts(C.Structure):
+    _fields_ = [("integrator", C.c_int32), ("q_form", C.c_int32), ("precision", C.c_int32),
+                ("skip_open", C.c_int32), ("length_only", C.c_int32), ("warps_per_block", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("refill_min", C.c_int32), ("tol_abs", C.c_double),
+                ("tol_rel", C.c_double), ("h_init", C.c_double), ("h_max", C.c_double), ("h_min", C.c_double),
+                ("max_length", C.c_double), ("max_steps", C.c_int64), ("euler_h", C.c_double),
+                ("retrace_q", C.c_double), ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
+                ("land_tol", C.c_double), ("timeout_s", C.c_double)]
+
+
+QSL_LINE_DTYPE = np.dtype([("q_perp", "<f8"), ("q_foot", "<f8"), ("q_det", "<f8"), ("b0", "<f8"), ("bf", "<f8"),
+                           ("bb", "<f8"), ("flux_f", "<f8"), ("flux_b", "<f8"), ("length", "<f4"),
+                           ("lam_f", "<f4"), ("lam_b", "<f4"), ("pad0", "<f4"), ("x_f", "<f4", (3,)),
+                           ("x_b", "<f4", (3,)), ("steps", "<i4"), ("face_f", "u1"), ("face_b", "u1"),
+                           ("status_f", "u1"), ("status_b", "u1")])
+assert QSL_LINE_DTYPE.itemsize == 112
+
+
+class qsl_stats(C.Structure):
+    _fields_ = [("lines", C.c_int64), ("stage_evals", C.c_int64), ("accepted", C.c_int64), ("rejected", C.c_int64),
+                ("landing", C.c_int64), ("retraced", C.c_int64), ("kernel_ms", C.c_double),
+                ("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_min", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+class qsl_refine_spec(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("coarse_order", C.c_int32), ("max_order", C.c_int32),
+                ("max_iters", C.c_int32), ("extent", C.c_int32 * 3), ("shift", C.c_int32),
+                ("out_order", C.c_int32), ("pad", C.c_int32), ("center", C.c_double * 3), ("u", C.c_double * 3),
+                ("v", C.c_double * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("tau", C.c_double),
+                ("proposal", C.c_void_p)]
+
+
+class qsl_samples(C.Structure):
+    _fields_ = [("capacity", C.c_int64), ("count", C.c_int64), ("key", C.c_void_p), ("q", C.c_void_p),
+                ("length", C.c_void_p), ("faces", C.c_void_p), ("status", C.c_void_p), ("iters", C.c_int32),
+                ("traced", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libqsl.so (built in-tree by paper_1609_00724_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise OSError("libqsl.so not found at %s: build it with `python -m paper_1609_00724_gb300.build`"
+                      % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dp = C.c_void_p, C.c_int, C.c_int64, C.c_void_p
+    L.qsl_last_error.restype = C.c_char_p
+    L.qsl_opts_default.argtypes = [C.POINTER(qsl_opts)]
+    L.qsl_load_field.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, dp, dp, dp, i32, vp, C.POINTER(vp)]
+    L.qsl_free_field.argtypes = [vp]
+    L.qsl_trace_seeds.argtypes = [vp, vp, i64, C.POINTER(qsl_opts), vp, i32, vp]
+    L.qsl_q_map_2d.argtypes = [vp, dp, dp, dp, i32, i32, C.POINTER(qsl_opts), vp, vp, vp, vp, i32, vp]
+    L.qsl_q_volume_3d.argtypes = [vp, dp, dp, i32, i32, i32, C.POINTER(qsl_opts), vp, vp, vp, vp, i32, vp]
+    L.qsl_fledge.argtypes = [vp, i32, vp, vp, i32, vp]
+    L.qsl_refine.argtypes = [vp, C.POINTER(qsl_refine_spec), C.POINTER(qsl_opts), C.POINTER(qsl_samples), vp, vp,
+                             i32, vp]
+    L.qsl_hilbert_encode.argtypes = [vp, i64, i32, i32, vp, i32, vp]
+    L.qsl_hilbert_decode.argtypes = [vp, i64, i32, i32, vp, i32, vp]
+    L.qsl_convert.argtypes = [vp, vp, i64, i32, i32, vp, i32, i32, vp, i32, vp]
+    L.qsl_last_stats.argtypes = [C.POINTER(qsl_stats)]
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != QSL_OK:
+        raise QslError(rc, lib().qsl_last_error().decode())
+    return rc
+
+
+# ------------------------------------------------------------------ marshalling
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _mem_of(*arrays):
+    kinds = {(_is_torch(a) and a.is_cuda) for a in arrays if a is not None}
+    if len(kinds) > 1:
+        raise ValueError("mix of device and host arrays")
+    return QSL_MEM_DEVICE if kinds == {True} else QSL_MEM_HOST
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        return C.c_void_p(a.data_ptr())
+    assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+    return C.c_void_p(a.ctypes.data)
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return C.c_void_p(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return C.c_void_p(0)
+
+
+def _d3(v):
+    return (C.c_double * 3)(*[float(x) for x in v])
+
+
+def qsl_opts_default(**kw):
+    o = qsl_opts()
+    lib().qsl_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if k in ("domain_lo", "domain_hi"):
+            getattr(o, k)[:] = [float(x) for x in v]
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Field:
+    """Owned handle of a packed field (qsl_load_field / qsl_free_field)."""
+
+    def __init__(self, handle, shape):
+        self.handle = handle
+        self.shape = shape
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qsl_free_field(self.handle)
+            self.handle = None
+
+
+def qsl_load_field(bx, by, bz, xc, yc, zc, interp_mode=QSL_PAPER_NORMALIZE_FIRST, stream=None):
+    """bx, by, bz: [nz, ny, nx] float32/float64 (torch CUDA tensors or numpy)."""
+    mem = _mem_of(bx, by, bz)
+    dt = str(bx.dtype)
+    dtype = QSL_F64 if "64" in dt else QSL_F32
+    nz, ny, nx = bx.shape
+    ax = [np.ascontiguousarray(a, dtype=np.float64) for a in (xc, yc, zc)]
+    h = C.c_void_p()
+    _check(lib().qsl_load_field(_ptr(bx), _ptr(by), _ptr(bz), dtype, mem, nx, ny, nz,
+                                *(a.ctypes.data_as(C.c_void_p) for a in ax), interp_mode, _stream(stream),
+                                C.byref(h)))
+    return Field(h, (nx, ny, nz))
+
+
+def qsl_trace_seeds(field, seeds, opts, out=None, stream=None):
+    """seeds: S x 3 float64. Returns a numpy record array (host seeds) or a
+    torch uint8 tensor of S*112 bytes (device seeds)."""
+    S = seeds.shape[0]
+    mem = _mem_of(seeds)
+    if out is None:
+        if mem == QSL_MEM_DEVICE:
+            import torch
+            out = torch.empty(S * QSL_LINE_DTYPE.itemsize, dtype=torch.uint8, device=seeds.device)
+        else:
+            out = np.zeros(S, dtype=QSL_LINE_DTYPE)
+    _check(lib().qsl_trace_seeds(field.handle, _ptr(seeds), S, C.byref(opts), _ptr(out), mem, _stream(stream)))
+    return out
+
+
+def lines_to_numpy(raw):
+    """Device qsl_line bytes (torch uint8) -> numpy record array."""
+    return np.frombuffer(raw.cpu().numpy().tobytes(), dtype=QSL_LINE_DTYPE)
+
+
+def qsl_q_map_2d(field, center, u, v, nu, nv, opts, q=None, length=None, faces=None, status=None, stream=None):
+    mem = _mem_of(q, length, faces, status)
+    _check(lib().qsl_q_map_2d(field.handle, _d3(center), _d3(u), _d3(v), nu, nv, C.byref(opts), _ptr(q),
+                              _ptr(length), _ptr(faces), _ptr(status), mem, _stream(stream)))
+
+
+def qsl_q_volume_3d(field, lo, hi, nx, ny, nz, opts, q=None, length=None, faces=None, status=None, stream=None):
+    mem = _mem_of(q, length, faces, status)
+    _check(lib().qsl_q_volume_3d(field.handle, _d3(lo), _d3(hi), nx, ny, nz, C.byref(opts), _ptr(q), _ptr(length),
+                                 _ptr(faces), _ptr(status), mem, _stream(stream)))
+
+
+def qsl_fledge(length, s_out, stream=None):
+    mem = _mem_of(length, s_out)
+    shape = np.array(list(length.shape), dtype=np.int64)
+    _check(lib().qsl_fledge(_ptr(length), len(length.shape), shape.ctypes.data_as(C.c_void_p), _ptr(s_out), mem,
+                            _stream(stream)))
+
+
+def refine_spec(**kw):
+    s = qsl_refine_spec()
+    s.max_iters = 64
+    s.shift = 1
+    for k, v in kw.items():
+        if k in ("extent", "center", "u", "v", "lo", "hi"):
+            arr = getattr(s, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        elif k == "proposal":
+            s._proposal_keep = v
+            s.proposal = _ptr(v).value if v is not None else None
+        else:
+            setattr(s, k, v)
+    return s
+
+
+def qsl_refine(field, spec, opts, key, q, length, faces=None, status=None, count=0, q_grid=None, l_grid=None,
+               stream=None):
+    """Sample arrays (capacity = len(key)) are caller-owned; returns
+    (count, iters, traced) and raises on errors other than QSL_ECAPACITY."""
+    mem = _mem_of(key, q, length, faces, status, q_grid, l_grid)
+    smp = qsl_samples()
+    smp.capacity = key.shape[0]
+    smp.count = count
+    smp.key, smp.q, smp.length = (_ptr(a).value for a in (key, q, length))
+    smp.faces = _ptr(faces).value if faces is not None else None
+    smp.status = _ptr(status).value if status is not None else None
+    rc = lib().qsl_refine(field.handle, C.byref(spec), C.byref(opts), C.byref(smp), _ptr(q_grid), _ptr(l_grid), mem,
+                          _stream(stream))
+    if rc not in (QSL_OK, QSL_ECAPACITY):
+        _check(rc)
+    return int(smp.count), int(smp.iters), int(smp.traced), rc
+
+
+def qsl_hilbert_encode(coords, ndim, bits, keys, stream=None):
+    mem = _mem_of(coords, keys)
+    _check(lib().qsl_hilbert_encode(_ptr(coords), coords.shape[0], ndim, bits, _ptr(keys), mem, _stream(stream)))
+
+
+def qsl_hilbert_decode(keys, ndim, bits, coords, stream=None):
+    mem = _mem_of(coords, keys)
+    _check(lib().qsl_hilbert_decode(_ptr(keys), keys.shape[0], ndim, bits, _ptr(coords), mem, _stream(stream)))
+
+
+def qsl_convert(keys, vals, ndim, max_order, extent, out_order, log_interp, out, stream=None):
+    mem = _mem_of(keys, vals, out)
+    ext = np.zeros(3, dtype=np.int32)
+    ext[:ndim] = extent[:ndim]
+    _check(lib().qsl_convert(_ptr(keys), _ptr(vals), keys.shape[0], ndim, max_order,
+                             ext.ctypes.data_as(C.c_void_p), out_order, int(log_interp), _ptr(out), mem,
+                             _stream(stream)))
+
+
+def qsl_last_stats():
+    s = qsl_stats()
+    _check(lib().qsl_last_stats(C.byref(s)))
+    return {k: getattr(s, k) for k, _ in s._fields_ if k != "pad"}
+
+
+EXPORTS = ["qsl_opts_default", "qsl_load_field", "qsl_free_field", "qsl_trace_seeds", "qsl_q_map_2d",
+           "qsl_q_volume_3d", "qsl_fledge", "qsl_refine", "qsl_hilbert_encode", "qsl_hilbert_decode", "qsl_convert",
+           "qsl_last_error", "qsl_last_stats"]

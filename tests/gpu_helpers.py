@@ -1,0 +1,63 @@
+"""Shared helpers of the GPU parity tests (inputs and comparisons only)."""
+import numpy as np
+
+# spec parity bar: Q rel <= 1e-3 for Q < 1e6, length rel <= 1e-5,
+# end-face labels exact for ends more than 1e-3 cells from a face edge
+Q_RTOL = 1e-3
+L_RTOL = 1e-5
+EDGE_CELLS = 1e-3
+
+# FP32 tracer tolerance used by the parity runs (the oracle runs at 1e-11)
+GPU_TOL = 1e-7
+
+
+def edge_distance(x, face, lo, hi):
+    """Distance (domain units) of an end point on `face` to the nearest edge of that face."""
+    ax = face // 2
+    d = np.inf
+    for a in range(3):
+        if a == ax:
+            continue
+        d = min(d, x[a] - lo[a], hi[a] - x[a])
+    return d
+
+
+def compare_lines(gpu, ref, cell, lo, hi, q_key_gpu="q_perp", q_key_ref="q_perp", q_rtol=Q_RTOL, l_rtol=L_RTOL):
+    """gpu: dict/record arrays from the CUDA path; ref: oracle dict. Returns a
+    report dict and raises AssertionError on a parity failure."""
+    n = len(ref["L"])
+    fails = []
+    label_checked = 0
+    q_checked = 0
+    worst_q = 0.0
+    worst_l = 0.0
+    for i in range(n):
+        sf, sb = int(ref["st_f"][i]), int(ref["st_b"][i])
+        away = True
+        for key_x, key_face in (("xf", "face_f"), ("xb", "face_b")):
+            f = int(ref[key_face][i])
+            if f != 255 and edge_distance(ref[key_x][i], f, lo, hi) <= EDGE_CELLS * cell:
+                away = False
+        if away:
+            label_checked += 1
+            if int(gpu["face_f"][i]) != int(ref["face_f"][i]) or int(gpu["face_b"][i]) != int(ref["face_b"][i]):
+                fails.append(("face", i, (gpu["face_f"][i], gpu["face_b"][i]), (ref["face_f"][i], ref["face_b"][i])))
+                continue
+        Lr = ref["L"][i]
+        if np.isfinite(Lr) and Lr > 0:
+            e = abs(gpu["L"][i] / Lr - 1)
+            worst_l = max(worst_l, e)
+            if not e <= l_rtol:
+                fails.append(("L", i, gpu["L"][i], Lr, e))
+        qr = ref[q_key_ref][i]
+        if np.isfinite(qr) and qr < 1e6 and away:
+            q_checked += 1
+            e = abs(gpu[q_key_gpu][i] / qr - 1)
+            worst_q = max(worst_q, e)
+            if not e <= q_rtol:
+                fails.append(("Q", i, gpu[q_key_gpu][i], qr, e))
+    rep = {"n": n, "labels_checked": label_checked, "q_checked": q_checked, "worst_q": worst_q, "worst_l": worst_l,
+           "fails": fails[:10], "n_fail": len(fails)}
+    print("parity:", {k: v for k, v in rep.items() if k != "fails"}, rep["fails"][:4])
+    assert not fails, rep
+    return rep

@@ -1,0 +1,199 @@
+"""GPU parity of the tracer (qsl_trace_seeds, qsl_q_map_2d, qsl_q_volume_3d)
+against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1609_00724_gb300 import inputs
+from gpu_helpers import GPU_TOL, compare_lines
+
+pytestmark = pytest.mark.gpu
+
+BOX_LO, BOX_HI = (-1.0, -1.0, 0.0), (1.0, 1.0, 1.0)
+
+
+@pytest.fixture(scope="module")
+def qsl():
+    from paper_1609_00724_gb300 import qsl as q
+    q.lib()
+    return q
+
+
+def _gpu_field(qsl, gf, mode):
+    t = [torch.as_tensor(np.ascontiguousarray(a)).cuda() if not isinstance(a, torch.Tensor) else a.cuda()
+         for a in (gf.bx, gf.by, gf.bz)]
+    return qsl.qsl_load_field(*t, gf.xc, gf.yc, gf.zc, interp_mode=mode)
+
+
+def _oracle_field(oracle_mod, gf, mode):
+    g = inputs.to_numpy64(gf)
+    return oracle_mod.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=mode)
+
+
+def _rec_to_dict(rec):
+    return {"q_perp": rec["q_perp"], "q_foot": rec["q_foot"], "q_det": rec["q_det"], "L": rec["length"],
+            "face_f": rec["face_f"], "face_b": rec["face_b"], "xf": rec["x_f"], "xb": rec["x_b"],
+            "st_f": rec["status_f"], "st_b": rec["status_b"]}
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_trace_seeds_charge_field(qsl, oracle_mod, mode):
+    ch = inputs.random_charges(4, 2)
+    gf = inputs.charge_field(ch, 64, dtype=torch.float32)
+    F = _gpu_field(qsl, gf, mode)
+    Fo = _oracle_field(oracle_mod, gf, mode)
+    seeds = inputs.random_seeds(600, 17)
+    seeds[:150, 2] = 0.0     # footpoints on the bottom face
+    seeds[150:160, 0] = 1.0  # on the x+ face
+    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL)
+    rec = qsl.lines_to_numpy(qsl.qsl_trace_seeds(F, torch.as_tensor(seeds).cuda(), o))
+    ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
+    g = _rec_to_dict(rec)
+    rep = compare_lines(g, ref, 2.0 / 63, BOX_LO, BOX_HI)
+    rep2 = compare_lines(g, ref, 2.0 / 63, BOX_LO, BOX_HI, "q_foot", "q_foot")
+    rep3 = compare_lines(g, ref, 2.0 / 63, BOX_LO, BOX_HI, "q_det", "q_det")
+    print(rep["worst_q"], rep["worst_l"], rep2["worst_q"], rep3["worst_q"])
+    assert rep["q_checked"] > 300
+    # statuses agree
+    assert np.array_equal(rec["status_f"], ref["st_f"]) and np.array_equal(rec["status_b"], ref["st_b"])
+    # host-memory path gives the same records as the device path
+    rec_h = qsl.qsl_trace_seeds(F, seeds, o)
+    assert np.array_equal(rec_h["face_f"], rec["face_f"])
+    assert np.allclose(rec_h["length"], rec["length"], rtol=1e-6)
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_config1_hyperbolic_map(qsl, oracle_mod, mode):
+    """The 256 x 256 map of the linear hyperbolic field on z = 0: raw mode
+    against the closed forms (golden fixture), both modes against the oracle
+    on a subsample that includes the 12 top-exit columns."""
+    gf = inputs.hyperbolic_field(64)
+    F = _gpu_field(qsl, gf, mode)
+    n = 256
+    q = torch.empty(n * n, device="cuda")
+    L = torch.empty(n * n, device="cuda")
+    faces = torch.empty(2 * n * n, dtype=torch.uint8, device="cuda")
+    st = torch.empty(n * n, dtype=torch.uint8, device="cuda")
+    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL, q_form=qsl.QSL_Q_FOOT)
+    qsl.qsl_q_map_2d(F, (0, 0, 0), (2, 0, 0), (0, 2, 0), n, n, o, q, L, faces, st)
+    torch.cuda.synchronize()
+    q, L, faces, st = q.cpu().numpy(), L.cpu().numpy(), faces.cpu().numpy().reshape(-1, 2), st.cpu().numpy()
+    assert np.all(st & 0x3f == 0)
+    if mode == 1:
+        import os
+        g = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "hyperbolic_closed_forms.txt"))
+        idx = g[:, 1].astype(int) * n + g[:, 0].astype(int)
+        assert np.array_equal(faces[idx, 0], g[:, 7].astype(int))
+        assert np.all(np.abs(q[idx] / g[:, 4] - 1) < 1e-3)
+        assert np.all(np.abs(L[idx] / g[:, 6] - 1) < 1e-5)
+    Fo = _oracle_field(oracle_mod, gf, mode)
+    cols = sorted(set(range(0, n, 7)) | set(range(122, 134)))
+    rows = list(range(3, n, 11))
+    pix = np.array([j * n + i for j in rows for i in cols])
+    seeds = oracle_mod.plane_seeds([0, 0, 0], [2, 0, 0], [0, 2, 0], n, n)[pix]
+    ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
+    g = {"q_foot": q[pix], "L": L[pix], "face_f": faces[pix, 0], "face_b": faces[pix, 1]}
+    compare_lines(g, ref, 1.0 / 63, BOX_LO, BOX_HI, "q_foot", "q_foot")
+
+
+def test_volume_map_matches_oracle(qsl, oracle_mod):
+    ch = inputs.random_charges(8, 3)
+    gf = inputs.charge_field(ch, 48, dtype=torch.float32)
+    F = _gpu_field(qsl, gf, 0)
+    nx, ny, nz = 40, 36, 17  # ragged against any tiling
+    N = nx * ny * nz
+    q = torch.empty(N, device="cuda")
+    L = torch.empty(N, device="cuda")
+    faces = torch.empty(2 * N, dtype=torch.uint8, device="cuda")
+    st = torch.empty(N, dtype=torch.uint8, device="cuda")
+    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL)
+    qsl.qsl_q_volume_3d(F, BOX_LO, BOX_HI, nx, ny, nz, o, q, L, faces, st)
+    torch.cuda.synchronize()
+    Fo = _oracle_field(oracle_mod, gf, 0)
+    idx = inputs.subsample(N, 500, 99)
+    seeds = oracle_mod.volume_seeds(BOX_LO, BOX_HI, nx, ny, nz)[idx]
+    ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
+    fc = faces.cpu().numpy().reshape(-1, 2)
+    g = {"q_perp": q.cpu().numpy()[idx], "L": L.cpu().numpy()[idx], "face_f": fc[idx, 0], "face_b": fc[idx, 1]}
+    compare_lines(g, ref, 2.0 / 47, BOX_LO, BOX_HI)
+
+
+def test_fp64_precision_matches_oracle_tightly(qsl, oracle_mod):
+    ch = inputs.random_charges(4, 5)
+    gf = inputs.charge_field(ch, 32, dtype=torch.float64)
+    F = _gpu_field(qsl, gf, 1)
+    Fo = _oracle_field(oracle_mod, gf, 1)
+    seeds = inputs.random_seeds(200, 23)
+    o = qsl.qsl_opts_default(tol_abs=1e-10, tol_rel=1e-10, precision=qsl.QSL_FP64)
+    rec = qsl.qsl_trace_seeds(F, seeds, o)
+    ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
+    # lengths are stored as float32 in the record: 3e-7 covers their rounding
+    compare_lines(_rec_to_dict(rec), ref, 2.0 / 31, BOX_LO, BOX_HI, q_rtol=2e-6, l_rtol=3e-7)
+
+
+def test_euler_matches_oracle_euler(qsl, oracle_mod):
+    """Fixed-step Euler (Sec. "Integration methods"): same steps on both sides."""
+    gf = inputs.hyperbolic_field(32)
+    F = _gpu_field(qsl, gf, 1)
+    Fo = _oracle_field(oracle_mod, gf, 1)
+    seeds = inputs.random_seeds(100, 4, margin=0.05)
+    o = qsl.qsl_opts_default(integrator=qsl.QSL_EULER, euler_h=0.2, precision=qsl.QSL_FP64)
+    rec = qsl.qsl_trace_seeds(F, seeds, o)
+    ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(integrator=1, euler_h=0.2))
+    compare_lines(_rec_to_dict(rec), ref, 1.0 / 31, BOX_LO, BOX_HI, q_rtol=1e-9, l_rtol=2e-7)
+
+
+def test_edge_cases(qsl, oracle_mod):
+    gf = inputs.hyperbolic_field(16)
+    F = _gpu_field(qsl, gf, 1)
+    o = qsl.qsl_opts_default(tol_abs=1e-6, tol_rel=1e-6)
+    # no seeds
+    out = qsl.qsl_trace_seeds(F, np.zeros((0, 3)), o)
+    assert out.shape == (0,)
+    # outside, on a face moving out, max length cutoff
+    seeds = np.array([[0.0, 0.0, -0.5], [0.3, 0.2, 0.0], [0.0, 0.0, 0.5]])
+    o2 = qsl.qsl_opts_default(tol_abs=1e-7, tol_rel=1e-7, max_length=0.2)
+    rec = qsl.qsl_trace_seeds(F, seeds, o2)
+    assert rec["status_f"][0] == qsl.QSL_LINE_OUTSIDE and np.isnan(rec["length"][0])
+    assert rec["face_b"][1] == 4 and rec["lam_b"][1] == 0.0
+    assert rec["status_f"][2] == qsl.QSL_LINE_MAXLEN and abs(rec["length"][2] - 0.4) < 1e-6
+    # zero field: the line cannot start
+    z = np.zeros((4, 4, 4))
+    ax = np.linspace(0, 1, 4)
+    Fz = qsl.qsl_load_field(z, z, z, ax, ax, ax, qsl.QSL_RAW_B)
+    rz = qsl.qsl_trace_seeds(Fz, np.array([[0.5, 0.5, 0.5]]), o)
+    assert rz["status_f"][0] == qsl.QSL_LINE_NULL
+    # non-finite field values are rejected
+    zb = z.copy()
+    zb[1, 1, 1] = np.nan
+    with pytest.raises(qsl.QslError) as e:
+        qsl.qsl_load_field(zb, z, z, ax, ax, ax)
+    assert e.value.code == qsl.QSL_ENONFINITE
+    # bad arguments
+    with pytest.raises(qsl.QslError) as e:
+        qsl.qsl_trace_seeds(F, seeds, qsl.qsl_opts_default(tol_abs=-1.0))
+    assert e.value.code == qsl.QSL_EINVAL
+    with pytest.raises(qsl.QslError):
+        qsl.qsl_load_field(z, z, z, ax, ax[::-1].copy(), ax)
+
+
+def test_skip_open_and_retrace_flag(qsl, oracle_mod):
+    ch = inputs.random_charges(4, 2)
+    gf = inputs.charge_field(ch, 64, dtype=torch.float32)
+    F = _gpu_field(qsl, gf, 0)
+    n = 128
+    q = torch.empty(n * n, device="cuda")
+    st = torch.empty(n * n, dtype=torch.uint8, device="cuda")
+    faces = torch.empty(2 * n * n, dtype=torch.uint8, device="cuda")
+    o = qsl.qsl_opts_default(tol_abs=1e-6, tol_rel=1e-6, skip_open=1, retrace_q=1e3)
+    qsl.qsl_q_map_2d(F, (0, 0, 0), (2, 0, 0), (0, 2, 0), n, n, o, q=q, faces=faces, status=st)
+    torch.cuda.synchronize()
+    q, st, fc = q.cpu().numpy(), st.cpu().numpy(), faces.cpu().numpy().reshape(-1, 2)
+    closed = (fc[:, 0] == 4) & (fc[:, 1] == 4)
+    assert np.all(np.isnan(q[~closed]))
+    assert np.all((st[~closed] & qsl.QSL_FLAG_OPEN_SKIPPED) != 0)
+    assert np.all(np.isfinite(q[closed]))
+    s = qsl.qsl_last_stats()
+    ret = (st & qsl.QSL_FLAG_RETRACED) != 0
+    assert s["retraced"] == ret.sum()
+    assert np.all(q[ret & closed] > 1e3 * 0.99)
