@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=GRID_N)
     ap.add_argument("--coarse", type=int, default=COARSE)
+    ap.add_argument("--profile-map", action="store_true",
+                    help="only run the coarse Q map (the tracer kernel) --steps times, for ncu captures")
     return ap.parse_args()
 
 
@@ -263,6 +265,16 @@ def main():
     qsl.lib()
     field_seed = FIELD_SEED + 1000 * rank
     gf = make_field(field_seed, dev, args.grid)
+    if args.profile_map:
+        F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
+        N = args.coarse * args.coarse
+        qm, Lm = torch.empty(N, device=dev), torch.empty(N, device=dev)
+        for _ in range(args.steps):
+            qsl.qsl_q_map_2d(F, (0, 0, 0), (2, 0, 0), (0, 2, 0), args.coarse, args.coarse, opts(qsl), q=qm, length=Lm)
+        st = qsl.qsl_last_stats()
+        print(json.dumps({"profile_map": True, "grid": args.grid, "coarse": args.coarse, "kernel_ms": st["kernel_ms"],
+                          "stage_evals": st["stage_evals"], "retraced": st["retraced"]}))
+        return
     bufs = alloc(torch, args.coarse, dev)
 
     def barrier():
