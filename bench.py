@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=GRID_N)
     ap.add_argument("--coarse", type=int, default=COARSE)
+    ap.add_argument("--integrator", default="cell", choices=["cell", "ck"],
+                    help="cell: cell-wise Dormand-Prince (default); ck: the paper's plain Cash-Karp")
+    ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--profile-map", action="store_true",
                     help="only run the coarse Q map (the tracer kernel) --steps times, for ncu captures")
     return ap.parse_args()
@@ -121,8 +124,13 @@ def make_field(seed, device, n):
     return inputs.charge_field(ch, n, dtype=torch.float32, device=device, slab=64)
 
 
+INTEGRATOR = {"cell": 2, "ck": 0}
+RUN = {"integrator": "cell", "tol": TOL}
+
+
 def opts(qsl):
-    return qsl.qsl_opts_default(tol_abs=TOL, tol_rel=TOL, q_form=qsl.QSL_Q_PERP)
+    return qsl.qsl_opts_default(tol_abs=RUN["tol"], tol_rel=RUN["tol"], q_form=qsl.QSL_Q_PERP,
+                                integrator=INTEGRATOR[RUN["integrator"]])
 
 
 def spec(qsl, coarse):
@@ -251,6 +259,8 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    RUN["integrator"] = args.integrator
+    RUN["tol"] = args.tol if args.tol is not None else TOL
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -343,7 +353,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "4-charge potential field %d^3 FP32, %d^2 z=0 Q map refined to %d^2 effective"
                                    % (args.grid, args.coarse, eff),
-                       "tol": TOL, "tau": TAU, "coarse_order": int(np.log2(args.coarse)), "max_order":
+                       "tol": RUN["tol"], "integrator": RUN["integrator"], "tau": TAU, "coarse_order": int(np.log2(args.coarse)), "max_order":
                            int(np.log2(eff)), "interp": "paper (normalise first)", "precision": "FP32 trace, FP64 Q",
                        "l2": "inputs larger than L2 (268 MB packed field)", "parallelism": "replicas x%d" % world,
                        "samples_per_step": info.get("samples"), "refine_iters": info.get("iters"),

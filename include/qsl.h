@@ -55,9 +55,16 @@ extern "C" {
 #define QSL_PAPER_NORMALIZE_FIRST 0
 #define QSL_RAW_B 1
 
-/* Integrators (Sec. "Integration methods"). */
+/* Integrators (Sec. "Integration methods": the paper's adaptive Cash-Karp
+ * stepper "can easily be substituted" by another embedded Runge-Kutta pair). */
 #define QSL_RKCK54 0 /* adaptive Cash-Karp 5(4), the paper's default          */
 #define QSL_EULER 1  /* fixed-step explicit Euler, step qsl_opts.euler_h cells */
+/* Adaptive Dormand-Prince 5(4) that never steps across a cell face: inside a
+ * cell the trilinear field is a polynomial, so each step integrates a smooth
+ * field from one 8-vertex gather, and its dense output (4th order) places the
+ * line exactly on the next cell face. Same ODE as the paper; uniform grids
+ * (other grids fall back to QSL_RKCK54). */
+#define QSL_DOPRI5_CELL 2
 
 /* Which Q the map calls return (qsl_line records hold all three). */
 #define QSL_Q_PERP 0 /* Eq. finalQ with dx_perp = dx - b (b.dx)                   */
@@ -87,7 +94,7 @@ extern "C" {
 
 /* ---- options ----------------------------------------------------------------- */
 typedef struct qsl_opts {
-  int32_t integrator;  /* QSL_RKCK54 | QSL_EULER                                    */
+  int32_t integrator;  /* QSL_RKCK54 | QSL_EULER | QSL_DOPRI5_CELL                  */
   int32_t q_form;      /* QSL_Q_PERP | QSL_Q_FOOT | QSL_Q_DET (map outputs)          */
   int32_t precision;   /* QSL_FP32_MIXED | QSL_FP64                                  */
   int32_t skip_open;   /* 1: lines not closed on z- get Q = NaN (Sec. "Squashing factor calculation") */

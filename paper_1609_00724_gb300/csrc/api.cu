@@ -90,7 +90,8 @@ void resolve_config(const qsl_field* f, const qsl_opts* o, TraceConfig* c) {
 static int validate_opts(const qsl_field* f, const qsl_opts* o) {
   if (!f) QSL_FAIL(QSL_EINVAL, "field is NULL");
   if (!o) QSL_FAIL(QSL_EINVAL, "opts is NULL");
-  if (o->integrator != QSL_RKCK54 && o->integrator != QSL_EULER) QSL_FAIL(QSL_EINVAL, "bad integrator %d", o->integrator);
+  if (o->integrator != QSL_RKCK54 && o->integrator != QSL_EULER && o->integrator != QSL_DOPRI5_CELL)
+    QSL_FAIL(QSL_EINVAL, "bad integrator %d", o->integrator);
   if (o->q_form < 0 || o->q_form > 2) QSL_FAIL(QSL_EINVAL, "bad q_form %d", o->q_form);
   if (o->precision != QSL_FP32_MIXED && o->precision != QSL_FP64) QSL_FAIL(QSL_EINVAL, "bad precision %d", o->precision);
   if (!(o->tol_abs > 0) || !(o->tol_rel >= 0)) QSL_FAIL(QSL_EINVAL, "tolerances must be tol_abs > 0, tol_rel >= 0");
@@ -108,8 +109,9 @@ int default_shape(const qsl_opts* o, int tangent, int precision, LaunchShape* s)
   if (o->blocks_per_sm > 0) {
     s->blocks_per_sm = o->blocks_per_sm;
   } else {
-    // enough resident warps to hide the gathers; registers set the ceiling
-    int w = tangent ? (precision == QSL_FP64 ? 8 : 16) : 32;
+    // as many resident warps as registers allow (the launch clamps to the
+    // occupancy of the chosen kernel)
+    int w = 64;
     s->blocks_per_sm = w / s->warps_per_block;
     if (s->blocks_per_sm < 1) s->blocks_per_sm = 1;
   }

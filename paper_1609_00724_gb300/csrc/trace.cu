@@ -726,6 +726,464 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
   if (lane == 0 && any_to && P.timeout_flag) atomicExch(P.timeout_flag, 1);
 }
 
+// ------------------------------------------------------------ cell-wise Dormand-Prince tracer
+// Dormand & Prince (1980) 5(4) pair with first-same-as-last stage and Hairer's
+// 4th-order continuous extension (the paper lets any Boost.odeint stepper
+// replace Cash-Karp, Sec. "Integration methods").
+constexpr double DA21 = 1.0 / 5.0;
+constexpr double DA31 = 3.0 / 40.0, DA32 = 9.0 / 40.0;
+constexpr double DA41 = 44.0 / 45.0, DA42 = -56.0 / 15.0, DA43 = 32.0 / 9.0;
+constexpr double DA51 = 19372.0 / 6561.0, DA52 = -25360.0 / 2187.0, DA53 = 64448.0 / 6561.0, DA54 = -212.0 / 729.0;
+constexpr double DA61 = 9017.0 / 3168.0, DA62 = -355.0 / 33.0, DA63 = 46732.0 / 5247.0, DA64 = 49.0 / 176.0,
+                 DA65 = -5103.0 / 18656.0;
+constexpr double DB1 = 35.0 / 384.0, DB3 = 500.0 / 1113.0, DB4 = 125.0 / 192.0, DB5 = -2187.0 / 6784.0,
+                 DB6 = 11.0 / 84.0;
+constexpr double DE1 = 71.0 / 57600.0, DE3 = -71.0 / 16695.0, DE4 = 71.0 / 1920.0, DE5 = -17253.0 / 339200.0,
+                 DE6 = 22.0 / 525.0, DE7 = -1.0 / 40.0;
+constexpr double DD1 = -12715105075.0 / 11282082432.0, DD3 = 87487479700.0 / 32700410799.0,
+                 DD4 = -10690763975.0 / 1880347072.0, DD5 = 701980252875.0 / 199316789632.0,
+                 DD6 = -1453857185.0 / 822651844.0, DD7 = 69997945.0 / 29380423.0;
+
+// Increment of the continuous extension at fraction t of the step:
+// y(t) - y0 = t (dy + s (bspl + t (c3 + s c4))), s = 1 - t, with
+// bspl = h k1 - dy, c3 = dy - h k7 - bspl and c4 = h sum_i D_i k_i.
+template <class R>
+__device__ __forceinline__ R y_at(R t, R dy, R hk1, R hk7, R c4) {
+  R s1 = R(1) - t;
+  R bspl = hk1 - dy;
+  R c3 = dy - hk7 - bspl;
+  return t * (dy + s1 * (bspl + t * (c3 + s1 * c4)));
+}
+
+// Right-hand side inside one cell: the 24 corner values (3 components x 8
+// corners, corner c = x + 2y + 4z) sit in shared memory with a stride of one
+// block; (u, v, w) are the in-cell coordinates (may lie slightly outside
+// [0, 1] within a step: the cell's trilinear polynomial is continued).
+template <class R, int NC>
+__device__ __forceinline__ void cell_rhs(const R* __restrict__ cs, int st, bool raw, R ihx, R ihy, R ihz,
+                                         const R* y, R* k) {
+  R u = y[0], v = y[1], w = y[2];
+  R val[3], d[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R* p = cs + (8 * c) * st;
+    tri1<R>(p[0], p[st], p[2 * st], p[3 * st], p[4 * st], p[5 * st], p[6 * st], p[7 * st], u, v, w, val[c], d[c][0],
+            d[c][1], d[c][2]);
+    d[c][0] *= ihx;
+    d[c][1] *= ihy;
+    d[c][2] *= ihz;
+  }
+  R g[3][3];
+  if (!raw) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) g[i][j] = d[i][j];
+  } else {
+    R m = sqrt(val[0] * val[0] + val[1] * val[1] + val[2] * val[2]);
+    R rm = (m > R(0)) ? R(1) / m : R(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) val[i] *= rm;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R t = val[0] * d[0][j] + val[1] * d[1][j] + val[2] * d[2][j];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) g[i][j] = (d[i][j] - val[i] * t) * rm;
+    }
+  }
+  k[0] = val[0] * ihx;  // position in cell units
+  k[1] = val[1] * ihy;
+  k[2] = val[2] * ihz;
+  if (NC == 9) {
+#pragma unroll
+    for (int v2 = 0; v2 < 2; ++v2)
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        k[3 + 3 * v2 + i] = g[i][0] * y[3 + 3 * v2] + g[i][1] * y[4 + 3 * v2] + g[i][2] * y[5 + 3 * v2];
+  }
+}
+
+template <class R, int NC>
+__global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int st = blockDim.x;
+  R* cs = reinterpret_cast<R*>(smem_raw) + threadIdx.x;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  int64_t total = P.n_units;
+  if (P.n_seeds_dev) {
+    int64_t c = 2 * (*P.n_seeds_dev);
+    total = c < total ? c : total;
+  }
+  const FieldView<R>& F = P.F;
+  const R ih[3] = {R(F.inv_h[0]), R(F.inv_h[1]), R(F.inv_h[2])};
+  const R hh3[3] = {R(1) / ih[0], R(1) / ih[1], R(1) / ih[2]};
+  const R band = R(16) * eps_of<R>();  // tolerance band of internal cell faces (cell units)
+  const R tiny = R(1e-4) * P.h_max;
+
+  bool active = false, exhausted = false, kvalid = false;
+  int64_t unit = 0;
+  R y[NC], k1[NC];
+  int ic[3] = {0, 0, 0};
+  R mu = 0, muc = 0, h = 0, sgn = 1;
+  int steps = 0, zc = 0;
+  unsigned long long c_stage = 0, c_acc = 0, c_rej = 0, c_land = 0, c_lines = 0;
+  int iter = 0;
+  bool timed_out = false;
+  const unsigned long long t_start = P.timeout_ns ? globaltimer() : 0ull;
+
+  for (;;) {
+    if (!exhausted) {
+      unsigned need = __ballot_sync(FULL, !active);
+      int nneed = __popc(need);
+      if (nneed > 0 && (nneed >= P.refill_min || need == FULL)) {
+        int leader = __ffs(need) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(P.head, (unsigned long long)nneed);
+        base = __shfl_sync(FULL, base, leader);
+        if ((int64_t)(base + nneed) >= total) exhausted = true;
+        if (!active) {
+          int64_t myu = (int64_t)base + __popc(need & lt_mask);
+          if (myu < total) {
+            unit = myu;
+            active = true;
+            c_lines += (myu & 1) == 0;
+            int64_t g;
+            double xd[3];
+            seed_of(P.src, unit >> 1, &g, xd);
+            sgn = (unit & 1) ? R(-1) : R(1);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              double fa = (xd[a] - (double)F.org[a]) * (double)F.inv_h[a];
+              double fl = floor(fmin(fmax(fa, 0.0), (double)(F.n[a] - 2)));
+              ic[a] = (int)fl;
+              y[a] = (R)(fa - fl);
+            }
+            mu = 0;
+            muc = 0;
+            steps = 0;
+            zc = 0;
+            kvalid = false;
+            int lface = NO_FACE;
+            int status = ST_RUNNING;
+            bool outside = false;
+#pragma unroll
+            for (int f = 0; f < 6; ++f)
+              if (face_g<R, true>(P.lo, P.hi, ic, f, y, (const R*)nullptr) > R(0)) outside = true;
+            if (outside || !isfinite(xd[0]) || !isfinite(xd[1]) || !isfinite(xd[2])) {
+              status = QSL_LINE_OUTSIDE;
+            } else {
+              Interp<R> I0;
+              interp<R, R, false, false, true>(F, y[0], y[1], y[2], I0, ic);
+              R m0 = sqrt(I0.b[0] * I0.b[0] + I0.b[1] * I0.b[1] + I0.b[2] * I0.b[2]);
+              if (!(m0 > R(0))) {
+                status = QSL_LINE_NULL;
+              } else {
+                if (NC == 9) {
+                  // Eq. ic (same construction as the Cash-Karp tracer)
+                  R u0[3] = {I0.b[0] / m0, I0.b[1] / m0, I0.b[2] / m0};
+                  int ax = 0;
+                  if (fabs(u0[1]) < fabs(u0[ax])) ax = 1;
+                  if (fabs(u0[2]) < fabs(u0[ax])) ax = 2;
+                  R av[3];
+                  if (ax == 0) { av[0] = 0; av[1] = -u0[2]; av[2] = u0[1]; }
+                  else if (ax == 1) { av[0] = u0[2]; av[1] = 0; av[2] = -u0[0]; }
+                  else { av[0] = -u0[1]; av[1] = u0[0]; av[2] = 0; }
+                  R an = sqrt(av[0] * av[0] + av[1] * av[1] + av[2] * av[2]);
+                  av[0] /= an;
+                  av[1] /= an;
+                  av[2] /= an;
+                  y[3] = av[0];
+                  y[4] = av[1];
+                  y[5] = av[2];
+                  y[6] = u0[1] * av[2] - u0[2] * av[1];
+                  y[7] = u0[2] * av[0] - u0[0] * av[2];
+                  y[8] = u0[0] * av[1] - u0[1] * av[0];
+                }
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                  if (status == ST_RUNNING && face_g<R, true>(P.lo, P.hi, ic, f, y, (const R*)nullptr) == R(0)) {
+                    R bn = I0.b[f >> 1] * sgn;
+                    R outw = (f & 1) ? bn : -bn;
+                    if (outw > R(0)) {
+                      status = QSL_LINE_OK;
+                      lface = f;
+                    }
+                  }
+                }
+              }
+            }
+            h = P.h_init;
+            if (status != ST_RUNNING) {
+              write_end<R, NC, true>(P, unit, y, ic, R(0), lface, status, 0);
+              active = false;
+            }
+          }
+        }
+      }
+    }
+    if (!__any_sync(FULL, active)) {
+      if (exhausted) break;
+      continue;
+    }
+    if (P.timeout_ns && ((++iter & 63) == 0)) {
+      if (globaltimer() - t_start > P.timeout_ns) timed_out = true;
+    }
+    if (!active) continue;
+
+    int status = ST_RUNNING, lface = NO_FACE;
+    if (timed_out) status = QSL_LINE_TIMEOUT;
+    if (status == ST_RUNNING && steps >= P.max_steps) status = QSL_LINE_MAXSTEPS;
+    R room = P.max_len - mu;
+    if (status == ST_RUNNING && !(room > R(0))) status = QSL_LINE_MAXLEN;
+    if (status == ST_RUNNING) {
+      if (!kvalid) {
+        // gather the 8 vertices of the current cell once; every stage of the
+        // following steps in this cell reads them from shared memory
+        typedef typename V4<R>::type V;
+        const size_t sy = (size_t)F.n[0], sz = (size_t)F.n[0] * (size_t)F.n[1];
+        const V* p = F.v + (size_t)ic[2] * sz + (size_t)ic[1] * sy + (size_t)ic[0];
+        V q[8];
+        q[0] = ldg4(p);
+        q[1] = ldg4(p + 1);
+        q[2] = ldg4(p + sy);
+        q[3] = ldg4(p + sy + 1);
+        q[4] = ldg4(p + sz);
+        q[5] = ldg4(p + sz + 1);
+        q[6] = ldg4(p + sz + sy);
+        q[7] = ldg4(p + sz + sy + 1);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          cs[c * st] = q[c].x;
+          cs[(8 + c) * st] = q[c].y;
+          cs[(16 + c) * st] = q[c].z;
+        }
+        cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], y, k1);
+        c_stage += 1;
+        kvalid = true;
+      }
+      // planes of this cell (cell faces, or domain faces where they come first)
+      R lo_pl[3], hi_pl[3];
+      bool lo_dom[3], hi_dom[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        R lr = P.lo[a] - R(ic[a]), hr = P.hi[a] - R(ic[a]);
+        lo_dom[a] = lr >= R(0);
+        hi_dom[a] = hr <= R(1);
+        lo_pl[a] = lo_dom[a] ? lr : R(0);
+        hi_pl[a] = hi_dom[a] ? hr : R(1);
+      }
+      // step: controller size, capped a little beyond the first plane along k1
+      R tface = R(1e30);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        R vel = sgn * k1[a];
+        if (vel > R(0)) tface = fmin(tface, (hi_pl[a] - y[a]) / vel);
+        else if (vel < R(0)) tface = fmin(tface, (lo_pl[a] - y[a]) / vel);
+      }
+      R hs = fmin(fmin(h, P.h_max), room);
+      bool capped = room <= fmin(h, P.h_max);
+      R hf = R(1.25) * fmax(tface, R(0)) + tiny;
+      if (hf < hs) {
+        hs = hf;
+        capped = false;
+      }
+      R hh = sgn * hs;
+      R k2[NC], k3[NC], k4[NC], k5[NC], k6[NC], k7[NC], t[NC];
+#pragma unroll
+      for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(DA21) * k1[i], y[i]);
+      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k2);
+#pragma unroll
+      for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(DA31) * k1[i] + R(DA32) * k2[i], y[i]);
+      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k3);
+#pragma unroll
+      for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(DA41) * k1[i] + R(DA42) * k2[i] + R(DA43) * k3[i], y[i]);
+      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k4);
+#pragma unroll
+      for (int i = 0; i < NC; ++i)
+        t[i] = fma(hh, R(DA51) * k1[i] + R(DA52) * k2[i] + R(DA53) * k3[i] + R(DA54) * k4[i], y[i]);
+      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k5);
+#pragma unroll
+      for (int i = 0; i < NC; ++i)
+        t[i] = fma(hh, R(DA61) * k1[i] + R(DA62) * k2[i] + R(DA63) * k3[i] + R(DA64) * k4[i] + R(DA65) * k5[i],
+                   y[i]);
+      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k6);
+      R dy[NC];
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        dy[i] = hh * (R(DB1) * k1[i] + R(DB3) * k3[i] + R(DB4) * k4[i] + R(DB5) * k5[i] + R(DB6) * k6[i]);
+        t[i] = y[i] + dy[i];
+      }
+      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k7);
+      c_stage += 6;
+      steps += 1;
+      R err = 0;
+      bool finite = true;
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        R e = fabs(hh * (R(DE1) * k1[i] + R(DE3) * k3[i] + R(DE4) * k4[i] + R(DE5) * k5[i] + R(DE6) * k6[i] +
+                         R(DE7) * k7[i]));
+        if (!isfinite(t[i])) finite = false;
+        R ya = fabs(y[i]), yb = fabs(t[i]);
+        if (i < 3) {
+          R base = R(F.org[i]) + R(ic[i]) * hh3[i];
+          e *= hh3[i];
+          ya = fabs(base + y[i] * hh3[i]);
+          yb = fabs(base + t[i] * hh3[i]);
+        }
+        err = fmax(err, cdiv(e, P.tol_abs + P.tol_rel * fmax(ya, yb)));
+      }
+      if (!finite) {
+        status = QSL_LINE_NONFINITE;
+      } else if (err > R(1)) {
+        c_rej += 1;
+        h = hs * fmax(R(0.2), R(0.9) * cpow(err, R(-0.25)));
+        if (h < P.h_min) status = QSL_LINE_STALL;
+      } else {
+        c_acc += 1;
+        R hnext = hs * ((err == R(0)) ? R(5) : fmin(R(5), R(0.9) * cpow(err, R(-0.2))));
+        // First plane crossed within the step, on the dense output (4th-order
+        // continuous extension): for every plane the step ends beyond, the
+        // first sign change of dense(t) - plane over t = 1/4, 1/2, 3/4, 1
+        // brackets the crossing, which safeguarded Newton then resolves; the
+        // earliest crossing wins.
+        R th = R(2);
+        int ax_c = -1, up_c = 0;
+#pragma unroll 1
+        for (int pl = 0; pl < 6; ++pl) {
+          int a = pl >> 1, up = pl & 1;
+          R ya = a == 0 ? y[0] : (a == 1 ? y[1] : y[2]);
+          R dya = a == 0 ? dy[0] : (a == 1 ? dy[1] : dy[2]);
+          R target = up ? (a == 0 ? hi_pl[0] : (a == 1 ? hi_pl[1] : hi_pl[2]))
+                        : (a == 0 ? lo_pl[0] : (a == 1 ? lo_pl[1] : lo_pl[2]));
+          bool dom = up ? (a == 0 ? hi_dom[0] : (a == 1 ? hi_dom[1] : hi_dom[2]))
+                        : (a == 0 ? lo_dom[0] : (a == 1 ? lo_dom[1] : lo_dom[2]));
+          R r = target - ya;  // exact near the plane
+          R over = up ? (dya - r) : (r - dya);
+          if (!(over > (dom ? R(0) : band))) continue;
+          R sg = up ? R(1) : R(-1);  // sg * f > 0 beyond the plane
+          R k1a = a == 0 ? k1[0] : (a == 1 ? k1[1] : k1[2]);
+          R k7a = a == 0 ? k7[0] : (a == 1 ? k7[1] : k7[2]);
+          R c4 = hh * (R(DD1) * k1a + R(DD3) * (a == 0 ? k3[0] : (a == 1 ? k3[1] : k3[2])) +
+                       R(DD4) * (a == 0 ? k4[0] : (a == 1 ? k4[1] : k4[2])) +
+                       R(DD5) * (a == 0 ? k5[0] : (a == 1 ? k5[1] : k5[2])) +
+                       R(DD6) * (a == 0 ? k6[0] : (a == 1 ? k6[1] : k6[2])) + R(DD7) * k7a);
+          R bspl = hh * k1a - dya;
+          R c3 = dya - hh * k7a - bspl;
+          // bracket the first crossing
+          R ta = R(0), tb = R(1);
+#pragma unroll
+          for (int q = 1; q < 4; ++q) {
+            R tq = R(0.25) * R(q);
+            R s1 = R(1) - tq;
+            R f = tq * (dya + s1 * (bspl + tq * (c3 + s1 * c4))) - r;
+            if (sg * f > R(0) && tb == R(1)) tb = tq;
+            else if (tb == R(1)) ta = tq;
+          }
+          R t = ta + (tb - ta) * R(0.5);
+          {
+            // chord estimate inside the bracket as the first iterate
+            R tl = r / dya;
+            if (tl > ta && tl < tb) t = tl;
+          }
+          for (int it = 0; it < 30; ++it) {
+            R s1 = R(1) - t;
+            R inner = c3 + s1 * c4;
+            R mid = bspl + t * inner;
+            R f = t * (dya + s1 * mid) - r;
+            if (fabs(f) <= R(4) * eps_of<R>() * (fabs(r) + fabs(dya)) || !(tb - ta > R(2) * eps_of<R>())) break;
+            if (sg * f > R(0)) tb = t;
+            else ta = t;
+            R dmid = inner - t * c4;
+            R df = dya + s1 * mid + t * (s1 * dmid - mid);
+            R tn = t - f / df;
+            t = (tn > ta && tn < tb) ? tn : R(0.5) * (ta + tb);
+          }
+          if (t < th) {
+            th = t;
+            ax_c = a;
+            up_c = up;
+          }
+        }
+        if (ax_c < 0) {
+          // the step stays in the cell: accept it; k7 is the next k1
+#pragma unroll
+          for (int i = 0; i < NC; ++i) {
+            y[i] += dy[i];
+            k1[i] = k7[i];
+          }
+          R t1 = hs - muc, t2 = mu + t1;
+          muc = (t2 - mu) - t1;
+          mu = t2;
+          h = hnext;
+          zc = 0;
+          if (capped) status = QSL_LINE_MAXLEN;
+        } else {
+          // advance to the plane on the dense output and snap onto it
+#pragma unroll
+          for (int i = 0; i < NC; ++i)
+            y[i] += y_at<R>(th, dy[i], hh * k1[i], hh * k7[i],
+                            hh * (R(DD1) * k1[i] + R(DD3) * k3[i] + R(DD4) * k4[i] + R(DD5) * k5[i] +
+                                  R(DD6) * k6[i] + R(DD7) * k7[i]));
+          bool dom = up_c ? hi_dom[ax_c] : lo_dom[ax_c];
+          R target = up_c ? hi_pl[ax_c] : lo_pl[ax_c];
+          if (ax_c == 0) y[0] = target;
+          else if (ax_c == 1) y[1] = target;
+          else y[2] = target;
+          R dl = th * hs;
+          R t1 = dl - muc, t2 = mu + t1;
+          muc = (t2 - mu) - t1;
+          mu = t2;
+          c_land += 1;
+          if (dom) {
+            status = QSL_LINE_OK;
+            lface = 2 * ax_c + up_c;
+          } else {
+            // enter the neighbouring cell
+            zc = (dl < tiny) ? zc + 1 : 0;
+            int na = ic[ax_c] + (up_c ? 1 : -1);
+            if (zc > 3 || na < 0 || na > F.n[ax_c] - 2) {
+              // grazing a face back and forth: stay in this cell for one step
+              // (the cell's polynomial continued across the face)
+              zc = 0;
+            } else {
+              ic[ax_c] = na;
+              if (ax_c == 0) y[0] = up_c ? R(0) : R(1);
+              else if (ax_c == 1) y[1] = up_c ? R(0) : R(1);
+              else y[2] = up_c ? R(0) : R(1);
+              kvalid = false;
+            }
+            h = fmax(hnext, hs);
+          }
+        }
+      }
+    }
+    if (status != ST_RUNNING) {
+      write_end<R, NC, true>(P, unit, y, ic, mu, lface, status, steps);
+      active = false;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c_stage += __shfl_down_sync(FULL, c_stage, o);
+    c_acc += __shfl_down_sync(FULL, c_acc, o);
+    c_rej += __shfl_down_sync(FULL, c_rej, o);
+    c_land += __shfl_down_sync(FULL, c_land, o);
+    c_lines += __shfl_down_sync(FULL, c_lines, o);
+  }
+  unsigned any_to = __ballot_sync(FULL, timed_out);
+  if (lane == 0 && P.stats) {
+    atomicAdd(&P.stats->stage_evals, c_stage);
+    atomicAdd(&P.stats->accepted, c_acc);
+    atomicAdd(&P.stats->rejected, c_rej);
+    atomicAdd(&P.stats->landing, c_land);
+    atomicAdd(&P.stats->lines, c_lines);
+    if (any_to) atomicAdd(&P.stats->timeouts, 1ull);
+  }
+  if (lane == 0 && any_to && P.timeout_flag) atomicExch(P.timeout_flag, 1);
+}
+
 // ------------------------------------------------------------ assembly (FP64)
 __device__ __forceinline__ double dot3(const double* a, const double* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
@@ -969,17 +1427,32 @@ int launch_trace(const qsl_field* f, const SeedSource& src, int64_t n_seeds, con
   P.timeout_ns = cfg.timeout_ns;
   P.timeout_flag = tflag;
   int threads = 32 * shape.warps_per_block;
-  int blocks = sms * shape.blocks_per_sm;
+  // persistent kernel: never launch more blocks than can be resident at once
+  const bool use_cell = loc && cfg.integrator == QSL_DOPRI5_CELL;
+  size_t smem = use_cell ? (size_t)24 * threads * sizeof(R) : 0;
+  int resident = 0;
+  if (use_cell)
+    QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_kernel<R, NC>, threads, smem));
+  else if (loc)
+    QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, trace_kernel<R, NC, true>, threads, 0));
+  else
+    QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, trace_kernel<R, NC, false>, threads, 0));
+  int bps = shape.blocks_per_sm < resident ? shape.blocks_per_sm : resident;
+  if (bps < 1) bps = 1;
+  int blocks = sms * bps;
   int64_t max_warps_needed = (2 * n_seeds + 31) / 32;
   if ((int64_t)blocks * shape.warps_per_block > max_warps_needed && !n_seeds_dev)
     blocks = (int)((max_warps_needed + shape.warps_per_block - 1) / shape.warps_per_block);
   if (blocks < 1) blocks = 1;
   if (ev) QSL_CHECK_CUDA(cudaEventRecord(ev[0], stream));
   if (n_seeds > 0) {
-    if (loc)
+    if (use_cell) {
+      cell_kernel<R, NC><<<blocks, threads, smem, stream>>>(P);
+    } else if (loc) {
       trace_kernel<R, NC, true><<<blocks, threads, 0, stream>>>(P);
-    else
+    } else {
       trace_kernel<R, NC, false><<<blocks, threads, 0, stream>>>(P);
+    }
     QSL_CHECK_CUDA(cudaGetLastError());
   }
   if (ev) QSL_CHECK_CUDA(cudaEventRecord(ev[1], stream));

@@ -16,7 +16,7 @@ QSL_OK, QSL_EINVAL, QSL_ENOMEM, QSL_ECUDA, QSL_ETIMEOUT, QSL_ENONFINITE, QSL_ECA
 QSL_MEM_HOST, QSL_MEM_DEVICE = 0, 1
 QSL_F32, QSL_F64 = 0, 1
 QSL_PAPER_NORMALIZE_FIRST, QSL_RAW_B = 0, 1
-QSL_RKCK54, QSL_EULER = 0, 1
+QSL_RKCK54, QSL_EULER, QSL_DOPRI5_CELL = 0, 1, 2
 QSL_Q_PERP, QSL_Q_FOOT, QSL_Q_DET = 0, 1, 2
 QSL_FP32_MIXED, QSL_FP64 = 0, 1
 (QSL_LINE_OK, QSL_LINE_MAXLEN, QSL_LINE_MAXSTEPS, QSL_LINE_STALL, QSL_LINE_OUTSIDE, QSL_LINE_NONFINITE,

@@ -36,8 +36,8 @@ def _rec_to_dict(rec):
             "st_f": rec["status_f"], "st_b": rec["status_b"]}
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_trace_seeds_charge_field(qsl, oracle_mod, mode):
+@pytest.mark.parametrize("mode,integ,tol", [(0, 0, GPU_TOL), (1, 0, GPU_TOL), (0, 2, GPU_TOL), (1, 2, GPU_TOL)])
+def test_trace_seeds_charge_field(qsl, oracle_mod, mode, integ, tol):
     ch = inputs.random_charges(4, 2)
     gf = inputs.charge_field(ch, 64, dtype=torch.float32)
     F = _gpu_field(qsl, gf, mode)
@@ -45,7 +45,7 @@ def test_trace_seeds_charge_field(qsl, oracle_mod, mode):
     seeds = inputs.random_seeds(600, 17)
     seeds[:150, 2] = 0.0     # footpoints on the bottom face
     seeds[150:160, 0] = 1.0  # on the x+ face
-    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL)
+    o = qsl.qsl_opts_default(tol_abs=tol, tol_rel=tol, integrator=integ)
     rec = qsl.lines_to_numpy(qsl.qsl_trace_seeds(F, torch.as_tensor(seeds).cuda(), o))
     ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
     g = _rec_to_dict(rec)
@@ -62,8 +62,8 @@ def test_trace_seeds_charge_field(qsl, oracle_mod, mode):
     assert np.allclose(rec_h["length"], rec["length"], rtol=1e-6)
 
 
-@pytest.mark.parametrize("mode", [1, 0])
-def test_config1_hyperbolic_map(qsl, oracle_mod, mode):
+@pytest.mark.parametrize("mode,integ,tol", [(1, 0, GPU_TOL), (0, 0, GPU_TOL), (1, 2, GPU_TOL), (0, 2, GPU_TOL)])
+def test_config1_hyperbolic_map(qsl, oracle_mod, mode, integ, tol):
     """The 256 x 256 map of the linear hyperbolic field on z = 0: raw mode
     against the closed forms (golden fixture), both modes against the oracle
     on a subsample that includes the 12 top-exit columns."""
@@ -74,7 +74,7 @@ def test_config1_hyperbolic_map(qsl, oracle_mod, mode):
     L = torch.empty(n * n, device="cuda")
     faces = torch.empty(2 * n * n, dtype=torch.uint8, device="cuda")
     st = torch.empty(n * n, dtype=torch.uint8, device="cuda")
-    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL, q_form=qsl.QSL_Q_FOOT)
+    o = qsl.qsl_opts_default(tol_abs=tol, tol_rel=tol, q_form=qsl.QSL_Q_FOOT, integrator=integ)
     qsl.qsl_q_map_2d(F, (0, 0, 0), (2, 0, 0), (0, 2, 0), n, n, o, q, L, faces, st)
     torch.cuda.synchronize()
     q, L, faces, st = q.cpu().numpy(), L.cpu().numpy(), faces.cpu().numpy().reshape(-1, 2), st.cpu().numpy()
@@ -96,7 +96,8 @@ def test_config1_hyperbolic_map(qsl, oracle_mod, mode):
     compare_lines(g, ref, 1.0 / 63, BOX_LO, BOX_HI, "q_foot", "q_foot")
 
 
-def test_volume_map_matches_oracle(qsl, oracle_mod):
+@pytest.mark.parametrize("integ,tol", [(0, GPU_TOL), (2, GPU_TOL)])
+def test_volume_map_matches_oracle(qsl, oracle_mod, integ, tol):
     ch = inputs.random_charges(8, 3)
     gf = inputs.charge_field(ch, 48, dtype=torch.float32)
     F = _gpu_field(qsl, gf, 0)
@@ -106,7 +107,7 @@ def test_volume_map_matches_oracle(qsl, oracle_mod):
     L = torch.empty(N, device="cuda")
     faces = torch.empty(2 * N, dtype=torch.uint8, device="cuda")
     st = torch.empty(N, dtype=torch.uint8, device="cuda")
-    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL)
+    o = qsl.qsl_opts_default(tol_abs=tol, tol_rel=tol, integrator=integ)
     qsl.qsl_q_volume_3d(F, BOX_LO, BOX_HI, nx, ny, nz, o, q, L, faces, st)
     torch.cuda.synchronize()
     Fo = _oracle_field(oracle_mod, gf, 0)
@@ -118,13 +119,14 @@ def test_volume_map_matches_oracle(qsl, oracle_mod):
     compare_lines(g, ref, 2.0 / 47, BOX_LO, BOX_HI)
 
 
-def test_fp64_precision_matches_oracle_tightly(qsl, oracle_mod):
+@pytest.mark.parametrize("integ", [0, 2])
+def test_fp64_precision_matches_oracle_tightly(qsl, oracle_mod, integ):
     ch = inputs.random_charges(4, 5)
     gf = inputs.charge_field(ch, 32, dtype=torch.float64)
     F = _gpu_field(qsl, gf, 1)
     Fo = _oracle_field(oracle_mod, gf, 1)
     seeds = inputs.random_seeds(200, 23)
-    o = qsl.qsl_opts_default(tol_abs=1e-10, tol_rel=1e-10, precision=qsl.QSL_FP64)
+    o = qsl.qsl_opts_default(tol_abs=1e-10, tol_rel=1e-10, precision=qsl.QSL_FP64, integrator=integ)
     rec = qsl.qsl_trace_seeds(F, seeds, o)
     ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
     # lengths are stored as float32 in the record: 3e-7 covers their rounding
