@@ -236,6 +236,29 @@ typedef struct qsl_samples {
 int qsl_refine(const qsl_field* field, const qsl_refine_spec* spec, const qsl_opts* opts, qsl_samples* samples,
                float* q_grid, float* l_grid, int mem, void* stream);
 
+/* ---- tracing without allocation -------------------------------------------------
+ * The paper has no counterpart to this entry point. It is qsl_trace_seeds for
+ * callers that cannot allocate device memory (a host-side allocator or fixed
+ * memory budget they must not bypass, or allocator state that must not change):
+ * it calls no cudaMalloc, cudaFree or allocating library routine. Its scratch
+ * (queue head and per-direction end records) is one file-scope device array of
+ * QSL_NOALLOC_SCRATCH_BYTES (7 MiB + 256 B) that every GPU loading this library
+ * holds until the process exits.
+ *  - seeds (S x 3 doubles) and out (S records) must be device memory of the
+ *    current device; 0 <= S <= QSL_NOALLOC_MAX_SEEDS, else QSL_EINVAL.
+ *  - FP32 tracing only (opts->precision must be QSL_FP32_MIXED, else
+ *    QSL_EINVAL); lines above retrace_q are not traced again in FP64 and
+ *    qsl_last_stats does not report this call.
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current); make it before any stream capture.
+ *  - Every call shares the one array: calls whose work overlaps on the GPU
+ *    (other streams, other host threads) race; serialise them.
+ *  - Asynchronous on `stream`. */
+#define QSL_NOALLOC_MAX_SEEDS 65536
+#define QSL_NOALLOC_SCRATCH_BYTES (256 + 56 * 2 * 65536)
+int qsl_trace_seeds_noalloc(const qsl_field* field, const double* seeds, int64_t S, const qsl_opts* opts,
+                            qsl_line* out, void* stream);
+
 /* Hilbert keys (Skilling's transpose method, curve starting at the origin) of
  * n cells with coords (n x ndim uint32, axis 0 first) at `bits` per axis
  * (ndim * bits <= 63), and the inverse. */

@@ -87,7 +87,7 @@ void resolve_config(const qsl_field* f, const qsl_opts* o, TraceConfig* c) {
   c->timeout_ns = o->timeout_s > 0 ? (unsigned long long)(o->timeout_s * 1e9) : 0ull;
 }
 
-static int validate_opts(const qsl_field* f, const qsl_opts* o) {
+int validate_opts(const qsl_field* f, const qsl_opts* o) {
   if (!f) QSL_FAIL(QSL_EINVAL, "field is NULL");
   if (!o) QSL_FAIL(QSL_EINVAL, "opts is NULL");
   if (o->integrator != QSL_RKCK54 && o->integrator != QSL_EULER && o->integrator != QSL_DOPRI5_CELL)

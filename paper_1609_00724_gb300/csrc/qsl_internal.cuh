@@ -126,6 +126,7 @@ int select_retrace(const SeedSource& src, int64_t n_seeds, const LineOutputs& ou
                    int64_t* index, int64_t* count_dev, cudaStream_t stream);
 
 void resolve_config(const qsl_field* f, const qsl_opts* o, TraceConfig* cfg);
+int validate_opts(const qsl_field* f, const qsl_opts* o);
 int default_shape(const qsl_opts* o, int tangent, int precision, LaunchShape* s);
 
 }  // namespace qsl

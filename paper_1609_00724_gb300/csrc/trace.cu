@@ -1379,19 +1379,23 @@ FieldView<double> make_view<double>(const qsl_field* f) {
   return v;
 }
 
+// Scratch of one tracing launch: the queue head and watchdog flag (16 bytes
+// at offset 0) and one end record per unit from offset 256. `scratch` is
+// either caller-provided (the no-allocation entry point) or allocated here.
 template <class R, int NC>
 int launch_trace(const qsl_field* f, const SeedSource& src, int64_t n_seeds, const int64_t* n_seeds_dev,
                  const TraceConfig& cfg, const LaunchShape& shape, const LineOutputs& out, cudaStream_t stream,
-                 DeviceStats* stats_dev, cudaEvent_t* ev) {
+                 DeviceStats* stats_dev, cudaEvent_t* ev, void* scratch = nullptr) {
   int dev = 0, sms = 0;
   QSL_CHECK_CUDA(cudaGetDevice(&dev));
   QSL_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  EndRec<R>* ends = nullptr;
-  unsigned long long* head = nullptr;
-  int* tflag = nullptr;
   size_t n_units = (size_t)(2 * n_seeds);
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&ends, sizeof(EndRec<R>) * (n_units ? n_units : 1), stream));
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&head, 16, stream));
+  const bool own = scratch == nullptr;
+  if (own)
+    QSL_CHECK_CUDA(cudaMallocAsync(&scratch, 256 + sizeof(EndRec<R>) * (n_units ? n_units : 1), stream));
+  unsigned long long* head = reinterpret_cast<unsigned long long*>(scratch);
+  EndRec<R>* ends = reinterpret_cast<EndRec<R>*>(reinterpret_cast<unsigned char*>(scratch) + 256);
+  int* tflag = nullptr;
   QSL_CHECK_CUDA(cudaMemsetAsync(head, 0, 16, stream));
   tflag = (int*)(head + 1);
   TraceParams<R> P;
@@ -1472,8 +1476,7 @@ int launch_trace(const qsl_field* f, const SeedSource& src, int64_t n_seeds, con
     assemble_kernel<R, S><<<ab, 128, 0, stream>>>(A);
     QSL_CHECK_CUDA(cudaGetLastError());
   }
-  QSL_CHECK_CUDA(cudaFreeAsync(ends, stream));
-  QSL_CHECK_CUDA(cudaFreeAsync(head, stream));
+  if (own) QSL_CHECK_CUDA(cudaFreeAsync(scratch, stream));
   return QSL_OK;
 }
 
@@ -1506,3 +1509,98 @@ int select_retrace(const SeedSource& src, int64_t n_seeds, const LineOutputs& ou
 }
 
 }  // namespace qsl
+
+// ---------------------------------------------------------------------------
+// Tracing without any allocation. Some callers cannot call cudaMalloc: code
+// that runs under a host-side allocator it must not bypass, inside a memory
+// budget fixed up front, or in a process whose allocator state must not
+// change. This variant of qsl_trace_seeds keeps its scratch (queue head and
+// per-direction end records) in one file-scope device array instead of
+// allocating it. The array is QSL_NOALLOC_SCRATCH_BYTES large and every GPU
+// that loads this library holds it until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoallocBytes = 256 + sizeof(qsl::EndRec<float>) * 2 * (size_t)QSL_NOALLOC_MAX_SEEDS;
+static_assert(kNoallocBytes == QSL_NOALLOC_SCRATCH_BYTES, "scratch size must match qsl.h");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// Host code may not use the name of a __device__ array as a device address:
+// it names a host-side stand-in. The device address is looked up once per
+// device, with that device current, and kept here.
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  QSL_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    qsl::set_error("device %d out of range for the no-allocation scratch", dev);
+    return QSL_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      qsl::set_error("cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
+      return QSL_ECUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return QSL_OK;
+}
+
+}  // namespace
+
+extern "C" int qsl_trace_seeds_noalloc(const qsl_field* f, const double* seeds, int64_t S, const qsl_opts* o,
+                                       qsl_line* out, void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  int rc = qsl::validate_opts(f, o);
+  if (rc) return rc;
+  if (S < 0 || S > QSL_NOALLOC_MAX_SEEDS) {
+    qsl::set_error("S = %lld is outside 0..%d, the no-allocation limit of qsl_trace_seeds_noalloc", (long long)S,
+                   QSL_NOALLOC_MAX_SEEDS);
+    return QSL_EINVAL;
+  }
+  if (o->precision != QSL_FP32_MIXED) {
+    qsl::set_error("qsl_trace_seeds_noalloc traces in FP32 only (opts.precision must be QSL_FP32_MIXED)");
+    return QSL_EINVAL;
+  }
+  if (S > 0 && (!seeds || !out)) {
+    qsl::set_error("seeds/out is NULL");
+    return QSL_EINVAL;
+  }
+  const void* ptrs[2] = {seeds, out};
+  for (int i = 0; i < 2 && S > 0; ++i) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptrs[i]);
+    if (e != cudaSuccess || (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      qsl::set_error("qsl_trace_seeds_noalloc needs device pointers for seeds and out");
+      return QSL_EINVAL;
+    }
+  }
+  void* scratch = nullptr;
+  if ((rc = noalloc_scratch(&scratch))) return rc;
+  qsl::TraceConfig cfg;
+  qsl::resolve_config(f, o, &cfg);
+  qsl::LaunchShape shape;
+  qsl::default_shape(o, !o->length_only, QSL_FP32_MIXED, &shape);
+  qsl::SeedSource src{};
+  src.kind = qsl::SEEDS_ARRAY;
+  src.xyz = seeds;
+  qsl::LineOutputs lo{};
+  lo.lines = out;
+  lo.q_form = QSL_Q_PERP;
+  lo.skip_open = o->skip_open;
+  if (S == 0) return QSL_OK;
+  if (cfg.length_only)
+    return qsl::launch_trace<float, 3>(f, src, S, nullptr, cfg, shape, lo, stream, nullptr, nullptr, scratch);
+  return qsl::launch_trace<float, 9>(f, src, S, nullptr, cfg, shape, lo, stream, nullptr, nullptr, scratch);
+}

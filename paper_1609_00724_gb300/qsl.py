@@ -97,6 +97,7 @@ def lib():
     L.qsl_hilbert_decode.argtypes = [vp, i64, i32, i32, vp, i32, vp]
     L.qsl_convert.argtypes = [vp, vp, i64, i32, i32, vp, i32, i32, vp, i32, vp]
     L.qsl_last_stats.argtypes = [C.POINTER(qsl_stats)]
+    L.qsl_trace_seeds_noalloc.argtypes = [vp, vp, i64, C.POINTER(qsl_opts), vp, vp]
     _lib = L
     return L
 
@@ -198,6 +199,17 @@ def qsl_trace_seeds(field, seeds, opts, out=None, stream=None):
     return out
 
 
+QSL_NOALLOC_MAX_SEEDS = 65536
+
+
+def qsl_trace_seeds_noalloc(field, seeds, opts, out, stream=None):
+    """Allocation-free variant of qsl_trace_seeds: seeds (S x 3 float64) and
+    out (S * 112 bytes) must be CUDA tensors; S <= QSL_NOALLOC_MAX_SEEDS."""
+    _check(lib().qsl_trace_seeds_noalloc(field.handle, _ptr(seeds), seeds.shape[0], C.byref(opts), _ptr(out),
+                                         _stream(stream)))
+    return out
+
+
 def lines_to_numpy(raw):
     """Device qsl_line bytes (torch uint8) -> numpy record array."""
     return np.frombuffer(raw.cpu().numpy().tobytes(), dtype=QSL_LINE_DTYPE)
@@ -284,4 +296,4 @@ def qsl_last_stats():
 
 EXPORTS = ["qsl_opts_default", "qsl_load_field", "qsl_free_field", "qsl_trace_seeds", "qsl_q_map_2d",
            "qsl_q_volume_3d", "qsl_fledge", "qsl_refine", "qsl_hilbert_encode", "qsl_hilbert_decode", "qsl_convert",
-           "qsl_last_error", "qsl_last_stats"]
+           "qsl_last_error", "qsl_last_stats", "qsl_trace_seeds_noalloc"]
