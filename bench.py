@@ -36,11 +36,14 @@ TOL = 1e-7
 FIELD_SEED = 2
 
 # Algorithmic FP32 work of one RK stage evaluation in the tangent tracer
-# (paper mode): trilinear value + gradient of 3 components (99 FLOP), cell
-# location (9), gradient scaling (9), deviation right-hand sides (30), the
-# stage's share of the Cash-Karp combinations, error norm and controller
-# (99); an FMA counts as 2 FLOP.
-FLOP_PER_STAGE = 246.0
+# (paper mode, an FMA counts as 2 FLOP). Cash-Karp kernel: trilinear value +
+# gradient of 3 components (99), cell location (9), gradient scaling (9),
+# deviation right-hand sides (30), the stage's share of the combinations,
+# error norm and controller (99). Cell-wise Dormand-Prince kernel: trilinear
+# value + gradient (99), scaling (12), deviation right-hand sides (30), the
+# stage's share of the combinations (414 per step) and error norm (144 per
+# step) over 6.5 evaluations per step (85).
+FLOP_PER_STAGE = {"ck": 246.0, "cell": 227.0}
 # FP32 peak of the FMA pipe: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -214,7 +217,8 @@ def parity_sample(qsl, gf, gf_cpu, coarse, n=200):
     fg = fc.cpu().numpy().reshape(-1, 2)[idx]
     ok = np.isfinite(ref["q_perp"]) & (ref["q_perp"] < 1e6)
     qe = np.abs(qg[ok] / ref["q_perp"][ok] - 1)
-    le = np.abs(lg / ref["L"] - 1)[ref["L"] > 0]
+    pos = ref["L"] > 0
+    le = np.abs(lg[pos] / ref["L"][pos] - 1)
     faces_eq = float(np.mean((fg[:, 0] == ref["face_f"]) & (fg[:, 1] == ref["face_b"])))
     return {"n": int(n), "q_max_rel": float(qe.max()), "q_p99_rel": float(np.quantile(qe, 0.99)),
             "l_max_rel": float(le.max()), "faces_equal": faces_eq}
@@ -301,6 +305,7 @@ def main():
     stage_evals = 0
     info = {}
     barrier()
+    launches0 = qsl.qsl_kernel_launches()
     with ClockSampler(local) as clk:
         start.record()
         for _ in range(args.steps):
@@ -309,6 +314,7 @@ def main():
         end.record()
         barrier()
     ms = start.elapsed_time(end)
+    launches = qsl.qsl_kernel_launches() - launches0
     t = torch.tensor([ms], device=dev)
     n_units = torch.tensor([float(traced_total)], device=dev)
     if world > 1:
@@ -327,7 +333,8 @@ def main():
         qsl.qsl_q_map_2d(F, (0, 0, 0), (2, 0, 0), (0, 2, 0), args.coarse, args.coarse, opts(qsl), q=qm, length=Lm)
     st = qsl.qsl_last_stats()
     kms = st["kernel_ms"]
-    achieved_tflops = st["stage_evals"] * FLOP_PER_STAGE / (kms / 1000.0) / 1e12
+    flop_per_stage = FLOP_PER_STAGE[RUN["integrator"]]
+    achieved_tflops = st["stage_evals"] * flop_per_stage / (kms / 1000.0) / 1e12
 
     # --- end to end through the C ABI with host buffers (pinned), copies inside
     eff = args.coarse << (P - P0)
@@ -360,11 +367,14 @@ def main():
                        "q_points_per_step": traced_total // max(args.steps, 1)},
             "clocks": clk.summary(),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": None,
+            "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "trace_kernel<float,9> (1024^2 coarse map)", "kernel_ms": kms,
-                         "stage_evals": st["stage_evals"], "peak_note": "FP32 FMA pipe at 2.07 GHz (derived)"}}
+                         "kernel": ("cell_kernel<float,9>" if RUN["integrator"] == "cell" else "trace_kernel<float,9>")
+                         + " (%d^2 coarse map)" % args.coarse, "kernel_ms": kms,
+                         "stage_evals": st["stage_evals"], "accepted": st["accepted"], "rejected": st["rejected"],
+                         "landings": st["landing"], "flop_per_stage": flop_per_stage,
+                         "peak_note": "FP32 FMA pipe at 2.07 GHz (derived from unit counts)"}}
     if rank == 0 and not args.no_cpu_baseline:
         gf_cpu = make_field(field_seed, "cpu", args.grid)
         rate, nseeds, cores, secs = oracle_sample_rate(gf_cpu, args.coarse)

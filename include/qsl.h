@@ -272,6 +272,11 @@ int qsl_hilbert_decode(const uint64_t* keys, int64_t n, int ndim, int bits, uint
 int qsl_convert(const uint64_t* keys, const float* vals, int64_t n, int ndim, int max_order, const int32_t* extent,
                 int out_order, int log_interp, float* out, int mem, void* stream);
 
+/* Kernels of this library launched by this process since the library was
+ * loaded (all threads). Radix sorts and scans inside qsl_refine run CUB
+ * kernels, which are not counted. */
+int64_t qsl_kernel_launches(void);
+
 /* Human-readable message of the last failing call on this thread. */
 const char* qsl_last_error(void);
 

@@ -11,6 +11,7 @@
 namespace qsl {
 
 static thread_local std::string g_err;
+std::atomic<long long> g_launches{0};
 
 void set_error(const char* fmt, ...) {
   char buf[1024];
@@ -145,6 +146,8 @@ extern "C" {
 
 const char* qsl_last_error(void) { return g_err.c_str(); }
 
+int64_t qsl_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
 void qsl_opts_default(qsl_opts* o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));
@@ -262,6 +265,7 @@ int qsl_load_field(const void* bx, const void* by, const void* bz, int dtype, in
     pack_kernel<double><<<blocks, 256, 0, stream>>>((const double*)p[0], (const double*)p[1],
                                                     (const double*)p[2], N, interp_mode == QSL_RAW_B, f->v32,
                                                     f->v64, bad);
+  qsl::count_launch();
   TRY(cudaGetLastError());
   TRY(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
   TRY(cudaStreamSynchronize(stream));

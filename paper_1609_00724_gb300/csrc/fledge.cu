@@ -129,15 +129,18 @@ int fledge_device(const float* L, int ndim, const int64_t* shape, float* S, cuda
   if (n > 0) {
     int b = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
     max_finite_kernel<<<b, 256, 0, stream>>>(L, n, fill);
+    qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
     if (ndim == 2) {
       dim3 grid((unsigned)((shape[1] + TX2 - 1) / TX2), (unsigned)((shape[0] + TY2 - 1) / TY2));
       sobel2d_kernel<<<grid, dim3(TX2, TY2), 0, stream>>>(L, (int)shape[0], (int)shape[1], fill, S);
+      qsl::count_launch();
     } else {
       dim3 grid((unsigned)((shape[2] + TX3 - 1) / TX3), (unsigned)((shape[1] + TY3 - 1) / TY3),
                 (unsigned)((shape[0] + TZ3 - 1) / TZ3));
       sobel3d_kernel<<<grid, dim3(TX3, TY3), 0, stream>>>(L, (int)shape[0], (int)shape[1], (int)shape[2], fill,
                                                          S);
+                                                         qsl::count_launch();
     }
     QSL_CHECK_CUDA(cudaGetLastError());
   }

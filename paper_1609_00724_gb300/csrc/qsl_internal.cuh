@@ -8,7 +8,13 @@
 
 #include "../../include/qsl.h"
 
+#include <atomic>
+
 namespace qsl {
+
+// Number of this library's kernel launches since load (qsl_kernel_launches).
+extern std::atomic<long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- errors
 void set_error(const char* fmt, ...);

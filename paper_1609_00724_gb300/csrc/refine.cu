@@ -334,6 +334,7 @@ int convert_device(const uint64_t* keys, const float* vals, int64_t n, int nd, i
   int64_t N = (int64_t)eo[0] * eo[1] * eo[2];
   if (N > 0) {
     convert_kernel<<<grid_for(N), 256, 0, s>>>(keys, vals, n, nd, p, d, eo[0], eo[1], eo[2], log_interp, out);
+    qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
   }
   return QSL_OK;
@@ -409,10 +410,12 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
     traced += m;
     int64_t tot = off + m;
     iota_kernel<<<grid_for(tot), 256, 0, s>>>(perm, tot);
+    qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
     if ((r = sort_pairs(smp->key, kA, perm, perm2, tot, nd * p, s))) return r;
     gather_kernel<<<grid_for(tot), 256, 0, s>>>(perm2, tot, smp->q, smp->length, smp->faces, smp->status, q2, L2,
                                                 fa2, st2);
+                                                qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
     QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, kA, tot * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     QSL_CHECK_CUDA(cudaMemcpyAsync(smp->q, q2, tot * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -427,10 +430,12 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
     *added = 0;
     if (m <= 0) return QSL_OK;
     cand_flags_kernel<<<grid_for(m), 256, 0, s>>>(cand, m, flags);
+    qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
     int r = exclusive_sum(flags, pos, m, s);
     if (r) return r;
     cand_scatter_kernel<<<grid_for(m), 256, 0, s>>>(cand, pos, m, cap - n, smp->key + n, cnt);
+    qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
     QSL_CHECK_CUDA(cudaMemcpyAsync(cnt_h, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     QSL_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -453,9 +458,11 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
       return QSL_ECAPACITY;
     }
     coarse_keys_kernel<<<grid_for(m), 256, 0, s>>>(m, nd, p, R, nc[0], nc[1], smp->key);
+    qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
     // trace in curve order (neighbouring seeds on neighbouring lanes)
     iota_kernel<<<grid_for(m), 256, 0, s>>>(perm, m);
+    qsl::count_launch();
     if ((rc = sort_pairs(smp->key, kA, perm, perm2, m, nd * p, s))) return rc;
     QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, kA, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     if ((rc = trace_and_merge(0, m))) return rc;
@@ -473,6 +480,7 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
       if ((rc = sc.alloc(&cells, m))) return rc;
       QSL_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t), s));
       mask_cells_kernel<<<grid_for(m), 256, 0, s>>>(mask, m, cells, cnt);
+      qsl::count_launch();
       QSL_CHECK_CUDA(cudaMemcpyAsync(cnt_h, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
       QSL_CHECK_CUDA(cudaStreamSynchronize(s));
       int64_t ncells = *cnt_h;
@@ -489,6 +497,7 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
       QSL_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t), s));
       if (want > 0) {
         proposal_keys_kernel<<<grid_for(want), 256, 0, s>>>(cells, ncd, nd, p, R, nc[0], nc[1], smp->key + n, cnt);
+        qsl::count_launch();
         QSL_CHECK_CUDA(cudaGetLastError());
         if ((rc = trace_and_merge(n, want))) return rc;
         n += want;
@@ -502,6 +511,7 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
     // (A) along the curve
     if (n > 1) {
       flag_pairs_kernel<<<grid_for(n - 1), 256, 0, s>>>(smp->key, smp->length, n, sp->tau, nd, p, reg, cand);
+      qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((rc = compact(n - 1, &added))) return rc;
       if ((rc = trace_and_merge(n, added))) return rc;
@@ -514,6 +524,7 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
       uint32_t dsh = (uint32_t)(R / 2 > 1 ? R / 2 : 1);
       uint32_t S = (it % 2 == 0) ? half + dsh : half - (dsh < half ? dsh : half);
       shift_keys_kernel<<<grid_for(n), 256, 0, s>>>(smp->key, n, nd, p, S, sk, perm);
+      qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((rc = sort_pairs(sk, sk2, perm, perm2, n, nd * (p + 1), s))) return rc;
       Region sreg;
@@ -522,6 +533,7 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
         sreg.hi[a] = reg.hi[a] + (a < nd ? S : 0);
       }
       flag_shifted_kernel<<<grid_for(n - 1), 256, 0, s>>>(sk2, perm2, smp->length, n, sp->tau, nd, p, S, sreg, cand);
+      qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((rc = compact(n - 1, &added))) return rc;
       if ((rc = trace_and_merge(n, added))) return rc;
@@ -569,6 +581,7 @@ int qsl_hilbert_encode(const uint32_t* coords, int64_t n, int ndim, int bits, ui
     QSL_CHECK_CUDA(cudaMemcpyAsync((void*)c, coords, n * ndim * 4, cudaMemcpyHostToDevice, s));
   }
   encode_kernel<<<grid_for(n), 256, 0, s>>>(c, n, ndim, bits, k);
+  qsl::count_launch();
   QSL_CHECK_CUDA(cudaGetLastError());
   if (mem == QSL_MEM_HOST) {
     QSL_CHECK_CUDA(cudaMemcpyAsync(keys, k, n * 8, cudaMemcpyDeviceToHost, s));
@@ -599,6 +612,7 @@ int qsl_hilbert_decode(const uint64_t* keys, int64_t n, int ndim, int bits, uint
     QSL_CHECK_CUDA(cudaMemcpyAsync((void*)k, keys, n * 8, cudaMemcpyHostToDevice, s));
   }
   decode_kernel<<<grid_for(n), 256, 0, s>>>(k, n, ndim, bits, c);
+  qsl::count_launch();
   QSL_CHECK_CUDA(cudaGetLastError());
   if (mem == QSL_MEM_HOST) {
     QSL_CHECK_CUDA(cudaMemcpyAsync(coords, c, n * ndim * 4, cudaMemcpyDeviceToHost, s));

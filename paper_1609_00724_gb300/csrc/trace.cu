@@ -1452,10 +1452,13 @@ int launch_trace(const qsl_field* f, const SeedSource& src, int64_t n_seeds, con
   if (n_seeds > 0) {
     if (use_cell) {
       cell_kernel<R, NC><<<blocks, threads, smem, stream>>>(P);
+      qsl::count_launch();
     } else if (loc) {
       trace_kernel<R, NC, true><<<blocks, threads, 0, stream>>>(P);
+      qsl::count_launch();
     } else {
       trace_kernel<R, NC, false><<<blocks, threads, 0, stream>>>(P);
+      qsl::count_launch();
     }
     QSL_CHECK_CUDA(cudaGetLastError());
   }
@@ -1474,6 +1477,7 @@ int launch_trace(const qsl_field* f, const SeedSource& src, int64_t n_seeds, con
     int ab = (int)((n_seeds + 127) / 128);
     if (ab > sms * 16) ab = sms * 16;
     assemble_kernel<R, S><<<ab, 128, 0, stream>>>(A);
+    qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
   }
   if (own) QSL_CHECK_CUDA(cudaFreeAsync(scratch, stream));
@@ -1504,6 +1508,7 @@ int select_retrace(const SeedSource& src, int64_t n_seeds, const LineOutputs& ou
   int blocks = (int)((n_seeds + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   select_kernel<<<blocks, 256, 0, stream>>>(n_seeds, out.q, out.lines, out.q_form, threshold, index, count_dev);
+  qsl::count_launch();
   QSL_CHECK_CUDA(cudaGetLastError());
   return QSL_OK;
 }

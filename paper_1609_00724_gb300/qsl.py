@@ -97,6 +97,7 @@ def lib():
     L.qsl_hilbert_decode.argtypes = [vp, i64, i32, i32, vp, i32, vp]
     L.qsl_convert.argtypes = [vp, vp, i64, i32, i32, vp, i32, i32, vp, i32, vp]
     L.qsl_last_stats.argtypes = [C.POINTER(qsl_stats)]
+    L.qsl_kernel_launches.restype = C.c_int64
     L.qsl_trace_seeds_noalloc.argtypes = [vp, vp, i64, C.POINTER(qsl_opts), vp, vp]
     _lib = L
     return L
@@ -288,6 +289,10 @@ def qsl_convert(keys, vals, ndim, max_order, extent, out_order, log_interp, out,
                              _stream(stream)))
 
 
+def qsl_kernel_launches():
+    return int(lib().qsl_kernel_launches())
+
+
 def qsl_last_stats():
     s = qsl_stats()
     _check(lib().qsl_last_stats(C.byref(s)))
@@ -296,4 +301,4 @@ def qsl_last_stats():
 
 EXPORTS = ["qsl_opts_default", "qsl_load_field", "qsl_free_field", "qsl_trace_seeds", "qsl_q_map_2d",
            "qsl_q_volume_3d", "qsl_fledge", "qsl_refine", "qsl_hilbert_encode", "qsl_hilbert_decode", "qsl_convert",
-           "qsl_last_error", "qsl_last_stats", "qsl_trace_seeds_noalloc"]
+           "qsl_last_error", "qsl_last_stats", "qsl_trace_seeds_noalloc", "qsl_kernel_launches"]
