@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--integrator", default="cell", choices=["cell", "ck"],
                     help="cell: cell-wise Dormand-Prince (default); ck: the paper's plain Cash-Karp")
     ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--config", default="refine2d", choices=["refine2d", "volume", "batch64"],
+                    help="refine2d: 1024^2 map refined to 4096^2 (default); volume: 512x512x256 Q/FLL/FLEDGE volume "
+                         "of an 8-charge field on 384^3")
     ap.add_argument("--profile-map", action="store_true",
                     help="only run the coarse Q map (the tracer kernel) --steps times, for ncu captures")
     return ap.parse_args()
@@ -261,6 +264,122 @@ def run_reference(args, rank, world):
     del torch
 
 
+def run_volume(args, qsl, torch, dev, rank, world, local):
+    """Config 3: 8 charges on 384^3 (FP32); one step = Q/FLL at 512x512x256
+    cell-centre seeds (FP32 trace, FP64 assembly, FP64 retrace above 1e6) and
+    the 3D FLEDGE of the length volume."""
+    from paper_1609_00724_gb300 import inputs
+    ch = inputs.random_charges(8, 3 + 1000 * rank)
+    gf = inputs.charge_field(ch, 384, dtype=torch.float32, device=dev, slab=32)
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
+    nx, ny, nz = 512, 512, 256
+    N = nx * ny * nz
+    q = torch.empty(N, device=dev)
+    L = torch.empty(N, device=dev)
+    S = torch.empty((nz, ny, nx), device=dev)
+    lo, hi = (-1.0, -1.0, 0.0), (1.0, 1.0, 1.0)
+
+    def step():
+        qsl.qsl_q_volume_3d(F, lo, hi, nx, ny, nz, opts(qsl), q=q, length=L)
+        qsl.qsl_fledge(L.view(nz, ny, nx), S)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    l0 = qsl.qsl_kernel_launches()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record()
+        for _ in range(args.steps):
+            step()
+        end.record()
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    st = qsl.qsl_last_stats()
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * N * args.steps / (ms_max / 1000.0)
+    fps = FLOP_PER_STAGE[RUN["integrator"]]
+    ach = st["stage_evals"] * fps / (st["kernel_ms"] / 1000.0) / 1e12
+    line = {"metric": "Q-points/s (3D Q/FLL/FLEDGE volume)", "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "8-charge potential field 384^3 FP32, 512x512x256 volume Q/FLL + 3D FLEDGE",
+                       "tol": RUN["tol"], "integrator": RUN["integrator"], "retraced_last_step": st["retraced"],
+                       "l2": "inputs larger than L2 (906 MB packed field)"},
+            "clocks": clk.summary(), "gpu_launches": qsl.qsl_kernel_launches() - l0,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "kernel_ms": st["kernel_ms"],
+                         "stage_evals": st["stage_evals"]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_batch(args, qsl, torch, dev, rank, world, local):
+    """Config 4: 64 independently seeded 4-charge fields, grid edge n ~ U{64..256},
+    each with a z=0 cut of m x m seeds, m ~ U{256..1024} (field i: seed
+    4000 + i); all cuts in one persistent launch recorded into a CUDA graph
+    (plan), with the launch shape and tolerance picked by the autotuner on a
+    sample of the first cut."""
+    from paper_1609_00724_gb300 import inputs
+    rng = np.random.Generator(np.random.PCG64(4 + 1000 * rank))
+    items, fields = [], []
+    for i in range(64):
+        n = int(rng.integers(64, 257))
+        m = int(rng.integers(256, 1025))
+        gf = inputs.charge_field(inputs.random_charges(4, 4000 + i + 1000 * rank), n, dtype=torch.float32,
+                                 device=dev, slab=64)
+        F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
+        del gf
+        fields.append(F)
+        items.append((F, (0, 0, 0), (2, 0, 0), (0, 2, 0), m, m))
+    N = sum(it[4] * it[5] for it in items)
+    o = opts(qsl)
+    # autotune on 131072 seeds of the first cut (several waves of the GPU)
+    m0 = items[0][4]
+    pick = inputs.subsample(m0 * m0, 131072, 17)
+    ii, jj = pick % m0, pick // m0
+    sd = np.column_stack([-1 + (ii + 0.5) * 2 / m0, -1 + (jj + 0.5) * 2 / m0, np.zeros(len(pick))])
+    rep = qsl.qsl_autotune(items[0][0], torch.as_tensor(sd).to(dev), o)
+    q = torch.empty(N, device=dev)
+    L = torch.empty(N, device=dev)
+    plan = qsl.Plan(items, o, q=q, length=L)
+    for _ in range(max(args.warmup, 3)):
+        plan.launch()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    l0 = qsl.qsl_kernel_launches()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        start.record()
+        for _ in range(args.steps):
+            plan.launch()
+        end.record()
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    st = plan.stats()
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * N * args.steps / (ms_max / 1000.0)
+    line = {"metric": "Q-points/s (64-field batch, one captured persistent launch)", "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 4-charge fields, n~U{64..256}^3, cuts m~U{256..1024}^2, %d seeds" % N,
+                       "integrator": RUN["integrator"], "autotune": rep,
+                       "l2": "inputs larger than L2 (%d packed fields)" % len(items)},
+            "clocks": clk.summary(), "gpu_launches": qsl.qsl_kernel_launches() - l0,
+            "stats_last_replay": st}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     RUN["integrator"] = args.integrator
@@ -277,6 +396,11 @@ def main():
     dev = torch.device("cuda", local)
     from paper_1609_00724_gb300 import qsl
     qsl.lib()
+    if args.config in ("volume", "batch64"):
+        (run_volume if args.config == "volume" else run_batch)(args, qsl, torch, dev, rank, world, local)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     field_seed = FIELD_SEED + 1000 * rank
     gf = make_field(field_seed, dev, args.grid)
     if args.profile_map:

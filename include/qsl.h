@@ -236,6 +236,62 @@ typedef struct qsl_samples {
 int qsl_refine(const qsl_field* field, const qsl_refine_spec* spec, const qsl_opts* opts, qsl_samples* samples,
                float* q_grid, float* l_grid, int mem, void* stream);
 
+/* ---- batches of fields and cuts: one persistent launch, captured plans ---------
+ * Many planar cuts of many fields (each its own grid size) traced in one
+ * persistent launch: the work queue spans all items, so uneven line lengths
+ * and unequal items share the GPU. Item k's pixels are written at offset
+ * sum_{i<k} nu_i*nv_i of the outputs (items concatenated in order, pixel
+ * layout as qsl_q_map_2d). Mixed uniform and rectilinear fields trace with
+ * QSL_RKCK54. */
+typedef struct qsl_batch_item {
+  const qsl_field* field;
+  double center[3], u[3], v[3]; /* planar cut, as qsl_q_map_2d */
+  int32_t nu, nv;
+} qsl_batch_item;
+
+/* One-shot batch: device outputs only (mem must be QSL_MEM_DEVICE). Returns
+ * after the work completes. */
+int qsl_q_map_batch(const qsl_batch_item* items, int n_items, const qsl_opts* opts, float* q, float* length,
+                    uint8_t* faces, uint8_t* status, int mem, void* stream);
+
+/* Plans: the batch (trace, FP64 assembly, selection and FP64 retrace of lines
+ * above retrace_q with a device-side count) recorded once into a CUDA graph
+ * with all scratch owned by the plan; qsl_plan_launch replays it on `stream`
+ * with no allocation and no host synchronisation. Outputs (device memory) are
+ * fixed at plan time; the fields must outlive the plan. */
+typedef struct qsl_plan qsl_plan;
+int qsl_plan_q_map_batch(const qsl_batch_item* items, int n_items, const qsl_opts* opts, float* q, float* length,
+                         uint8_t* faces, uint8_t* status, qsl_plan** out);
+int qsl_plan_launch(qsl_plan* plan, void* stream);
+/* Synchronises `stream` and copies the counters of the plan's last replay. */
+int qsl_plan_stats(qsl_plan* plan, void* stream, qsl_stats* out);
+void qsl_plan_free(qsl_plan* plan);
+
+/* ---- autotuner -----------------------------------------------------------------
+ * Picks, on a sample of S seeds (device memory, S >= 1) of the caller's
+ * workload:
+ *  - the loosest tolerance in {1e-5, 1e-6, 1e-7, 1e-8} whose Q (relative error
+ *    <= 2e-4 for Q < 1e6), lengths (<= 2e-6) and end faces (<= 0.1 % of lines
+ *    differ) agree with an FP64 trace of the same seeds at tol 1e-10 (a fifth
+ *    of the 1e-3 / 1e-5 accuracy bar);
+ *  - the fastest launch shape (warps per block 2/4/8, blocks per SM at most
+ *    2 or as many as fit, refill threshold 1/8) at that tolerance, timed with
+ *    CUDA events on `stream`.
+ * Writes the choice into *opts (tol_abs = tol_rel, warps_per_block,
+ * blocks_per_sm, refill_min) and into *report (optional). The result is cached
+ * per (grid size, interpolation mode, integrator, q_form, length_only, input
+ * tolerance); a cached call does no GPU work. Synchronous. */
+typedef struct qsl_tune_report {
+  int32_t warps_per_block, blocks_per_sm, refill_min, cached;
+  double tol;            /* chosen tolerance                                  */
+  double q_err, l_err;   /* worst relative errors at that tolerance           */
+  double face_mismatch;  /* fraction of sample lines with different end faces */
+  double sample_ms;      /* time of the chosen shape on the sample            */
+  int64_t sample_seeds;
+} qsl_tune_report;
+int qsl_autotune(const qsl_field* field, const double* seeds, int64_t S, qsl_opts* opts, qsl_tune_report* report,
+                 void* stream);
+
 /* ---- tracing without allocation -------------------------------------------------
  * The paper has no counterpart to this entry point. It is qsl_trace_seeds for
  * callers that cannot allocate device memory (a host-side allocator or fixed

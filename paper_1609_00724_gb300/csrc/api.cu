@@ -322,13 +322,11 @@ int run_lines(const qsl_field* f, const SeedSource& src, int64_t S, const qsl_op
     QSL_CHECK_CUDA(cudaMallocAsync((void**)&count, sizeof(int64_t), stream));
     rc = select_retrace(src, S, out, o->retrace_q, index, count, stream);
     if (rc) return rc;
-    SeedSource s2 = src;
-    s2.index = index;
     LineOutputs o2 = out;
     o2.retraced = 1;
     LaunchShape sh2;
     default_shape(o, 1, QSL_FP64, &sh2);
-    rc = trace_and_assemble(f, s2, S, count, cfg, QSL_FP64, sh2, o2, stream, g_last.dev, &g_last.ev[2]);
+    rc = trace_and_assemble(f, src, S, count, cfg, QSL_FP64, sh2, o2, stream, g_last.dev, &g_last.ev[2], index);
     if (rc) return rc;
     g_last.n_ev = 4;
     QSL_CHECK_CUDA(cudaMemcpyAsync(g_last.retraced_host, count, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));

@@ -79,7 +79,6 @@ struct SeedSource {
   double c[3], u[3], v[3];  // plane: centre + axes; volume/keys3: lo (c) and hi (u)
   const double* xyz;        // SEEDS_ARRAY: S x 3
   const uint64_t* keys;     // SEEDS_KEYS*: Hilbert keys
-  const int64_t* index;     // optional: local seed j -> global seed index[j]
 };
 
 // Outputs of the assembly step (each optional).
@@ -121,10 +120,15 @@ struct LaunchShape {
 // Runs the tracer over `n_seeds` seeds of `src` (n_seeds may live on the
 // device: `n_seeds_dev` != nullptr overrides n_seeds as an upper bound), then
 // assembles Q/FLL into `out`. Precision: 0 = FP32 trace, 1 = FP64 trace.
-// ev (optional): two events recorded around the tracer kernel.
+// ev (optional): two events recorded around the tracer kernel. index
+// (optional, device): launch seed j traces seed index[j] (FP64 retrace lists).
+// scratch (optional, device): 256 + end_record_bytes(precision) * 2 * n_seeds
+// bytes of caller memory; allocated per call when null.
 int trace_and_assemble(const qsl_field* f, const SeedSource& src, int64_t n_seeds, const int64_t* n_seeds_dev,
                        const TraceConfig& cfg, int precision, const LaunchShape& shape, const LineOutputs& out,
-                       cudaStream_t stream, DeviceStats* stats_dev, cudaEvent_t* ev);
+                       cudaStream_t stream, DeviceStats* stats_dev, cudaEvent_t* ev, const int64_t* index = nullptr,
+                       void* scratch = nullptr);
+size_t end_record_bytes(int precision);
 
 // Selects seeds whose chosen Q exceeds `threshold` (or is not finite while
 // L is) into `index` (device), count into count_dev (device).

@@ -295,9 +295,7 @@ __device__ __forceinline__ void seed_position(const SeedSource& s, int64_t g, do
   }
 }
 
-__device__ __forceinline__ void seed_of(const SeedSource& s, int64_t j, int64_t* g, double* x) {
-  int64_t gi = s.index ? s.index[j] : j;
-  *g = gi;
+__device__ __forceinline__ void seed_of(const SeedSource& s, int64_t gi, double* x) {
   if (s.kind == SEEDS_KEYS2 || s.kind == SEEDS_KEYS3) {
     int nd = (s.kind == SEEDS_KEYS2) ? 2 : 3;
     uint32_t c[3] = {0, 0, 0};
@@ -321,24 +319,55 @@ struct EndRec {
   int32_t face, status, steps, pad;
 };
 
+// One problem of a launch: a field, its tracing domain and step scales, and
+// where its seeds come from. Single-problem launches carry one inline item;
+// batch launches (many fields and cuts in one persistent launch) a table.
 template <class R>
-struct TraceParams {
+struct Item {
   FieldView<R> F;
   SeedSource src;
+  R lo[3], hi[3];              // domain bounds: domain units (global frame) or grid-index units (local frame)
+  double lo_d[3], hi_d[3];     // domain bounds in domain units
+  R max_len, h_init, h_max, h_min, euler_h, land_tol;  // domain units
+  int64_t seed_start;          // global id of the item's first seed (outputs are concatenated in item order)
+};
+
+template <class R>
+struct TraceParams {
+  Item<R> item0;               // the problem of a single-problem launch
+  const Item<R>* items;        // batch launches: device table sorted by seed_start, else nullptr
+  int n_items;
+  const int64_t* index;        // optional: unit seed j -> global seed id index[j] (FP64 retrace lists)
   int64_t n_units;             // 2 x seeds
   const int64_t* n_seeds_dev;  // optional device count of seeds
   EndRec<R>* ends;
   unsigned long long* head;
   DeviceStats* stats;
-  R lo[3], hi[3];              // domain bounds: domain units (global frame) or grid-index units (local frame)
-  double lo_d[3], hi_d[3];     // domain bounds in domain units
-  R max_len, tol_abs, tol_rel, h_init, h_max, h_min, euler_h, land_tol;
+  R tol_abs, tol_rel;
   long long max_steps;
   int euler;
   int refill_min;
   unsigned long long timeout_ns;  // per-warp watchdog, 0 = none
   int* timeout_flag;
 };
+
+// Problem and seed of launch seed j: global id, item, position.
+template <class R>
+__device__ __forceinline__ const Item<R>* resolve_seed(const TraceParams<R>& P, int64_t j, int64_t* g, double* x) {
+  int64_t s = P.index ? P.index[j] : j;
+  const Item<R>* E = &P.item0;
+  if (P.items) {
+    int lo = 0, hi = P.n_items - 1;  // last item with seed_start <= s
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (P.items[mid].seed_start <= s) lo = mid; else hi = mid - 1;
+    }
+    E = &P.items[lo];
+  }
+  *g = s;
+  seed_of(E->src, s - E->seed_start, x);
+  return E;
+}
 
 // Outward signed distance of the point from face f: global frame, x in domain
 // units; local frame, the point is vertex ic + x in cell units and lo/hi are
@@ -392,19 +421,19 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 }
 
 template <class R, int NC, bool LOC>
-__device__ __forceinline__ void write_end(const TraceParams<R>& P, int64_t unit, const R* y, const int* ic, R mu,
-                                          int face, int status, int steps) {
+__device__ __forceinline__ void write_end(const TraceParams<R>& P, const Item<R>* E, int64_t unit, const R* y,
+                                          const int* ic, R mu, int face, int status, int steps) {
   EndRec<R>& e = P.ends[unit];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (LOC)
-      e.x[a] = (R)((double)P.F.org[a] + ((double)ic[a] + (double)y[a]) / (double)P.F.inv_h[a]);
+      e.x[a] = (R)((double)E->F.org[a] + ((double)ic[a] + (double)y[a]) / (double)E->F.inv_h[a]);
     else
       e.x[a] = y[a];
   }
   if (status == QSL_LINE_OK && face != NO_FACE) {
     int a = face >> 1;
-    e.x[a] = (R)((face & 1) ? P.hi_d[a] : P.lo_d[a]);  // exactly on the face
+    e.x[a] = (R)((face & 1) ? E->hi_d[a] : E->lo_d[a]);  // exactly on the face
   }
   if (NC == 9)
 #pragma unroll
@@ -419,7 +448,7 @@ __device__ __forceinline__ void write_end(const TraceParams<R>& P, int64_t unit,
 }
 
 template <class R, int NC, bool LOC>
-__global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
+__global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ TraceParams<R> P) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -428,7 +457,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
     int64_t c = 2 * (*P.n_seeds_dev);
     total = c < total ? c : total;
   }
-  const FieldView<R>& F = P.F;
+  const Item<R>* E = &P.item0;
 
   bool active = false;
   bool exhausted = false;  // warp-uniform
@@ -466,13 +495,13 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
             // ---- initialise this unit
             int64_t g;
             double xd[3];
-            seed_of(P.src, unit >> 1, &g, xd);
+            E = resolve_seed(P, unit >> 1, &g, xd);
             sgn = (unit & 1) ? R(-1) : R(1);
             if (LOC) {
 #pragma unroll
               for (int a = 0; a < 3; ++a) {
-                double fa = (xd[a] - (double)F.org[a]) * (double)F.inv_h[a];
-                double fl = floor(fmin(fmax(fa, 0.0), (double)(F.n[a] - 2)));
+                double fa = (xd[a] - (double)E->F.org[a]) * (double)E->F.inv_h[a];
+                double fl = floor(fmin(fmax(fa, 0.0), (double)(E->F.n[a] - 2)));
                 ic[a] = (int)fl;
                 y[a] = (R)(fa - fl);
               }
@@ -490,12 +519,12 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
             bool outside = false;
 #pragma unroll
             for (int f = 0; f < 6; ++f)
-              if (face_g<R, LOC>(P.lo, P.hi, ic, f, y, (const R*)nullptr) > R(0)) outside = true;
+              if (face_g<R, LOC>(E->lo, E->hi, ic, f, y, (const R*)nullptr) > R(0)) outside = true;
             if (outside || !isfinite(xd[0]) || !isfinite(xd[1]) || !isfinite(xd[2])) {
               status = QSL_LINE_OUTSIDE;
             } else {
               Interp<R> I0;
-              interp<R, R, false, false, LOC>(F, y[0], y[1], y[2], I0, ic);
+              interp<R, R, false, false, LOC>(E->F, y[0], y[1], y[2], I0, ic);
               R m0 = sqrt(I0.b[0] * I0.b[0] + I0.b[1] * I0.b[1] + I0.b[2] * I0.b[2]);
               if (!(m0 > R(0))) {
                 status = QSL_LINE_NULL;
@@ -527,7 +556,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
                 // this side at once with zero length
 #pragma unroll
                 for (int f = 0; f < 6; ++f) {
-                  if (status == ST_RUNNING && face_g<R, LOC>(P.lo, P.hi, ic, f, y, (const R*)nullptr) == R(0)) {
+                  if (status == ST_RUNNING && face_g<R, LOC>(E->lo, E->hi, ic, f, y, (const R*)nullptr) == R(0)) {
                     R bn = I0.b[f >> 1] * sgn;
                     R outw = (f & 1) ? bn : -bn;
                     if (outw > R(0)) {
@@ -538,9 +567,9 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
                 }
               }
             }
-            h = P.euler ? P.euler_h : P.h_init;
+            h = P.euler ? E->euler_h : E->h_init;
             if (status != ST_RUNNING) {
-              write_end<R, NC, LOC>(P, unit, y, ic, R(0), lface, status, 0);
+              write_end<R, NC, LOC>(P, E, unit, y, ic, R(0), lface, status, 0);
               active = false;
             }
           }
@@ -562,9 +591,9 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
     R hs = lhm;
     if (status == ST_RUNNING && phase == 0) {
       if (steps >= P.max_steps) status = QSL_LINE_MAXSTEPS;
-      R room = P.max_len - mu;
+      R room = E->max_len - mu;
       if (status == ST_RUNNING && !(room > R(0))) status = QSL_LINE_MAXLEN;
-      R hcap = P.euler ? P.euler_h : P.h_max;
+      R hcap = P.euler ? E->euler_h : E->h_max;
       hs = fmin(h, hcap);
       capped = false;
       if (room <= hs) {
@@ -575,10 +604,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
     if (status == ST_RUNNING) {
       R dy[NC], yerr[NC];
       if (P.euler) {
-        euler_step<R, R, NC, LOC>(F, y, sgn * hs, dy, yerr, ic);
+        euler_step<R, R, NC, LOC>(E->F, y, sgn * hs, dy, yerr, ic);
         c_stage += 1;
       } else {
-        ck_step<R, R, NC, LOC>(F, y, sgn * hs, dy, yerr, ic);
+        ck_step<R, R, NC, LOC>(E->F, y, sgn * hs, dy, yerr, ic);
         c_stage += 6;
       }
       steps += 1;
@@ -592,8 +621,8 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
           R e = fabs(yerr[i]), ya = fabs(y[i]), yb = fabs(yn);
           if (LOC && i < 3) {
             // position error in domain units, scaled by |x| in domain units
-            R hh = R(1) / R(F.inv_h[i]);
-            R base = R(F.org[i]) + R(ic[i]) * hh;
+            R hh = R(1) / R(E->F.inv_h[i]);
+            R base = R(E->F.org[i]) + R(ic[i]) * hh;
             e *= hh;
             ya = fabs(base + y[i] * hh);
             yb = fabs(base + yn * hh);
@@ -606,13 +635,13 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
         } else if (!P.euler && err > R(1)) {
           c_rej += 1;
           h = hs * fmax(R(0.2), R(0.9) * cpow(err, R(-0.25)));
-          if (h < P.h_min) status = QSL_LINE_STALL;
+          if (h < E->h_min) status = QSL_LINE_STALL;
         } else {
           c_acc += 1;
           bool inside = true;
 #pragma unroll
           for (int f = 0; f < 6; ++f)
-            if (face_g<R, LOC>(P.lo, P.hi, ic, f, y, dy) > R(0)) inside = false;
+            if (face_g<R, LOC>(E->lo, E->hi, ic, f, y, dy) > R(0)) inside = false;
           if (inside) {
 #pragma unroll
             for (int i = 0; i < NC; ++i) y[i] += dy[i];
@@ -621,7 +650,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
 #pragma unroll
               for (int a = 0; a < 3; ++a) {
                 R fl = floor(y[a]);
-                int ni = min(max(ic[a] + (int)fl, 0), F.n[a] - 2);
+                int ni = min(max(ic[a] + (int)fl, 0), E->F.n[a] - 2);
                 y[a] -= R(ni - ic[a]);
                 ic[a] = ni;
               }
@@ -637,11 +666,11 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
             yh[0] = dy[0];
             yh[1] = dy[1];
             yh[2] = dy[2];
-            lface = chord_face<R, LOC>(P.lo, P.hi, ic, y, yh);
+            lface = chord_face<R, LOC>(E->lo, E->hi, ic, y, yh);
             la = 0;
             lb = hs;
-            lga = face_g<R, LOC>(P.lo, P.hi, ic, lface, y, (const R*)nullptr);
-            lgb = face_g<R, LOC>(P.lo, P.hi, ic, lface, y, yh);
+            lga = face_g<R, LOC>(E->lo, E->hi, ic, lface, y, (const R*)nullptr);
+            lgb = face_g<R, LOC>(E->lo, E->hi, ic, lface, y, yh);
             lside = 0;
             lit = 0;
             lround = 0;
@@ -651,16 +680,16 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
       } else {
         c_land += 1;
         lit += 1;
-        R gm = face_g<R, LOC>(P.lo, P.hi, ic, lface, y, dy);
+        R gm = face_g<R, LOC>(E->lo, E->hi, ic, lface, y, dy);
         // converged when within the landing tolerance or at the resolution of
         // the step increment along the face normal
         R dn = fabs(lface >> 1 == 0 ? dy[0] : (lface >> 1 == 1 ? dy[1] : dy[2]));
-        R gtol = fmax(P.land_tol, R(4) * eps_of<R>() * dn);
+        R gtol = fmax(E->land_tol, R(4) * eps_of<R>() * dn);
         if (fabs(gm) <= gtol || lit >= 60 || !isfinite(gm) || !(lb - la > eps_of<R>() * lb)) {
           R worst = R(-1);
 #pragma unroll
           for (int f = 0; f < 6; ++f)
-            if (f != lface) worst = fmax(worst, face_g<R, LOC>(P.lo, P.hi, ic, f, y, dy));
+            if (f != lface) worst = fmax(worst, face_g<R, LOC>(E->lo, E->hi, ic, f, y, dy));
           if (worst > gtol && lround < 8) {
             // the landed point is outside another face: that face was crossed first
             lround += 1;
@@ -668,11 +697,11 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
             yh[1] = dy[1];
             yh[2] = dy[2];
             R hi_h = lhm;
-            lface = chord_face<R, LOC>(P.lo, P.hi, ic, y, yh);
+            lface = chord_face<R, LOC>(E->lo, E->hi, ic, y, yh);
             la = 0;
             lb = hi_h;
-            lga = face_g<R, LOC>(P.lo, P.hi, ic, lface, y, (const R*)nullptr);
-            lgb = face_g<R, LOC>(P.lo, P.hi, ic, lface, y, yh);
+            lga = face_g<R, LOC>(E->lo, E->hi, ic, lface, y, (const R*)nullptr);
+            lgb = face_g<R, LOC>(E->lo, E->hi, ic, lface, y, yh);
             lside = 0;
             lit = 0;
             lhm = la + (lb - la) * lga / (lga - lgb);
@@ -701,7 +730,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const TraceParams<R> P) {
       }
     }
     if (status != ST_RUNNING) {
-      write_end<R, NC, LOC>(P, unit, y, ic, mu, lface, status, steps);
+      write_end<R, NC, LOC>(P, E, unit, y, ic, mu, lface, status, steps);
       active = false;
     }
   }
@@ -804,7 +833,7 @@ __device__ __forceinline__ void cell_rhs(const R* __restrict__ cs, int st, bool 
 }
 
 template <class R, int NC>
-__global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
+__global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ TraceParams<R> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int st = blockDim.x;
   R* cs = reinterpret_cast<R*>(smem_raw) + threadIdx.x;
@@ -816,11 +845,10 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
     int64_t c = 2 * (*P.n_seeds_dev);
     total = c < total ? c : total;
   }
-  const FieldView<R>& F = P.F;
-  const R ih[3] = {R(F.inv_h[0]), R(F.inv_h[1]), R(F.inv_h[2])};
-  const R hh3[3] = {R(1) / ih[0], R(1) / ih[1], R(1) / ih[2]};
+  const Item<R>* E = &P.item0;
+  R ih[3] = {R(1), R(1), R(1)}, hh3[3] = {R(1), R(1), R(1)};  // spacing of the lane's field
   const R band = R(16) * eps_of<R>();  // tolerance band of internal cell faces (cell units)
-  const R tiny = R(1e-4) * P.h_max;
+  R tiny = R(0);
 
   bool active = false, exhausted = false, kvalid = false;
   int64_t unit = 0;
@@ -851,12 +879,18 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
             c_lines += (myu & 1) == 0;
             int64_t g;
             double xd[3];
-            seed_of(P.src, unit >> 1, &g, xd);
+            E = resolve_seed(P, unit >> 1, &g, xd);
             sgn = (unit & 1) ? R(-1) : R(1);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              double fa = (xd[a] - (double)F.org[a]) * (double)F.inv_h[a];
-              double fl = floor(fmin(fmax(fa, 0.0), (double)(F.n[a] - 2)));
+              ih[a] = R(E->F.inv_h[a]);
+              hh3[a] = R(1) / ih[a];
+            }
+            tiny = R(1e-4) * E->h_max;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              double fa = (xd[a] - (double)E->F.org[a]) * (double)E->F.inv_h[a];
+              double fl = floor(fmin(fmax(fa, 0.0), (double)(E->F.n[a] - 2)));
               ic[a] = (int)fl;
               y[a] = (R)(fa - fl);
             }
@@ -870,12 +904,12 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
             bool outside = false;
 #pragma unroll
             for (int f = 0; f < 6; ++f)
-              if (face_g<R, true>(P.lo, P.hi, ic, f, y, (const R*)nullptr) > R(0)) outside = true;
+              if (face_g<R, true>(E->lo, E->hi, ic, f, y, (const R*)nullptr) > R(0)) outside = true;
             if (outside || !isfinite(xd[0]) || !isfinite(xd[1]) || !isfinite(xd[2])) {
               status = QSL_LINE_OUTSIDE;
             } else {
               Interp<R> I0;
-              interp<R, R, false, false, true>(F, y[0], y[1], y[2], I0, ic);
+              interp<R, R, false, false, true>(E->F, y[0], y[1], y[2], I0, ic);
               R m0 = sqrt(I0.b[0] * I0.b[0] + I0.b[1] * I0.b[1] + I0.b[2] * I0.b[2]);
               if (!(m0 > R(0))) {
                 status = QSL_LINE_NULL;
@@ -903,7 +937,7 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
                 }
 #pragma unroll
                 for (int f = 0; f < 6; ++f) {
-                  if (status == ST_RUNNING && face_g<R, true>(P.lo, P.hi, ic, f, y, (const R*)nullptr) == R(0)) {
+                  if (status == ST_RUNNING && face_g<R, true>(E->lo, E->hi, ic, f, y, (const R*)nullptr) == R(0)) {
                     R bn = I0.b[f >> 1] * sgn;
                     R outw = (f & 1) ? bn : -bn;
                     if (outw > R(0)) {
@@ -914,9 +948,9 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
                 }
               }
             }
-            h = P.h_init;
+            h = E->h_init;
             if (status != ST_RUNNING) {
-              write_end<R, NC, true>(P, unit, y, ic, R(0), lface, status, 0);
+              write_end<R, NC, true>(P, E, unit, y, ic, R(0), lface, status, 0);
               active = false;
             }
           }
@@ -935,15 +969,15 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
     int status = ST_RUNNING, lface = NO_FACE;
     if (timed_out) status = QSL_LINE_TIMEOUT;
     if (status == ST_RUNNING && steps >= P.max_steps) status = QSL_LINE_MAXSTEPS;
-    R room = P.max_len - mu;
+    R room = E->max_len - mu;
     if (status == ST_RUNNING && !(room > R(0))) status = QSL_LINE_MAXLEN;
     if (status == ST_RUNNING) {
       if (!kvalid) {
         // gather the 8 vertices of the current cell once; every stage of the
         // following steps in this cell reads them from shared memory
         typedef typename V4<R>::type V;
-        const size_t sy = (size_t)F.n[0], sz = (size_t)F.n[0] * (size_t)F.n[1];
-        const V* p = F.v + (size_t)ic[2] * sz + (size_t)ic[1] * sy + (size_t)ic[0];
+        const size_t sy = (size_t)E->F.n[0], sz = (size_t)E->F.n[0] * (size_t)E->F.n[1];
+        const V* p = E->F.v + (size_t)ic[2] * sz + (size_t)ic[1] * sy + (size_t)ic[0];
         V q[8];
         q[0] = ldg4(p);
         q[1] = ldg4(p + 1);
@@ -959,7 +993,7 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
           cs[(8 + c) * st] = q[c].y;
           cs[(16 + c) * st] = q[c].z;
         }
-        cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], y, k1);
+        cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], y, k1);
         c_stage += 1;
         kvalid = true;
       }
@@ -968,7 +1002,7 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
       bool lo_dom[3], hi_dom[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        R lr = P.lo[a] - R(ic[a]), hr = P.hi[a] - R(ic[a]);
+        R lr = E->lo[a] - R(ic[a]), hr = E->hi[a] - R(ic[a]);
         lo_dom[a] = lr >= R(0);
         hi_dom[a] = hr <= R(1);
         lo_pl[a] = lo_dom[a] ? lr : R(0);
@@ -982,8 +1016,8 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
         if (vel > R(0)) tface = fmin(tface, (hi_pl[a] - y[a]) / vel);
         else if (vel < R(0)) tface = fmin(tface, (lo_pl[a] - y[a]) / vel);
       }
-      R hs = fmin(fmin(h, P.h_max), room);
-      bool capped = room <= fmin(h, P.h_max);
+      R hs = fmin(fmin(h, E->h_max), room);
+      bool capped = room <= fmin(h, E->h_max);
       R hf = R(1.25) * fmax(tface, R(0)) + tiny;
       if (hf < hs) {
         hs = hf;
@@ -993,29 +1027,29 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
       R k2[NC], k3[NC], k4[NC], k5[NC], k6[NC], k7[NC], t[NC];
 #pragma unroll
       for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(DA21) * k1[i], y[i]);
-      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k2);
+      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k2);
 #pragma unroll
       for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(DA31) * k1[i] + R(DA32) * k2[i], y[i]);
-      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k3);
+      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k3);
 #pragma unroll
       for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(DA41) * k1[i] + R(DA42) * k2[i] + R(DA43) * k3[i], y[i]);
-      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k4);
+      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k4);
 #pragma unroll
       for (int i = 0; i < NC; ++i)
         t[i] = fma(hh, R(DA51) * k1[i] + R(DA52) * k2[i] + R(DA53) * k3[i] + R(DA54) * k4[i], y[i]);
-      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k5);
+      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k5);
 #pragma unroll
       for (int i = 0; i < NC; ++i)
         t[i] = fma(hh, R(DA61) * k1[i] + R(DA62) * k2[i] + R(DA63) * k3[i] + R(DA64) * k4[i] + R(DA65) * k5[i],
                    y[i]);
-      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k6);
+      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k6);
       R dy[NC];
 #pragma unroll
       for (int i = 0; i < NC; ++i) {
         dy[i] = hh * (R(DB1) * k1[i] + R(DB3) * k3[i] + R(DB4) * k4[i] + R(DB5) * k5[i] + R(DB6) * k6[i]);
         t[i] = y[i] + dy[i];
       }
-      cell_rhs<R, NC>(cs, st, F.raw, ih[0], ih[1], ih[2], t, k7);
+      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k7);
       c_stage += 6;
       steps += 1;
       R err = 0;
@@ -1027,7 +1061,7 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
         if (!isfinite(t[i])) finite = false;
         R ya = fabs(y[i]), yb = fabs(t[i]);
         if (i < 3) {
-          R base = R(F.org[i]) + R(ic[i]) * hh3[i];
+          R base = R(E->F.org[i]) + R(ic[i]) * hh3[i];
           e *= hh3[i];
           ya = fabs(base + y[i] * hh3[i]);
           yb = fabs(base + t[i] * hh3[i]);
@@ -1039,7 +1073,7 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
       } else if (err > R(1)) {
         c_rej += 1;
         h = hs * fmax(R(0.2), R(0.9) * cpow(err, R(-0.25)));
-        if (h < P.h_min) status = QSL_LINE_STALL;
+        if (h < E->h_min) status = QSL_LINE_STALL;
       } else {
         c_acc += 1;
         R hnext = hs * ((err == R(0)) ? R(5) : fmin(R(5), R(0.9) * cpow(err, R(-0.2))));
@@ -1143,7 +1177,7 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
             // enter the neighbouring cell
             zc = (dl < tiny) ? zc + 1 : 0;
             int na = ic[ax_c] + (up_c ? 1 : -1);
-            if (zc > 3 || na < 0 || na > F.n[ax_c] - 2) {
+            if (zc > 3 || na < 0 || na > E->F.n[ax_c] - 2) {
               // grazing a face back and forth: stay in this cell for one step
               // (the cell's polynomial continued across the face)
               zc = 0;
@@ -1160,7 +1194,7 @@ __global__ void __launch_bounds__(128) cell_kernel(const TraceParams<R> P) {
       }
     }
     if (status != ST_RUNNING) {
-      write_end<R, NC, true>(P, unit, y, ic, mu, lface, status, steps);
+      write_end<R, NC, true>(P, E, unit, y, ic, mu, lface, status, steps);
       active = false;
     }
   }
@@ -1233,35 +1267,32 @@ __device__ void end_terms(const FieldView<S>& F, const double* x, const double* 
   }
 }
 
-template <class R, class S>
+template <class R>
 struct AssembleParams {
-  FieldView<S> F;
-  SeedSource src;
-  int64_t n_seeds;
-  const int64_t* n_seeds_dev;
-  const EndRec<R>* ends;
+  TraceParams<R> T;  // the launch's problems, seeds and end records
   LineOutputs out;
   int tangent;
 };
 
-template <class R, class S>
-__global__ void __launch_bounds__(128) assemble_kernel(const AssembleParams<R, S> P) {
-  int64_t n = P.n_seeds;
-  if (P.n_seeds_dev) n = min(n, *P.n_seeds_dev);
+template <class R>
+__global__ void __launch_bounds__(128) assemble_kernel(const __grid_constant__ AssembleParams<R> P) {
+  int64_t n = P.T.n_units / 2;
+  if (P.T.n_seeds_dev) n = min(n, *P.T.n_seeds_dev);
   const double NaN = __longlong_as_double(0x7ff8000000000000ll);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     int64_t g;
     double x0[3];
-    seed_of(P.src, j, &g, x0);
-    const EndRec<R>& ef = P.ends[2 * j];
-    const EndRec<R>& eb = P.ends[2 * j + 1];
+    const Item<R>* E = resolve_seed(P.T, j, &g, x0);
+    const FieldView<R>& FV = E->F;
+    const EndRec<R>& ef = P.T.ends[2 * j];
+    const EndRec<R>& eb = P.T.ends[2 * j + 1];
     double q_perp = NaN, q_foot = NaN, q_det = NaN, b0 = NaN, bf = NaN, bb = NaN, ff = NaN, fb = NaN;
     int sf = ef.status, sb = eb.status;
     double L = NaN;
     if (sf != QSL_LINE_OUTSIDE) L = (double)ef.mu + (double)eb.mu;
     if (sf != QSL_LINE_OUTSIDE && sf != QSL_LINE_NULL) {
       Interp<double> I0;
-      interp<double, S, false, true>(P.F, x0[0], x0[1], x0[2], I0);
+      interp<double, R, false, true>(FV, x0[0], x0[1], x0[2], I0);
       b0 = I0.m;
     }
     bool okf = (sf == QSL_LINE_OK || sf == QSL_LINE_MAXLEN);
@@ -1278,8 +1309,8 @@ __global__ void __launch_bounds__(128) assemble_kernel(const AssembleParams<R, S
         d2b[i] = eb.d2[i];
       }
       EndTerms tf, tb;
-      end_terms<S>(P.F, xf, d1f, d2f, ef.face, sf == QSL_LINE_OK, tf);
-      end_terms<S>(P.F, xb, d1b, d2b, eb.face, sb == QSL_LINE_OK, tb);
+      end_terms<R>(FV, xf, d1f, d2f, ef.face, sf == QSL_LINE_OK, tf);
+      end_terms<R>(FV, xb, d1b, d2b, eb.face, sb == QSL_LINE_OK, tb);
       bf = tf.bmag;
       bb = tb.bmag;
       double br = tf.A * tb.B + tb.A * tf.B - 2.0 * tb.C * tf.C;
@@ -1379,13 +1410,42 @@ FieldView<double> make_view<double>(const qsl_field* f) {
   return v;
 }
 
+// One problem of a launch from a field, its seed source and its resolved
+// configuration (domain bounds, step scales in domain units).
+template <class R>
+Item<R> make_item(const qsl_field* f, const SeedSource& src, const TraceConfig& cfg, int64_t seed_start, bool loc) {
+  Item<R> it;
+  it.F = make_view<R>(f);
+  it.src = src;
+  it.seed_start = seed_start;
+  for (int a = 0; a < 3; ++a) {
+    it.lo_d[a] = cfg.lo[a];
+    it.hi_d[a] = cfg.hi[a];
+    // the local frame measures positions in grid-index units
+    it.lo[a] = loc ? (R)((cfg.lo[a] - f->org[a]) / f->h[a]) : (R)cfg.lo[a];
+    it.hi[a] = loc ? (R)((cfg.hi[a] - f->org[a]) / f->h[a]) : (R)cfg.hi[a];
+  }
+  it.max_len = (R)cfg.max_len;
+  it.h_init = (R)(cfg.h_init * cfg.cell);
+  it.h_max = (R)(cfg.h_max * cfg.cell);
+  it.h_min = (R)(cfg.h_min * cfg.cell);
+  it.euler_h = (R)(cfg.euler_h * cfg.cell);
+  // landing tolerance in the frame's units (cell units of the coarsest axis
+  // in the local frame); the kernel also stops at the resolution of the step
+  double lt = loc ? cfg.land_tol / fmax(fmax(f->h[0], f->h[1]), f->h[2]) : cfg.land_tol;
+  it.land_tol = (R)lt;
+  return it;
+}
+
 // Scratch of one tracing launch: the queue head and watchdog flag (16 bytes
 // at offset 0) and one end record per unit from offset 256. `scratch` is
-// either caller-provided (the no-allocation entry point) or allocated here.
+// either caller-provided (no-allocation entry point, captured plans) or
+// allocated here.
 template <class R, int NC>
-int launch_trace(const qsl_field* f, const SeedSource& src, int64_t n_seeds, const int64_t* n_seeds_dev,
-                 const TraceConfig& cfg, const LaunchShape& shape, const LineOutputs& out, cudaStream_t stream,
-                 DeviceStats* stats_dev, cudaEvent_t* ev, void* scratch = nullptr) {
+int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bool loc, const int64_t* index,
+                 int64_t n_seeds, const int64_t* n_seeds_dev, const TraceConfig& cfg, const LaunchShape& shape,
+                 const LineOutputs& out, cudaStream_t stream, DeviceStats* stats_dev, cudaEvent_t* ev,
+                 void* scratch) {
   int dev = 0, sms = 0;
   QSL_CHECK_CUDA(cudaGetDevice(&dev));
   QSL_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1395,41 +1455,24 @@ int launch_trace(const qsl_field* f, const SeedSource& src, int64_t n_seeds, con
     QSL_CHECK_CUDA(cudaMallocAsync(&scratch, 256 + sizeof(EndRec<R>) * (n_units ? n_units : 1), stream));
   unsigned long long* head = reinterpret_cast<unsigned long long*>(scratch);
   EndRec<R>* ends = reinterpret_cast<EndRec<R>*>(reinterpret_cast<unsigned char*>(scratch) + 256);
-  int* tflag = nullptr;
   QSL_CHECK_CUDA(cudaMemsetAsync(head, 0, 16, stream));
-  tflag = (int*)(head + 1);
   TraceParams<R> P;
-  P.F = make_view<R>(f);
-  P.src = src;
+  P.item0 = item0;
+  P.items = items_dev;
+  P.n_items = n_items;
+  P.index = index;
   P.n_units = 2 * n_seeds;
   P.n_seeds_dev = n_seeds_dev;
   P.ends = ends;
   P.head = head;
   P.stats = stats_dev;
-  const bool loc = f->uniform != 0;
-  for (int a = 0; a < 3; ++a) {
-    P.lo_d[a] = cfg.lo[a];
-    P.hi_d[a] = cfg.hi[a];
-    // the local frame measures positions in grid-index units
-    P.lo[a] = loc ? (R)((cfg.lo[a] - f->org[a]) / f->h[a]) : (R)cfg.lo[a];
-    P.hi[a] = loc ? (R)((cfg.hi[a] - f->org[a]) / f->h[a]) : (R)cfg.hi[a];
-  }
-  P.max_len = (R)cfg.max_len;
   P.tol_abs = (R)cfg.tol_abs;
   P.tol_rel = (R)cfg.tol_rel;
-  P.h_init = (R)(cfg.h_init * cfg.cell);
-  P.h_max = (R)(cfg.h_max * cfg.cell);
-  P.h_min = (R)(cfg.h_min * cfg.cell);
-  P.euler_h = (R)(cfg.euler_h * cfg.cell);
-  // landing tolerance in the frame's units (cell units of the coarsest axis
-  // in the local frame); the kernel also stops at the resolution of the step
-  double lt = loc ? cfg.land_tol / fmax(fmax(f->h[0], f->h[1]), f->h[2]) : cfg.land_tol;
-  P.land_tol = (R)lt;
   P.max_steps = cfg.max_steps;
   P.euler = cfg.integrator == QSL_EULER;
   P.refill_min = shape.refill_min > 0 ? shape.refill_min : 1;
   P.timeout_ns = cfg.timeout_ns;
-  P.timeout_flag = tflag;
+  P.timeout_flag = reinterpret_cast<int*>(head + 1);
   int threads = 32 * shape.warps_per_block;
   // persistent kernel: never launch more blocks than can be resident at once
   const bool use_cell = loc && cfg.integrator == QSL_DOPRI5_CELL;
@@ -1464,19 +1507,14 @@ int launch_trace(const qsl_field* f, const SeedSource& src, int64_t n_seeds, con
   }
   if (ev) QSL_CHECK_CUDA(cudaEventRecord(ev[1], stream));
   // assembly
-  typedef typename std::conditional<sizeof(R) == 4, float, double>::type S;
-  AssembleParams<R, S> A;
-  A.F = make_view<S>(f);
-  A.src = src;
-  A.n_seeds = n_seeds;
-  A.n_seeds_dev = n_seeds_dev;
-  A.ends = ends;
+  AssembleParams<R> A;
+  A.T = P;
   A.out = out;
   A.tangent = NC == 9;
   if (n_seeds > 0) {
     int ab = (int)((n_seeds + 127) / 128);
     if (ab > sms * 16) ab = sms * 16;
-    assemble_kernel<R, S><<<ab, 128, 0, stream>>>(A);
+    assemble_kernel<R><<<ab, 128, 0, stream>>>(A);
     qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
   }
@@ -1484,20 +1522,33 @@ int launch_trace(const qsl_field* f, const SeedSource& src, int64_t n_seeds, con
   return QSL_OK;
 }
 
+template <class R>
+int launch_any(const Item<R>& item0, const Item<R>* items_dev, int n_items, bool loc, const int64_t* index,
+               int64_t n_seeds, const int64_t* n_seeds_dev, const TraceConfig& cfg, const LaunchShape& shape,
+               const LineOutputs& out, cudaStream_t stream, DeviceStats* stats_dev, cudaEvent_t* ev, void* scratch) {
+  if (cfg.length_only)
+    return launch_trace<R, 3>(item0, items_dev, n_items, loc, index, n_seeds, n_seeds_dev, cfg, shape, out, stream,
+                              stats_dev, ev, scratch);
+  return launch_trace<R, 9>(item0, items_dev, n_items, loc, index, n_seeds, n_seeds_dev, cfg, shape, out, stream,
+                            stats_dev, ev, scratch);
+}
+
 }  // namespace
 
 int trace_and_assemble(const qsl_field* f, const SeedSource& src, int64_t n_seeds, const int64_t* n_seeds_dev,
                        const TraceConfig& cfg, int precision, const LaunchShape& shape, const LineOutputs& out,
-                       cudaStream_t stream, DeviceStats* stats_dev, cudaEvent_t* ev) {
-  bool tangent = !cfg.length_only;
-  if (precision == QSL_FP64) {
-    if (tangent)
-      return launch_trace<double, 9>(f, src, n_seeds, n_seeds_dev, cfg, shape, out, stream, stats_dev, ev);
-    return launch_trace<double, 3>(f, src, n_seeds, n_seeds_dev, cfg, shape, out, stream, stats_dev, ev);
-  }
-  if (tangent)
-    return launch_trace<float, 9>(f, src, n_seeds, n_seeds_dev, cfg, shape, out, stream, stats_dev, ev);
-  return launch_trace<float, 3>(f, src, n_seeds, n_seeds_dev, cfg, shape, out, stream, stats_dev, ev);
+                       cudaStream_t stream, DeviceStats* stats_dev, cudaEvent_t* ev, const int64_t* index,
+                       void* scratch) {
+  bool loc = f->uniform != 0;
+  if (precision == QSL_FP64)
+    return qsl::launch_any<double>(make_item<double>(f, src, cfg, 0, loc), nullptr, 0, loc, index, n_seeds, n_seeds_dev,
+                              cfg, shape, out, stream, stats_dev, ev, scratch);
+  return qsl::launch_any<float>(make_item<float>(f, src, cfg, 0, loc), nullptr, 0, loc, index, n_seeds, n_seeds_dev, cfg,
+                           shape, out, stream, stats_dev, ev, scratch);
+}
+
+size_t end_record_bytes(int precision) {
+  return precision == QSL_FP64 ? sizeof(EndRec<double>) : sizeof(EndRec<float>);
 }
 
 int select_retrace(const SeedSource& src, int64_t n_seeds, const LineOutputs& out, double threshold,
@@ -1605,7 +1656,260 @@ extern "C" int qsl_trace_seeds_noalloc(const qsl_field* f, const double* seeds, 
   lo.q_form = QSL_Q_PERP;
   lo.skip_open = o->skip_open;
   if (S == 0) return QSL_OK;
-  if (cfg.length_only)
-    return qsl::launch_trace<float, 3>(f, src, S, nullptr, cfg, shape, lo, stream, nullptr, nullptr, scratch);
-  return qsl::launch_trace<float, 9>(f, src, S, nullptr, cfg, shape, lo, stream, nullptr, nullptr, scratch);
+  return qsl::trace_and_assemble(f, src, S, nullptr, cfg, QSL_FP32_MIXED, shape, lo, stream, nullptr, nullptr,
+                                 nullptr, scratch);
 }
+
+// ---------------------------------------------------------------------------
+// Batches: planar Q/FLL maps of many fields in one persistent launch, and
+// plans that capture such a launch (trace, FP64 assembly, FP64 retrace) in a
+// CUDA graph for replay.
+// ---------------------------------------------------------------------------
+#include <vector>
+
+struct qsl_plan {
+  int n_items = 0;
+  int64_t total = 0;
+  bool loc = true;
+  int precision = QSL_FP32_MIXED;
+  double retrace_q = 0;
+  qsl::TraceConfig cfg{};
+  qsl::LaunchShape shape{}, shape64{};
+  qsl::LineOutputs out{};
+  qsl::Item<float> first32{};
+  qsl::Item<double> first64{};
+  void* table32 = nullptr;
+  void* table64 = nullptr;
+  void* scratch32 = nullptr;
+  void* scratch64 = nullptr;
+  int64_t* index = nullptr;
+  int64_t* count = nullptr;
+  float* qtmp = nullptr;
+  qsl::DeviceStats* stats = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int device = -1;
+};
+
+namespace {
+
+void plan_release(qsl_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  void* bufs[] = {p->table32, p->table64, p->scratch32, p->scratch64, p->index, p->count, p->qtmp, p->stats};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete p;
+}
+
+// Validates the items and fills the plan's tables and scratch (synchronous).
+int plan_build(const qsl_batch_item* items, int n_items, const qsl_opts* o, float* q, float* length, uint8_t* faces,
+               uint8_t* status, qsl_plan** out) {
+  *out = nullptr;
+  if (n_items < 1 || !items) {
+    qsl::set_error("need at least one batch item");
+    return QSL_EINVAL;
+  }
+  int rc = QSL_OK;
+  for (int k = 0; k < n_items; ++k) {
+    if ((rc = qsl::validate_opts(items[k].field, o))) return rc;
+    if (items[k].nu < 0 || items[k].nv < 0) {
+      qsl::set_error("item %d: nu, nv must be >= 0", k);
+      return QSL_EINVAL;
+    }
+  }
+  qsl_plan* p = new qsl_plan();
+  cudaGetDevice(&p->device);
+  p->n_items = n_items;
+  p->precision = o->precision;
+  p->retrace_q = (o->precision == QSL_FP32_MIXED && !o->length_only) ? o->retrace_q : 0.0;
+  qsl::default_shape(o, !o->length_only, o->precision, &p->shape);
+  qsl::default_shape(o, 1, QSL_FP64, &p->shape64);
+  for (int k = 0; k < n_items; ++k) p->loc = p->loc && items[k].field->uniform;
+  std::vector<qsl::Item<float>> t32(n_items);
+  std::vector<qsl::Item<double>> t64(n_items);
+  int64_t start = 0;
+  for (int k = 0; k < n_items; ++k) {
+    const qsl_batch_item& it = items[k];
+    qsl::TraceConfig c;
+    qsl::resolve_config(it.field, o, &c);
+    if (k == 0) p->cfg = c;
+    qsl::SeedSource src{};
+    src.kind = qsl::SEEDS_PLANE;
+    src.n[0] = it.nu;
+    src.n[1] = it.nv;
+    src.n[2] = 1;
+    for (int a = 0; a < 3; ++a) {
+      src.c[a] = it.center[a];
+      src.u[a] = it.u[a];
+      src.v[a] = it.v[a];
+    }
+    t32[k] = qsl::make_item<float>(it.field, src, c, start, p->loc);
+    t64[k] = qsl::make_item<double>(it.field, src, c, start, p->loc);
+    start += (int64_t)it.nu * it.nv;
+  }
+  p->total = start;
+  p->first32 = t32[0];
+  p->first64 = t64[0];
+  p->out.q = q;
+  p->out.length = length;
+  p->out.faces = faces;
+  p->out.status = status;
+  p->out.q_form = o->q_form;
+  p->out.skip_open = o->skip_open;
+#define PLAN_TRY(call)                                                         \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      qsl::set_error("%s failed: %s", #call, cudaGetErrorString(e_));          \
+      plan_release(p);                                                         \
+      return e_ == cudaErrorMemoryAllocation ? QSL_ENOMEM : QSL_ECUDA;         \
+    }                                                                          \
+  } while (0)
+  size_t n_units = (size_t)(2 * p->total);
+  PLAN_TRY(cudaMalloc(&p->table32, sizeof(qsl::Item<float>) * n_items));
+  PLAN_TRY(cudaMemcpy(p->table32, t32.data(), sizeof(qsl::Item<float>) * n_items, cudaMemcpyHostToDevice));
+  PLAN_TRY(cudaMalloc(&p->scratch32, 256 + qsl::end_record_bytes(o->precision) * (n_units ? n_units : 1)));
+  PLAN_TRY(cudaMalloc((void**)&p->stats, sizeof(qsl::DeviceStats)));
+  if (o->precision == QSL_FP64 || p->retrace_q > 0) {
+    PLAN_TRY(cudaMalloc(&p->table64, sizeof(qsl::Item<double>) * n_items));
+    PLAN_TRY(cudaMemcpy(p->table64, t64.data(), sizeof(qsl::Item<double>) * n_items, cudaMemcpyHostToDevice));
+  }
+  if (p->retrace_q > 0) {
+    PLAN_TRY(cudaMalloc(&p->scratch64, 256 + sizeof(qsl::EndRec<double>) * (n_units ? n_units : 1)));
+    PLAN_TRY(cudaMalloc((void**)&p->index, sizeof(int64_t) * (p->total ? p->total : 1)));
+    PLAN_TRY(cudaMalloc((void**)&p->count, sizeof(int64_t)));
+    if (!q) {
+      PLAN_TRY(cudaMalloc((void**)&p->qtmp, sizeof(float) * (p->total ? p->total : 1)));
+      p->out.q = p->qtmp;
+    }
+  }
+#undef PLAN_TRY
+  *out = p;
+  return QSL_OK;
+}
+
+// Issues the plan's work on `s` (allocates nothing; capturable).
+int plan_enqueue(qsl_plan* p, cudaStream_t s) {
+  int rc;
+  QSL_CHECK_CUDA(cudaMemsetAsync(p->stats, 0, sizeof(qsl::DeviceStats), s));
+  if (p->precision == QSL_FP64) {
+    return qsl::launch_any<double>(p->first64, (const qsl::Item<double>*)p->table64, p->n_items, p->loc, nullptr,
+                              p->total, nullptr, p->cfg, p->shape, p->out, s, p->stats, nullptr, p->scratch32);
+  }
+  rc = qsl::launch_any<float>(p->first32, (const qsl::Item<float>*)p->table32, p->n_items, p->loc, nullptr, p->total,
+                         nullptr, p->cfg, p->shape, p->out, s, p->stats, nullptr, p->scratch32);
+  if (rc || p->retrace_q <= 0 || p->total == 0) return rc;
+  qsl::SeedSource none{};
+  if ((rc = qsl::select_retrace(none, p->total, p->out, p->retrace_q, p->index, p->count, s))) return rc;
+  qsl::LineOutputs o2 = p->out;
+  o2.retraced = 1;
+  return qsl::launch_any<double>(p->first64, (const qsl::Item<double>*)p->table64, p->n_items, p->loc, p->index,
+                            p->total, p->count, p->cfg, p->shape64, o2, s, p->stats, nullptr, p->scratch64);
+}
+
+}  // namespace
+
+extern "C" {
+
+int qsl_q_map_batch(const qsl_batch_item* items, int n_items, const qsl_opts* opts, float* q, float* length,
+                    uint8_t* faces, uint8_t* status, int mem, void* stream_) {
+  cudaStream_t s = (cudaStream_t)stream_;
+  if (mem != QSL_MEM_DEVICE) {
+    qsl::set_error("qsl_q_map_batch takes device outputs (mem = QSL_MEM_DEVICE)");
+    return QSL_EINVAL;
+  }
+  qsl_plan* p = nullptr;
+  int rc = plan_build(items, n_items, opts, q, length, faces, status, &p);
+  if (rc) return rc;
+  rc = plan_enqueue(p, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  plan_release(p);
+  if (rc) return rc;
+  if (e != cudaSuccess) {
+    qsl::set_error("batch failed: %s", cudaGetErrorString(e));
+    return QSL_ECUDA;
+  }
+  return QSL_OK;
+}
+
+int qsl_plan_q_map_batch(const qsl_batch_item* items, int n_items, const qsl_opts* opts, float* q, float* length,
+                         uint8_t* faces, uint8_t* status, qsl_plan** out) {
+  if (!out) {
+    qsl::set_error("out is NULL");
+    return QSL_EINVAL;
+  }
+  qsl_plan* p = nullptr;
+  int rc = plan_build(items, n_items, opts, q, length, faces, status, &p);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    qsl::set_error("stream capture failed to start: %s", cudaGetErrorString(e));
+    plan_release(p);
+    return QSL_ECUDA;
+  }
+  rc = plan_enqueue(p, p->cap_stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(p->cap_stream, &g);
+  p->graph = g;
+  if (rc || e != cudaSuccess) {
+    if (!rc) qsl::set_error("stream capture failed: %s", cudaGetErrorString(e));
+    plan_release(p);
+    return rc ? rc : QSL_ECUDA;
+  }
+  e = cudaGraphInstantiate(&p->exec, g, 0);
+  if (e != cudaSuccess) {
+    qsl::set_error("graph instantiation failed: %s", cudaGetErrorString(e));
+    plan_release(p);
+    return QSL_ECUDA;
+  }
+  *out = p;
+  return QSL_OK;
+}
+
+int qsl_plan_launch(qsl_plan* p, void* stream) {
+  if (!p || !p->exec) {
+    qsl::set_error("plan is NULL or not instantiated");
+    return QSL_EINVAL;
+  }
+  cudaError_t e = cudaGraphLaunch(p->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    qsl::set_error("cudaGraphLaunch failed: %s", cudaGetErrorString(e));
+    return QSL_ECUDA;
+  }
+  qsl::count_launch();
+  return QSL_OK;
+}
+
+int qsl_plan_stats(qsl_plan* p, void* stream, qsl_stats* out) {
+  if (!p || !out) {
+    qsl::set_error("NULL argument");
+    return QSL_EINVAL;
+  }
+  qsl::DeviceStats h{};
+  QSL_CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  QSL_CHECK_CUDA(cudaMemcpy(&h, p->stats, sizeof h, cudaMemcpyDeviceToHost));
+  memset(out, 0, sizeof(*out));
+  out->lines = p->total;
+  out->stage_evals = (int64_t)h.stage_evals;
+  out->accepted = (int64_t)h.accepted;
+  out->rejected = (int64_t)h.rejected;
+  out->landing = (int64_t)h.landing;
+  if (p->count) {
+    int64_t c = 0;
+    QSL_CHECK_CUDA(cudaMemcpy(&c, p->count, sizeof c, cudaMemcpyDeviceToHost));
+    out->retraced = c;
+  }
+  out->warps_per_block = p->shape.warps_per_block;
+  out->blocks_per_sm = p->shape.blocks_per_sm;
+  out->refill_min = p->shape.refill_min;
+  return QSL_OK;
+}
+
+void qsl_plan_free(qsl_plan* p) { plan_release(p); }
+
+}  // extern "C"

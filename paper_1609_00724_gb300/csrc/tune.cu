@@ -1,0 +1,170 @@
+// Autotuner of the tracer: picks the launch shape (warps per block, resident
+// blocks per SM, refill threshold of the work queue) and the loosest step
+// tolerance whose Q and length stay within stated bounds of an FP64
+// reference traced at tol 1e-10 on the same sample of seeds. Each candidate is
+// timed with CUDA events on the caller's stream. Results are cached per
+// (grid size, interpolation mode, integrator, q_form, length_only).
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "qsl_internal.cuh"
+
+namespace {
+
+typedef std::tuple<int, int, int, int, int, int, int, int> TuneKey;
+std::mutex g_tune_mu;
+std::map<TuneKey, qsl_tune_report> g_tune_cache;
+
+struct DevLines {
+  qsl_line* p = nullptr;
+  ~DevLines() {
+    if (p) cudaFree(p);
+  }
+};
+
+int time_trace(const qsl_field* f, const double* seeds, int64_t S, const qsl_opts* o, qsl_line* out,
+               cudaStream_t s, double* ms_out) {
+  cudaEvent_t e0, e1;
+  QSL_CHECK_CUDA(cudaEventCreate(&e0));
+  QSL_CHECK_CUDA(cudaEventCreate(&e1));
+  QSL_CHECK_CUDA(cudaEventRecord(e0, s));
+  int rc = qsl_trace_seeds(f, seeds, S, o, out, QSL_MEM_DEVICE, s);
+  QSL_CHECK_CUDA(cudaEventRecord(e1, s));
+  QSL_CHECK_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = ms;
+  return rc;
+}
+
+// Worst relative errors of `got` against `ref` (Q below 1e6 and both ends on
+// the same faces; lengths where the reference is positive).
+void errors(const std::vector<qsl_line>& got, const std::vector<qsl_line>& ref, int q_form, double* eq, double* el,
+            double* face_mismatch) {
+  double wq = 0, wl = 0;
+  int64_t fm = 0;
+  for (size_t i = 0; i < ref.size(); ++i) {
+    const qsl_line& a = got[i];
+    const qsl_line& b = ref[i];
+    if (a.face_f != b.face_f || a.face_b != b.face_b) {
+      ++fm;
+      continue;
+    }
+    double qa = q_form == QSL_Q_FOOT ? a.q_foot : (q_form == QSL_Q_DET ? a.q_det : a.q_perp);
+    double qb = q_form == QSL_Q_FOOT ? b.q_foot : (q_form == QSL_Q_DET ? b.q_det : b.q_perp);
+    if (std::isfinite(qb) && qb < 1e6) wq = fmax(wq, fabs(qa / qb - 1.0));
+    if (b.length > 0) wl = fmax(wl, fabs((double)a.length / (double)b.length - 1.0));
+  }
+  *eq = wq;
+  *el = wl;
+  *face_mismatch = ref.empty() ? 0.0 : (double)fm / (double)ref.size();
+}
+
+}  // namespace
+
+extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, qsl_opts* opts,
+                            qsl_tune_report* report, void* stream_) {
+  cudaStream_t s = (cudaStream_t)stream_;
+  int rc = qsl::validate_opts(f, opts);
+  if (rc) return rc;
+  if (S < 1 || !seeds) {
+    qsl::set_error("autotune needs at least one sample seed (device memory)");
+    return QSL_EINVAL;
+  }
+  TuneKey key(f->n[0], f->n[1], f->n[2], f->mode, opts->integrator, opts->q_form, opts->length_only,
+              (int)std::lround(-std::log10(fmax(opts->tol_rel, 1e-30))));
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      opts->warps_per_block = it->second.warps_per_block;
+      opts->blocks_per_sm = it->second.blocks_per_sm;
+      opts->refill_min = it->second.refill_min;
+      opts->tol_abs = opts->tol_rel = it->second.tol;
+      if (report) {
+        *report = it->second;
+        report->cached = 1;
+      }
+      return QSL_OK;
+    }
+  }
+  DevLines d;
+  QSL_CHECK_CUDA(cudaMalloc((void**)&d.p, sizeof(qsl_line) * S));
+  std::vector<qsl_line> ref(S), got(S);
+  // FP64 reference at tight tolerance
+  qsl_opts r = *opts;
+  r.precision = QSL_FP64;
+  r.tol_abs = r.tol_rel = 1e-10;
+  r.retrace_q = 0;
+  double ms = 0;
+  if ((rc = time_trace(f, seeds, S, &r, d.p, s, &ms))) return rc;
+  QSL_CHECK_CUDA(cudaMemcpy(ref.data(), d.p, sizeof(qsl_line) * S, cudaMemcpyDeviceToHost));
+  // tolerance: the loosest candidate within a tenth of the parity bar
+  const double tols[] = {1e-5, 1e-6, 1e-7, 1e-8};
+  qsl_opts base = *opts;
+  base.retrace_q = 0;
+  double chosen_tol = tols[3], eq = 0, el = 0, fm = 0;
+  for (double t : tols) {
+    qsl_opts c = base;
+    c.tol_abs = c.tol_rel = t;
+    if ((rc = time_trace(f, seeds, S, &c, d.p, s, &ms))) return rc;
+    QSL_CHECK_CUDA(cudaMemcpy(got.data(), d.p, sizeof(qsl_line) * S, cudaMemcpyDeviceToHost));
+    errors(got, ref, opts->q_form, &eq, &el, &fm);
+    if (eq <= 2e-4 && el <= 2e-6 && fm <= 1e-3) {
+      chosen_tol = t;
+      break;
+    }
+  }
+  // launch shape: fastest of the candidates at the chosen tolerance (best of 2)
+  const int wpb[] = {2, 4, 8};
+  const int bps[] = {32, 2};
+  const int refill[] = {1, 8};
+  double best = 1e30;
+  int bw = 4, bb = 32, br = 1;
+  for (int w : wpb)
+    for (int b : bps)
+      for (int rf : refill) {
+        qsl_opts c = base;
+        c.tol_abs = c.tol_rel = chosen_tol;
+        c.warps_per_block = w;
+        c.blocks_per_sm = b;
+        c.refill_min = rf;
+        double t1 = 0, t2 = 0;
+        if ((rc = time_trace(f, seeds, S, &c, d.p, s, &t1))) return rc;
+        if ((rc = time_trace(f, seeds, S, &c, d.p, s, &t2))) return rc;
+        double t = fmin(t1, t2);
+        if (t < best) {
+          best = t;
+          bw = w;
+          bb = b;
+          br = rf;
+        }
+      }
+  qsl_tune_report rep;
+  memset(&rep, 0, sizeof rep);
+  rep.warps_per_block = bw;
+  rep.blocks_per_sm = bb;
+  rep.refill_min = br;
+  rep.tol = chosen_tol;
+  rep.q_err = eq;
+  rep.l_err = el;
+  rep.face_mismatch = fm;
+  rep.sample_ms = best;
+  rep.sample_seeds = S;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = rep;
+  }
+  opts->warps_per_block = bw;
+  opts->blocks_per_sm = bb;
+  opts->refill_min = br;
+  opts->tol_abs = opts->tol_rel = chosen_tol;
+  if (report) *report = rep;
+  return QSL_OK;
+}

@@ -70,6 +70,17 @@ class qsl_samples(C.Structure):
                 ("traced", C.c_int32)]
 
 
+class qsl_batch_item(C.Structure):
+    _fields_ = [("field", C.c_void_p), ("center", C.c_double * 3), ("u", C.c_double * 3), ("v", C.c_double * 3),
+                ("nu", C.c_int32), ("nv", C.c_int32)]
+
+
+class qsl_tune_report(C.Structure):
+    _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_min", C.c_int32),
+                ("cached", C.c_int32), ("tol", C.c_double), ("q_err", C.c_double), ("l_err", C.c_double),
+                ("face_mismatch", C.c_double), ("sample_ms", C.c_double), ("sample_seeds", C.c_int64)]
+
+
 _lib = None
 
 
@@ -98,6 +109,13 @@ def lib():
     L.qsl_convert.argtypes = [vp, vp, i64, i32, i32, vp, i32, i32, vp, i32, vp]
     L.qsl_last_stats.argtypes = [C.POINTER(qsl_stats)]
     L.qsl_kernel_launches.restype = C.c_int64
+    L.qsl_q_map_batch.argtypes = [C.POINTER(qsl_batch_item), i32, C.POINTER(qsl_opts), vp, vp, vp, vp, i32, vp]
+    L.qsl_plan_q_map_batch.argtypes = [C.POINTER(qsl_batch_item), i32, C.POINTER(qsl_opts), vp, vp, vp, vp,
+                                       C.POINTER(vp)]
+    L.qsl_plan_launch.argtypes = [vp, vp]
+    L.qsl_plan_stats.argtypes = [vp, vp, C.POINTER(qsl_stats)]
+    L.qsl_plan_free.argtypes = [vp]
+    L.qsl_autotune.argtypes = [vp, vp, i64, C.POINTER(qsl_opts), C.POINTER(qsl_tune_report), vp]
     L.qsl_trace_seeds_noalloc.argtypes = [vp, vp, i64, C.POINTER(qsl_opts), vp, vp]
     _lib = L
     return L
@@ -198,6 +216,59 @@ def qsl_trace_seeds(field, seeds, opts, out=None, stream=None):
             out = np.zeros(S, dtype=QSL_LINE_DTYPE)
     _check(lib().qsl_trace_seeds(field.handle, _ptr(seeds), S, C.byref(opts), _ptr(out), mem, _stream(stream)))
     return out
+
+
+def _batch_items(items):
+    """items: list of (Field, center, u, v, nu, nv)."""
+    arr = (qsl_batch_item * len(items))()
+    for k, (F, c, u, v, nu, nv) in enumerate(items):
+        arr[k].field = F.handle.value if hasattr(F.handle, "value") else F.handle
+        arr[k].center[:] = [float(x) for x in c]
+        arr[k].u[:] = [float(x) for x in u]
+        arr[k].v[:] = [float(x) for x in v]
+        arr[k].nu, arr[k].nv = int(nu), int(nv)
+    return arr
+
+
+def qsl_q_map_batch(items, opts, q=None, length=None, faces=None, status=None, stream=None):
+    """Maps of many (field, cut) items in one persistent launch; outputs are
+    device tensors holding the items' pixels concatenated in order."""
+    arr = _batch_items(items)
+    _check(lib().qsl_q_map_batch(arr, len(items), C.byref(opts), _ptr(q), _ptr(length), _ptr(faces), _ptr(status),
+                                 QSL_MEM_DEVICE, _stream(stream)))
+
+
+class Plan:
+    """A batch recorded into a CUDA graph (qsl_plan_q_map_batch)."""
+
+    def __init__(self, items, opts, q=None, length=None, faces=None, status=None):
+        self._keep = (items, q, length, faces, status)
+        arr = _batch_items(items)
+        h = C.c_void_p()
+        _check(lib().qsl_plan_q_map_batch(arr, len(items), C.byref(opts), _ptr(q), _ptr(length), _ptr(faces),
+                                          _ptr(status), C.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib().qsl_plan_launch(self.handle, _stream(stream)))
+
+    def stats(self, stream=None):
+        st = qsl_stats()
+        _check(lib().qsl_plan_stats(self.handle, _stream(stream), C.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_ if k != "pad"}
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qsl_plan_free(self.handle)
+            self.handle = None
+
+
+def qsl_autotune(field, seeds, opts, stream=None):
+    """Tunes opts in place on device sample seeds (S x 3 float64); returns the report."""
+    rep = qsl_tune_report()
+    _check(lib().qsl_autotune(field.handle, _ptr(seeds), seeds.shape[0], C.byref(opts), C.byref(rep),
+                              _stream(stream)))
+    return {k: getattr(rep, k) for k, _ in rep._fields_}
 
 
 QSL_NOALLOC_MAX_SEEDS = 65536
@@ -301,4 +372,5 @@ def qsl_last_stats():
 
 EXPORTS = ["qsl_opts_default", "qsl_load_field", "qsl_free_field", "qsl_trace_seeds", "qsl_q_map_2d",
            "qsl_q_volume_3d", "qsl_fledge", "qsl_refine", "qsl_hilbert_encode", "qsl_hilbert_decode", "qsl_convert",
-           "qsl_last_error", "qsl_last_stats", "qsl_trace_seeds_noalloc", "qsl_kernel_launches"]
+           "qsl_last_error", "qsl_last_stats", "qsl_trace_seeds_noalloc", "qsl_kernel_launches", "qsl_q_map_batch",
+           "qsl_plan_q_map_batch", "qsl_plan_launch", "qsl_plan_stats", "qsl_plan_free", "qsl_autotune"]

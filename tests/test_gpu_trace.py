@@ -199,3 +199,40 @@ def test_skip_open_and_retrace_flag(qsl, oracle_mod):
     ret = (st & qsl.QSL_FLAG_RETRACED) != 0
     assert s["retraced"] == ret.sum()
     assert np.all(q[ret & closed] > 1e3 * 0.99)
+
+
+def test_config3_volume_full_size_sampled(qsl, oracle_mod):
+    """8 charges on 384^3 (FP32), Q/FLL at 512 x 512 x 256 cell-centre seeds and
+    the 3D FLEDGE of the length volume, in the launch configuration the bench
+    uses; sampled seeds against the FP64 oracle, FLEDGE against the oracle's
+    Sobel on a sub-block."""
+    ch = inputs.random_charges(8, 3)
+    gf = inputs.charge_field(ch, 384, dtype=torch.float32, device="cuda", slab=32)
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
+    nx, ny, nz = 512, 512, 256
+    N = nx * ny * nz
+    q = torch.empty(N, device="cuda")
+    L = torch.empty(N, device="cuda")
+    faces = torch.empty(2 * N, dtype=torch.uint8, device="cuda")
+    st = torch.empty(N, dtype=torch.uint8, device="cuda")
+    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL, integrator=qsl.QSL_DOPRI5_CELL)
+    qsl.qsl_q_volume_3d(F, BOX_LO, BOX_HI, nx, ny, nz, o, q, L, faces, st)
+    S = torch.empty((nz, ny, nx), device="cuda")
+    qsl.qsl_fledge(L.view(nz, ny, nx), S)
+    torch.cuda.synchronize()
+    idx = inputs.subsample(N, 120, 11)
+    g = inputs.GridField(*(a.cpu().numpy().astype(np.float64) for a in (gf.bx, gf.by, gf.bz)), gf.xc, gf.yc, gf.zc)
+    del gf
+    Fo = oracle_mod.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
+    del g
+    seeds = oracle_mod.volume_seeds(BOX_LO, BOX_HI, nx, ny, nz)[idx]
+    ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
+    del Fo
+    fc = faces.cpu().numpy().reshape(-1, 2)
+    gd = {"q_perp": q.cpu().numpy()[idx], "L": L.cpu().numpy()[idx], "face_f": fc[idx, 0], "face_b": fc[idx, 1]}
+    compare_lines(gd, ref, 2.0 / 383, BOX_LO, BOX_HI)
+    # 3D FLEDGE on a block of the GPU length volume (the Sobel input is that same array)
+    Lb = L.view(nz, ny, nx)[100:140, 200:260, 300:350].contiguous().cpu().numpy()
+    Sb = S[101:139, 201:259, 301:349].cpu().numpy()
+    want = oracle_mod.fledge(Lb)[1:-1, 1:-1, 1:-1]
+    assert np.allclose(Sb, want, rtol=1e-4, atol=1e-4 * want.max())
