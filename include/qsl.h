@@ -267,6 +267,34 @@ int qsl_plan_launch(qsl_plan* plan, void* stream);
 int qsl_plan_stats(qsl_plan* plan, void* stream, qsl_stats* out);
 void qsl_plan_free(qsl_plan* plan);
 
+/* ---- learned refinement proposal (spec addition; the paper has none) -------
+ * A 3-layer CNN over coarse tiles with 2 channels (normalised FLEDGE, log10 Q)
+ * giving, per coarse cell, the probability that FLL-jump refinement
+ * (Sec. "Adaptive refinements") will sample inside it:
+ *   conv3x3 2->32 + ReLU, conv3x3 32->32 + ReLU, conv3x3 32->1 (logit),
+ * zero padding, stride 1. Weights are BF16 in the passes (FP32 master copy and
+ * Adam state); contractions accumulate in FP32. Parameters, flattened in this
+ * order: w1[32][2][3][3], b1[32], w2[32][32][3][3], b2[32], w3[1][32][3][3],
+ * b3[1] (QSL_CNN_NPARAMS floats). Tensors are NCHW float32 in device memory. */
+#define QSL_CNN_NPARAMS (32 * 2 * 9 + 32 + 32 * 32 * 9 + 32 + 32 * 9 + 1)
+typedef struct qsl_cnn qsl_cnn;
+/* params: host array of QSL_CNN_NPARAMS floats (initial FP32 master). */
+int qsl_cnn_create(const float* params, qsl_cnn** out);
+/* Copies the FP32 master parameters to host memory. */
+int qsl_cnn_params(const qsl_cnn* cnn, float* params);
+/* prob[n][h][w] = sigmoid(logit) for x[n][2][h][w]. */
+int qsl_cnn_forward(qsl_cnn* cnn, const float* x, int n, int h, int w, float* prob, void* stream);
+/* Mean binary cross-entropy over pixels, pos_weight * y * softplus(-z) +
+ * (1 - y) * softplus(z), and its gradient w.r.t. the parameters (device,
+ * QSL_CNN_NPARAMS floats; overwritten). loss: one device float. */
+int qsl_cnn_loss_grad(qsl_cnn* cnn, const float* x, const float* y, int n, int h, int w, float pos_weight,
+                      float* loss, float* grad, void* stream);
+/* One Adam update (bias-corrected) of the FP32 master from `grad`; refreshes
+ * the BF16 weights. */
+int qsl_cnn_adam_step(qsl_cnn* cnn, const float* grad, float lr, float beta1, float beta2, float eps, void* stream);
+void qsl_cnn_free(qsl_cnn* cnn);
+int qsl_cnn_nparams(void);
+
 /* ---- autotuner -----------------------------------------------------------------
  * Picks, on a sample of S seeds (device memory, S >= 1) of the caller's
  * workload:

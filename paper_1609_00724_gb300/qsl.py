@@ -115,6 +115,12 @@ def lib():
     L.qsl_plan_launch.argtypes = [vp, vp]
     L.qsl_plan_stats.argtypes = [vp, vp, C.POINTER(qsl_stats)]
     L.qsl_plan_free.argtypes = [vp]
+    L.qsl_cnn_create.argtypes = [vp, C.POINTER(vp)]
+    L.qsl_cnn_params.argtypes = [vp, vp]
+    L.qsl_cnn_forward.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+    L.qsl_cnn_loss_grad.argtypes = [vp, vp, vp, i32, i32, i32, C.c_float, vp, vp, vp]
+    L.qsl_cnn_adam_step.argtypes = [vp, vp, C.c_float, C.c_float, C.c_float, C.c_float, vp]
+    L.qsl_cnn_free.argtypes = [vp]
     L.qsl_autotune.argtypes = [vp, vp, i64, C.POINTER(qsl_opts), C.POINTER(qsl_tune_report), vp]
     L.qsl_trace_seeds_noalloc.argtypes = [vp, vp, i64, C.POINTER(qsl_opts), vp, vp]
     _lib = L
@@ -271,6 +277,48 @@ def qsl_autotune(field, seeds, opts, stream=None):
     return {k: getattr(rep, k) for k, _ in rep._fields_}
 
 
+QSL_CNN_NPARAMS = 32 * 2 * 9 + 32 + 32 * 32 * 9 + 32 + 32 * 9 + 1
+
+
+class Cnn:
+    """The refinement-proposal CNN (qsl_cnn_*): forward, loss/gradient, Adam."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == QSL_CNN_NPARAMS
+        h = C.c_void_p()
+        _check(lib().qsl_cnn_create(p.ctypes.data_as(C.c_void_p), C.byref(h)))
+        self.handle = h
+
+    def params(self):
+        out = np.zeros(QSL_CNN_NPARAMS, dtype=np.float32)
+        _check(lib().qsl_cnn_params(self.handle, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def forward(self, x, prob=None, stream=None):
+        n, c, h, w = x.shape
+        assert c == 2
+        if prob is None:
+            import torch
+            prob = torch.empty((n, h, w), dtype=torch.float32, device=x.device)
+        _check(lib().qsl_cnn_forward(self.handle, _ptr(x), n, h, w, _ptr(prob), _stream(stream)))
+        return prob
+
+    def loss_grad(self, x, y, pos_weight, loss, grad, stream=None):
+        n, c, h, w = x.shape
+        _check(lib().qsl_cnn_loss_grad(self.handle, _ptr(x), _ptr(y), n, h, w, C.c_float(pos_weight), _ptr(loss),
+                                       _ptr(grad), _stream(stream)))
+
+    def adam(self, grad, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check(lib().qsl_cnn_adam_step(self.handle, _ptr(grad), C.c_float(lr), C.c_float(beta1), C.c_float(beta2),
+                                       C.c_float(eps), _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qsl_cnn_free(self.handle)
+            self.handle = None
+
+
 QSL_NOALLOC_MAX_SEEDS = 65536
 
 
@@ -373,4 +421,6 @@ def qsl_last_stats():
 EXPORTS = ["qsl_opts_default", "qsl_load_field", "qsl_free_field", "qsl_trace_seeds", "qsl_q_map_2d",
            "qsl_q_volume_3d", "qsl_fledge", "qsl_refine", "qsl_hilbert_encode", "qsl_hilbert_decode", "qsl_convert",
            "qsl_last_error", "qsl_last_stats", "qsl_trace_seeds_noalloc", "qsl_kernel_launches", "qsl_q_map_batch",
-           "qsl_plan_q_map_batch", "qsl_plan_launch", "qsl_plan_stats", "qsl_plan_free", "qsl_autotune"]
+           "qsl_plan_q_map_batch", "qsl_plan_launch", "qsl_plan_stats", "qsl_plan_free", "qsl_autotune",
+           "qsl_cnn_create", "qsl_cnn_params", "qsl_cnn_forward", "qsl_cnn_loss_grad", "qsl_cnn_adam_step",
+           "qsl_cnn_free", "qsl_cnn_nparams"]
