@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--integrator", default="cell", choices=["cell", "ck"],
                     help="cell: cell-wise Dormand-Prince (default); ck: the paper's plain Cash-Karp")
     ap.add_argument("--tol", type=float, default=None)
-    ap.add_argument("--config", default="refine2d", choices=["refine2d", "volume", "batch64"],
+    ap.add_argument("--config", default="refine2d", choices=["refine2d", "volume", "batch64", "learned"],
                     help="refine2d: 1024^2 map refined to 4096^2 (default); volume: 512x512x256 Q/FLL/FLEDGE volume "
                          "of an 8-charge field on 384^3")
     ap.add_argument("--profile-map", action="store_true",
@@ -380,6 +380,75 @@ def run_batch(args, qsl, torch, dev, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_learned(args, qsl, torch, dev, rank, world, local):
+    """Config 5: the learned refinement proposal. Training: 2000 tracer-generated
+    maps (random 4-12-charge fields on 128^3, coarse 128^2 z=0 cuts refined two
+    orders by the plain criterion). Evaluation: an 8-charge field on 512^3, a
+    coarse 256 x 256 x 128 cell-centre volume refined two orders (1024 x 1024 x
+    512 effective). Compared: wall time of the plain criterion with FP64
+    everywhere against the learned proposal (CNN on the coarse z-slices) with
+    FP32 tracing and the plain criterion as fallback; recall of the plain
+    run's samples."""
+    from paper_1609_00724_gb300 import inputs, learned
+    n_train = int(os.environ.get("QSL_LEARNED_MAPS", "2000"))
+    o32 = opts(qsl)
+    o64 = qsl.qsl_opts_default(tol_abs=RUN["tol"], tol_rel=RUN["tol"], integrator=INTEGRATOR[RUN["integrator"]],
+                               precision=qsl.QSL_FP64)
+    ot = qsl.qsl_opts_default(tol_abs=1e-6, tol_rel=1e-6, integrator=INTEGRATOR[RUN["integrator"]])
+    X, Y, t_data = learned.make_training_set(n_train, grid=128, coarse=128, levels=2, tau=TAU, seed0=5000, opts=ot,
+                                             device=dev)
+    n_fit = int(0.9 * n_train)
+    t0 = time.perf_counter()
+    net, hist, pw = learned.train(X[:n_fit], Y[:n_fit], epochs=12, batch=32, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    thr, frac = learned.calibrate(net, X[n_fit:], Y[n_fit:], recall=0.995)
+    del X, Y
+    gf = inputs.charge_field(inputs.random_charges(8, 5), 512, dtype=torch.float32, device=dev, slab=16)
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
+    del gf
+    coarse = (256, 256, 128)  # x, y, z
+    cap = int(os.environ.get("QSL_LEARNED_CAPACITY", str(96 * 1024 * 1024)))
+    spec = learned.volume_spec(coarse, 2, TAU)
+    res = {}
+    # plain criterion, FP64 everywhere
+    smp = learned.Samples(cap, dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_p, it_p, tr_p, rc_p = smp.refine(F, spec, o64)
+    torch.cuda.synchronize()
+    res["plain_fp64"] = {"seconds": time.perf_counter() - t0, "samples": n_p, "iters": it_p, "rc": rc_p}
+    plain_keys = smp.key[:n_p].clone()
+    del smp
+    # learned proposal + FP32, plain criterion as fallback
+    smp = learned.Samples(cap, dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    smp.refine(F, learned.volume_spec(coarse, 2, TAU, max_iters=0), o32)
+    L, Q, _ = learned.coarse_grids(smp, 3, spec.max_order, 2, coarse[::-1])
+    mask = learned.propose(net, learned.features_slices(L, Q), thr).contiguous()
+    n_l, it_l, tr_l, rc_l = smp.refine(F, learned.volume_spec(coarse, 2, TAU, proposal=mask), o32)
+    torch.cuda.synchronize()
+    res["learned_fp32"] = {"seconds": time.perf_counter() - t0, "samples": n_l, "iters": it_l, "rc": rc_l,
+                           "proposed_cells": int(mask.sum().item())}
+    lk = smp.key[:n_l]
+    pos = torch.searchsorted(lk, plain_keys)
+    pos = pos.clamp(max=n_l - 1)
+    hit = (lk[pos] == plain_keys)
+    recall = float(hit.float().mean().item())
+    line = {"metric": "refined-map wall time: learned proposal + FP32 vs plain FP64 (recall of plain samples)",
+            "value": res["plain_fp64"]["seconds"] / res["learned_fp32"]["seconds"], "unit": "x speed-up",
+            "n_gpus": world, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "8-charge field 512^3, coarse 256x256x128 -> 1024x1024x512 effective",
+                       "training": {"maps": n_train, "data_s": t_data, "train_s": t_train, "final_loss": hist[-1],
+                                    "pos_weight": pw, "threshold": thr, "proposed_frac_heldout": frac},
+                       "tau": TAU, "tol": RUN["tol"]},
+            "results": res, "recall": recall}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     RUN["integrator"] = args.integrator
@@ -396,8 +465,9 @@ def main():
     dev = torch.device("cuda", local)
     from paper_1609_00724_gb300 import qsl
     qsl.lib()
-    if args.config in ("volume", "batch64"):
-        (run_volume if args.config == "volume" else run_batch)(args, qsl, torch, dev, rank, world, local)
+    if args.config in ("volume", "batch64", "learned"):
+        {"volume": run_volume, "batch64": run_batch, "learned": run_learned}[args.config](
+            args, qsl, torch, dev, rank, world, local)
         if world > 1:
             torch.distributed.destroy_process_group()
         return

@@ -119,10 +119,12 @@ __global__ void coarse_keys_kernel(int64_t n, int nd, int bits, int R, int nc0, 
   }
 }
 
-// Proposal: every effective cell of the flagged coarse cells except the coarse
-// sample itself (it already exists). One thread per (flagged cell, sub-cell).
+// Proposal: every effective cell of the flagged coarse cells that is not
+// already a sample (binary search in the sorted keys). One thread per
+// (flagged cell, sub-cell).
 __global__ void proposal_keys_kernel(const int64_t* __restrict__ cells, const int64_t* ncells_dev, int nd, int bits,
-                                     int R, int nc0, int nc1, uint64_t* keys, int64_t* count) {
+                                     int R, int nc0, int nc1, const uint64_t* __restrict__ have, int64_t n_have,
+                                     uint64_t* keys, int64_t* count) {
   int64_t ncells = *ncells_dev;
   int64_t per = 1;
   for (int a = 0; a < nd; ++a) per *= R;
@@ -132,10 +134,16 @@ __global__ void proposal_keys_kernel(const int64_t* __restrict__ cells, const in
     int64_t i = cell % nc0, rem = cell / nc0;
     int64_t j = rem % nc1, k = rem / nc1;
     int64_t s0 = sub % R, s1 = (sub / R) % R, s2 = nd == 3 ? sub / (R * R) : 0;
-    if (s0 == R / 2 && s1 == R / 2 && (nd == 2 || s2 == R / 2)) continue;
     uint32_t c[3] = {(uint32_t)(i * R + s0), (uint32_t)(j * R + s1), (uint32_t)(k * R + s2)};
+    uint64_t key = hilbert_key_dev(c, nd, bits);
+    int64_t lo = 0, hi = n_have;  // already a sample?
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if (have[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    if (lo < n_have && have[lo] == key) continue;
     unsigned long long pos = atomicAdd((unsigned long long*)count, 1ull);
-    keys[pos] = hilbert_key_dev(c, nd, bits);
+    keys[pos] = key;
   }
 }
 
@@ -467,40 +475,56 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
     QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, kA, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     if ((rc = trace_and_merge(0, m))) return rc;
     n = m;
-    // optional proposal: flagged coarse cells are sampled densely
-    if (sp->proposal) {
-      const uint8_t* mask = sp->proposal;
-      uint8_t* mask_dev = nullptr;
-      if (mem_proposal == QSL_MEM_HOST) {
-        if ((rc = sc.alloc(&mask_dev, m))) return rc;
-        QSL_CHECK_CUDA(cudaMemcpyAsync(mask_dev, mask, m, cudaMemcpyHostToDevice, s));
-        mask = mask_dev;
-      }
-      int64_t* cells = nullptr;
-      if ((rc = sc.alloc(&cells, m))) return rc;
-      QSL_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t), s));
-      mask_cells_kernel<<<grid_for(m), 256, 0, s>>>(mask, m, cells, cnt);
-      qsl::count_launch();
-      QSL_CHECK_CUDA(cudaMemcpyAsync(cnt_h, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-      QSL_CHECK_CUDA(cudaStreamSynchronize(s));
-      int64_t ncells = *cnt_h;
-      int64_t per = 1;
-      for (int a = 0; a < nd; ++a) per *= R;
-      int64_t want = ncells * (per - 1);
-      if (want > cap - n) {
-        set_error("capacity too small for the proposal (%lld more samples)", (long long)want);
-        return QSL_ECAPACITY;
-      }
+  }
+  // optional proposal (fresh runs and resumed ones): every effective cell of
+  // the flagged coarse cells that is not a sample yet is traced, before the
+  // FLL-jump iterations, which then continue as the fallback criterion
+  if (sp->proposal) {
+    int nc[3] = {1, 1, 1};
+    for (int a = 0; a < nd; ++a) nc[a] = ext[a] / R;
+    int64_t m = (int64_t)nc[0] * nc[1] * nc[2];
+    const uint8_t* mask = sp->proposal;
+    uint8_t* mask_dev = nullptr;
+    if (mem_proposal == QSL_MEM_HOST) {
+      if ((rc = sc.alloc(&mask_dev, m))) return rc;
+      QSL_CHECK_CUDA(cudaMemcpyAsync(mask_dev, mask, m, cudaMemcpyHostToDevice, s));
+      mask = mask_dev;
+    }
+    int64_t* cells = nullptr;
+    if ((rc = sc.alloc(&cells, m))) return rc;
+    QSL_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t), s));
+    mask_cells_kernel<<<grid_for(m), 256, 0, s>>>(mask, m, cells, cnt);
+    qsl::count_launch();
+    QSL_CHECK_CUDA(cudaMemcpyAsync(cnt_h, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    QSL_CHECK_CUDA(cudaStreamSynchronize(s));
+    int64_t ncells = *cnt_h;
+    int64_t per = 1;
+    for (int a = 0; a < nd; ++a) per *= R;
+    int64_t want = ncells * per;
+    if (want > cap - n) {
+      set_error("capacity too small for the proposal (up to %lld more samples)", (long long)want);
+      return QSL_ECAPACITY;
+    }
+    if (want > 0) {
       int64_t* ncd = nullptr;
       if ((rc = sc.alloc(&ncd, 1))) return rc;
       QSL_CHECK_CUDA(cudaMemcpyAsync(ncd, cnt, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
       QSL_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t), s));
-      if (want > 0) {
-        proposal_keys_kernel<<<grid_for(want), 256, 0, s>>>(cells, ncd, nd, p, R, nc[0], nc[1], smp->key + n, cnt);
+      proposal_keys_kernel<<<grid_for(want), 256, 0, s>>>(cells, ncd, nd, p, R, nc[0], nc[1], smp->key, n,
+                                                            smp->key + n, cnt);
+      qsl::count_launch();
+      QSL_CHECK_CUDA(cudaGetLastError());
+      QSL_CHECK_CUDA(cudaMemcpyAsync(cnt_h, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      QSL_CHECK_CUDA(cudaStreamSynchronize(s));
+      int64_t got = *cnt_h;
+      if (got > 0) {
+        // trace the new cells in curve order (neighbouring seeds on neighbouring lanes)
+        iota_kernel<<<grid_for(got), 256, 0, s>>>(perm, got);
         qsl::count_launch();
-        QSL_CHECK_CUDA(cudaGetLastError());
-        if ((rc = trace_and_merge(n, want))) return rc;
-        n += want;
+        if ((rc = sort_pairs(smp->key + n, kA, perm, perm2, got, nd * p, s))) return rc;
+        QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key + n, kA, got * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        if ((rc = trace_and_merge(n, got))) return rc;
+        n += got;
       }
     }
   }
