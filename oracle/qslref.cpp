@@ -301,11 +301,39 @@ void land(const Field& F, const Opts& o, const double* lo, const double* hi, int
     }
     double a = 0.0, b = hi_h;
     double ga = face_g(lo, hi, face, y), gb = face_g(lo, hi, face, yhi);
+    if (!(ga < 0.0)) {
+      // The step starts on this face (a seed on the face whose field points
+      // into the domain) and ends beyond it again: the line's end is the
+      // later crossing, not lambda = 0. Halve the step until a point inside
+      // brackets that crossing; if none is found the line only grazes the face.
+      double hh = hi_h;
+      bool found = false;
+      for (int k = 0; k < 60 && !found; ++k) {
+        hh *= 0.5;
+        any_step(F, o, s, ncomp, y, hh, ym, yerr, st);
+        if (st) st->landing += 1;
+        e->steps += 1;
+        double gg = face_g(lo, hi, face, ym);
+        if (gg < 0.0) {
+          a = hh;
+          ga = gg;
+          found = true;
+        } else {
+          b = hh;
+          gb = gg;
+        }
+      }
+      if (!found) {
+        a = 0.0;
+        ga = 0.0;
+        b = 0.0;
+      }
+    }
     int side = 0;
     hm = b;
     std::memcpy(ym, yhi, sizeof(double) * ncomp);
     for (int it = 0; it < 200; ++it) {
-      hm = a + (b - a) * ga / (ga - gb);
+      hm = (b > a) ? a + (b - a) * ga / (ga - gb) : a;
       any_step(F, o, s, ncomp, y, hm, ym, yerr, st);
       if (st) st->landing += 1;
       e->steps += 1;

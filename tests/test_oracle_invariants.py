@@ -172,3 +172,31 @@ def test_footpoint_fd_on_bottom_face(oracle_mod):
         assert abs(q_fd / r["q_foot"][i] - 1) < 3 * fl + 1e-5, (x0, q_fd, r["q_foot"][i], fl)
         checked += 1
     assert checked >= 8
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_loop_from_face_is_continuous(oracle_mod, fields, mode):
+    """A seed on z = 0 where the field points weakly inward can loop back to
+    the same face: the line's length is the later crossing, continuous in the
+    seed. Moving the seed a distance d inside changes L by O(d), so the
+    difference must shrink tenfold from d = 1e-9 to d = 1e-10 (a landing that
+    stops at the start point would give L = 0 and a difference of L)."""
+    F = fields[mode]
+    n = 24
+    xs = np.linspace(-0.97, 0.97, 90)
+    s = np.stack(np.meshgrid(xs, xs, indexing="ij"), -1).reshape(-1, 2)
+    seeds = np.concatenate([s, np.zeros((len(s), 1))], 1)
+    o = oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11)
+    r = oracle_mod.trace_seeds(F, seeds, o)
+    loop = (r["face_f"] == 4) & (r["face_b"] == 4) & (r["L"] < 0.5 / (n - 1))
+    near_zero = np.where(loop)[0]
+    assert len(near_zero) >= 10
+    idx = near_zero[:30]
+    diffs = []
+    for d in (1e-9, 1e-10):
+        s2 = seeds[idx].copy()
+        s2[:, 2] += d
+        r2 = oracle_mod.trace_seeds(F, s2, o)
+        diffs.append(np.abs(r2["L"] - r["L"][idx]))
+    assert np.all(r["L"][idx] > 0)
+    assert np.all(diffs[1] <= 0.2 * diffs[0] + 1e-12), np.c_[r["L"][idx], diffs[0], diffs[1]]
