@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--integrator", default="cell", choices=["cell", "ck"],
                     help="cell: cell-wise Dormand-Prince (default); ck: the paper's plain Cash-Karp")
     ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (fixed tolerance and shape)")
     ap.add_argument("--config", default="refine2d", choices=["refine2d", "volume", "batch64", "learned"],
                     help="refine2d: 1024^2 map refined to 4096^2 (default); volume: 512x512x256 Q/FLL/FLEDGE volume "
                          "of an 8-charge field on 384^3")
@@ -135,8 +136,11 @@ RUN = {"integrator": "cell", "tol": TOL}
 
 
 def opts(qsl):
-    return qsl.qsl_opts_default(tol_abs=RUN["tol"], tol_rel=RUN["tol"], q_form=qsl.QSL_Q_PERP,
-                                integrator=INTEGRATOR[RUN["integrator"]])
+    o = qsl.qsl_opts_default(tol_abs=RUN["tol"], tol_rel=RUN["tol"], q_form=qsl.QSL_Q_PERP,
+                             integrator=INTEGRATOR[RUN["integrator"]])
+    if "shape" in RUN:
+        o.warps_per_block, o.blocks_per_sm, o.refill_min = RUN["shape"]
+    return o
 
 
 def spec(qsl, coarse):
@@ -220,11 +224,52 @@ def parity_sample(qsl, gf, gf_cpu, coarse, n=200):
     fg = fc.cpu().numpy().reshape(-1, 2)[idx]
     ok = np.isfinite(ref["q_perp"]) & (ref["q_perp"] < 1e6)
     qe = np.abs(qg[ok] / ref["q_perp"][ok] - 1)
-    pos = ref["L"] > 0
-    le = np.abs(lg[pos] / ref["L"][pos] - 1)
+    # length error relative to max(L, one cell): sub-cell loops are held to an
+    # absolute bound (their length is set by a cancellation in B_n)
+    cell = float(min(np.min(np.diff(a)) for a in (g.xc, g.yc, g.zc)))
+    pos = np.isfinite(ref["L"])
+    le = np.abs(lg[pos] - ref["L"][pos]) / np.maximum(ref["L"][pos], cell)
     faces_eq = float(np.mean((fg[:, 0] == ref["face_f"]) & (fg[:, 1] == ref["face_b"])))
     return {"n": int(n), "q_max_rel": float(qe.max()), "q_p99_rel": float(np.quantile(qe, 0.99)),
             "l_max_rel": float(le.max()), "faces_equal": faces_eq}
+
+
+def refined_parity(bufs, n_samples, gf_cpu, coarse, n=200):
+    """Refined samples (keys off the coarse lattice, i.e. placed by the FLL-jump
+    criterion near QSLs) of the last step against the FP64 oracle at tol 1e-11;
+    lattice positions come from the oracle's own Hilbert decode."""
+    import oracle
+    from paper_1609_00724_gb300 import inputs
+    eff = coarse << (P - P0)
+    p = int(np.log2(eff))
+    R = eff // coarse
+    keys = bufs["key"][:n_samples].cpu().numpy()
+    q = bufs["q"][:n_samples].cpu().numpy()
+    L = bufs["L"][:n_samples].cpu().numpy()
+    pick = inputs.subsample(n_samples, min(n_samples, 40 * n), 23)
+    seeds, idx = [], []
+    for i in pick:
+        c = oracle.hilbert_coords(int(keys[i]), 2, p)
+        if c[0] % R == R // 2 and c[1] % R == R // 2:
+            continue  # coarse-lattice sample
+        a, b = (c[0] + 0.5) / eff - 0.5, (c[1] + 0.5) / eff - 0.5
+        seeds.append([2 * a, 2 * b, 0.0])
+        idx.append(i)
+        if len(idx) == n:
+            break
+    g = inputs.to_numpy64(gf_cpu)
+    Fo = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
+    ref = oracle.trace_seeds(Fo, np.array(seeds), oracle.default_opts(tol_abs=1e-11, tol_rel=1e-11,
+                                                                       nthreads=os.cpu_count()))
+    idx = np.array(idx)
+    ok = np.isfinite(ref["q_perp"]) & (ref["q_perp"] < 1e6)
+    qe = np.abs(q[idx][ok] / ref["q_perp"][ok] - 1)
+    cell = float(min(np.min(np.diff(a)) for a in (g.xc, g.yc, g.zc)))
+    pos = np.isfinite(ref["L"])
+    le = np.abs(L[idx][pos] - ref["L"][pos]) / np.maximum(ref["L"][pos], cell)
+    return {"n": int(len(idx)), "q_checked": int(ok.sum()), "q_max_rel": float(qe.max()),
+            "q_p99_rel": float(np.quantile(qe, 0.99)), "l_max_rel": float(le.max()),
+            "q_median": float(np.median(ref["q_perp"][ok]))}
 
 
 def run_reference(args, rank, world):
@@ -407,7 +452,7 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
     gf = inputs.charge_field(inputs.random_charges(8, 5), 512, dtype=torch.float32, device=dev, slab=16)
     F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
     del gf
-    coarse = (256, 256, 128)  # x, y, z
+    coarse = tuple(int(v) for v in os.environ.get("QSL_LEARNED_COARSE", "256,256,128").split(","))  # x, y, z
     cap = int(os.environ.get("QSL_LEARNED_CAPACITY", str(96 * 1024 * 1024)))
     spec = learned.volume_spec(coarse, 2, TAU)
     res = {}
@@ -419,6 +464,17 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
     torch.cuda.synchronize()
     res["plain_fp64"] = {"seconds": time.perf_counter() - t0, "samples": n_p, "iters": it_p, "rc": rc_p}
     plain_keys = smp.key[:n_p].clone()
+    ext = [c * 4 for c in coarse]
+    out_order = spec.max_order - 1
+    qp = learned.converted_q(smp, 3, spec.max_order, ext, out_order)
+    del smp
+    # plain criterion with FP32 tracing (what the network is compared with)
+    smp = learned.Samples(cap, dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_3, it_3, _, rc_3 = smp.refine(F, spec, o32)
+    torch.cuda.synchronize()
+    res["plain_fp32"] = {"seconds": time.perf_counter() - t0, "samples": n_3, "iters": it_3, "rc": rc_3}
     del smp
     # learned proposal + FP32, plain criterion as fallback
     smp = learned.Samples(cap, dev)
@@ -426,7 +482,8 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
     t0 = time.perf_counter()
     smp.refine(F, learned.volume_spec(coarse, 2, TAU, max_iters=0), o32)
     L, Q, _ = learned.coarse_grids(smp, 3, spec.max_order, 2, coarse[::-1])
-    mask = learned.propose(net, learned.features_slices(L, Q), thr).contiguous()
+    budget = max(0, int(0.8 * (cap - smp.count) / 64))
+    mask = learned.propose(net, learned.features_slices(L, Q), thr, budget=budget).contiguous()
     n_l, it_l, tr_l, rc_l = smp.refine(F, learned.volume_spec(coarse, 2, TAU, proposal=mask), o32)
     torch.cuda.synchronize()
     res["learned_fp32"] = {"seconds": time.perf_counter() - t0, "samples": n_l, "iters": it_l, "rc": rc_l,
@@ -436,6 +493,10 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
     pos = pos.clamp(max=n_l - 1)
     hit = (lk[pos] == plain_keys)
     recall = float(hit.float().mean().item())
+    ql = learned.converted_q(smp, 3, spec.max_order, ext, out_order)
+    qsl_pix = torch.nan_to_num(qp, nan=0.0) >= 100.0
+    qsl_recall = float(((torch.nan_to_num(ql, nan=0.0) >= 100.0) & qsl_pix).sum().item() /
+                       max(1, int(qsl_pix.sum().item())))
     line = {"metric": "refined-map wall time: learned proposal + FP32 vs plain FP64 (recall of plain samples)",
             "value": res["plain_fp64"]["seconds"] / res["learned_fp32"]["seconds"], "unit": "x speed-up",
             "n_gpus": world, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
@@ -444,7 +505,8 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
                        "training": {"maps": n_train, "data_s": t_data, "train_s": t_train, "final_loss": hist[-1],
                                     "pos_weight": pw, "threshold": thr, "proposed_frac_heldout": frac},
                        "tau": TAU, "tol": RUN["tol"]},
-            "results": res, "recall": recall}
+            "results": res, "sample_recall": recall, "qsl_pixel_recall": qsl_recall,
+            "qsl_pixels": int(qsl_pix.sum().item()), "recall_grid": [e >> 1 for e in ext]}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -484,6 +546,19 @@ def main():
                           "stage_evals": st["stage_evals"], "retraced": st["retraced"]}))
         return
     bufs = alloc(torch, args.coarse, dev)
+    # autotune (tolerance and launch shape) on 131072 seeds of the coarse map
+    from paper_1609_00724_gb300 import inputs as _inp
+    c = args.coarse
+    pick = _inp.subsample(c * c, min(131072, c * c), 17)
+    ii, jj = pick % c, pick // c
+    sd = np.column_stack([-1 + (ii + 0.5) * 2 / c, -1 + (jj + 0.5) * 2 / c, np.zeros(len(pick))])
+    F0 = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
+    tuned = opts(qsl)
+    tune_rep = qsl.qsl_autotune(F0, torch.as_tensor(sd).to(dev), tuned) if not args.no_tune else None
+    del F0
+    if tune_rep:
+        RUN["tol"] = tuned.tol_rel
+        RUN["shape"] = (tuned.warps_per_block, tuned.blocks_per_sm, tuned.refill_min)
 
     def barrier():
         if world > 1:
@@ -557,6 +632,7 @@ def main():
                        "tol": RUN["tol"], "integrator": RUN["integrator"], "tau": TAU, "coarse_order": int(np.log2(args.coarse)), "max_order":
                            int(np.log2(eff)), "interp": "paper (normalise first)", "precision": "FP32 trace, FP64 Q",
                        "l2": "inputs larger than L2 (268 MB packed field)", "parallelism": "replicas x%d" % world,
+                       "autotune": tune_rep,
                        "samples_per_step": info.get("samples"), "refine_iters": info.get("iters"),
                        "q_points_per_step": traced_total // max(args.steps, 1)},
             "clocks": clk.summary(),
@@ -576,6 +652,7 @@ def main():
                                 "sample": "%d seeded seeds of the %d^2 coarse map, tol %g, %.1f s"
                                           % (nseeds, args.coarse, TOL, secs)}
         line["parity"] = parity_sample(qsl, gf, gf_cpu, args.coarse)
+        line["parity_refined"] = refined_parity(bufs, int(info.get("samples") or 0), gf_cpu, args.coarse)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

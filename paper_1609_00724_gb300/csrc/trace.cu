@@ -675,6 +675,12 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
             lit = 0;
             lround = 0;
             lhm = la + (lb - la) * lga / (lga - lgb);
+            if (!(lga < R(0))) {
+              // the step starts on this face and ends beyond it again (a line
+              // curving back out): seek an inside point by halving first
+              lside = 2;
+              lhm = R(0.5) * lb;
+            }
           }
         }
       } else {
@@ -685,7 +691,19 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
         // the step increment along the face normal
         R dn = fabs(lface >> 1 == 0 ? dy[0] : (lface >> 1 == 1 ? dy[1] : dy[2]));
         R gtol = fmax(E->land_tol, R(4) * eps_of<R>() * dn);
-        if (fabs(gm) <= gtol || lit >= 60 || !isfinite(gm) || !(lb - la > eps_of<R>() * lb)) {
+        if (lside == 2 && lit < 60 && isfinite(gm)) {
+          // seeking an inside point below the outside step lb
+          if (gm < R(0)) {
+            la = lhm;
+            lga = gm;
+            lside = 0;
+            lhm = la + (lb - la) * lga / (lga - lgb);
+          } else {
+            lb = lhm;
+            lgb = gm;
+            lhm = R(0.5) * lhm;
+          }
+        } else if (fabs(gm) <= gtol || lit >= 60 || !isfinite(gm) || !(lb - la > eps_of<R>() * lb)) {
           R worst = R(-1);
 #pragma unroll
           for (int f = 0; f < 6; ++f)
@@ -705,6 +723,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
             lside = 0;
             lit = 0;
             lhm = la + (lb - la) * lga / (lga - lgb);
+            if (!(lga < R(0))) {
+              lside = 2;
+              lhm = R(0.5) * lb;
+            }
           } else {
 #pragma unroll
             for (int i = 0; i < NC; ++i) y[i] += dy[i];
@@ -1105,18 +1127,25 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
                        R(DD6) * (a == 0 ? k6[0] : (a == 1 ? k6[1] : k6[2])) + R(DD7) * k7a);
           R bspl = hh * k1a - dya;
           R c3 = dya - hh * k7a - bspl;
+          // The offset along the axis is t * P(t) with the cubic
+          // P(t) = dya + (1 - t) (bspl + t (c3 + (1 - t) c4)). A step that
+          // starts on the plane (r = 0: a seed on a domain face, or the face
+          // just entered) has the trivial root t = 0; the crossing sought is
+          // the root of P, so P is solved instead (the root t = 0 divided out).
+          const bool defl = (r == R(0));
           // bracket the first crossing
           R ta = R(0), tb = R(1);
 #pragma unroll
           for (int q = 1; q < 4; ++q) {
             R tq = R(0.25) * R(q);
             R s1 = R(1) - tq;
-            R f = tq * (dya + s1 * (bspl + tq * (c3 + s1 * c4))) - r;
+            R pq = dya + s1 * (bspl + tq * (c3 + s1 * c4));
+            R f = defl ? pq : tq * pq - r;
             if (sg * f > R(0) && tb == R(1)) tb = tq;
             else if (tb == R(1)) ta = tq;
           }
           R t = ta + (tb - ta) * R(0.5);
-          {
+          if (!defl) {
             // chord estimate inside the bracket as the first iterate
             R tl = r / dya;
             if (tl > ta && tl < tb) t = tl;
@@ -1125,12 +1154,14 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
             R s1 = R(1) - t;
             R inner = c3 + s1 * c4;
             R mid = bspl + t * inner;
-            R f = t * (dya + s1 * mid) - r;
+            R pv = dya + s1 * mid;
+            R f = defl ? pv : t * pv - r;
             if (fabs(f) <= R(4) * eps_of<R>() * (fabs(r) + fabs(dya)) || !(tb - ta > R(2) * eps_of<R>())) break;
             if (sg * f > R(0)) tb = t;
             else ta = t;
             R dmid = inner - t * c4;
-            R df = dya + s1 * mid + t * (s1 * dmid - mid);
+            R dp = s1 * dmid - mid;
+            R df = defl ? dp : pv + t * dp;
             R tn = t - f / df;
             t = (tn > ta && tn < tb) ? tn : R(0.5) * (ta + tb);
           }

@@ -44,9 +44,11 @@ int time_trace(const qsl_field* f, const double* seeds, int64_t S, const qsl_opt
 }
 
 // Worst relative errors of `got` against `ref` (Q below 1e6 and both ends on
-// the same faces; lengths where the reference is positive).
-void errors(const std::vector<qsl_line>& got, const std::vector<qsl_line>& ref, int q_form, double* eq, double* el,
-            double* face_mismatch) {
+// the same faces). Length errors are taken relative to max(L, cell): a line
+// shorter than a cell that leaves at a grazing angle has a length set by a
+// cancellation in the field samples, so it is held to an absolute bound.
+void errors(const std::vector<qsl_line>& got, const std::vector<qsl_line>& ref, int q_form, double cell, double* eq,
+            double* el, double* face_mismatch) {
   double wq = 0, wl = 0;
   int64_t fm = 0;
   for (size_t i = 0; i < ref.size(); ++i) {
@@ -59,7 +61,8 @@ void errors(const std::vector<qsl_line>& got, const std::vector<qsl_line>& ref, 
     double qa = q_form == QSL_Q_FOOT ? a.q_foot : (q_form == QSL_Q_DET ? a.q_det : a.q_perp);
     double qb = q_form == QSL_Q_FOOT ? b.q_foot : (q_form == QSL_Q_DET ? b.q_det : b.q_perp);
     if (std::isfinite(qb) && qb < 1e6) wq = fmax(wq, fabs(qa / qb - 1.0));
-    if (b.length > 0) wl = fmax(wl, fabs((double)a.length / (double)b.length - 1.0));
+    if (std::isfinite(b.length))
+      wl = fmax(wl, fabs((double)a.length - (double)b.length) / fmax((double)b.length, cell));
   }
   *eq = wq;
   *el = wl;
@@ -105,7 +108,7 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
   double ms = 0;
   if ((rc = time_trace(f, seeds, S, &r, d.p, s, &ms))) return rc;
   QSL_CHECK_CUDA(cudaMemcpy(ref.data(), d.p, sizeof(qsl_line) * S, cudaMemcpyDeviceToHost));
-  // tolerance: the loosest candidate within a tenth of the parity bar
+  // tolerance: the loosest candidate within a fifth of the parity bar
   const double tols[] = {1e-5, 1e-6, 1e-7, 1e-8};
   qsl_opts base = *opts;
   base.retrace_q = 0;
@@ -115,7 +118,7 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
     c.tol_abs = c.tol_rel = t;
     if ((rc = time_trace(f, seeds, S, &c, d.p, s, &ms))) return rc;
     QSL_CHECK_CUDA(cudaMemcpy(got.data(), d.p, sizeof(qsl_line) * S, cudaMemcpyDeviceToHost));
-    errors(got, ref, opts->q_form, &eq, &el, &fm);
+    errors(got, ref, opts->q_form, f->cell, &eq, &el, &fm);
     if (eq <= 2e-4 && el <= 2e-6 && fm <= 1e-3) {
       chosen_tol = t;
       break;

@@ -205,6 +205,24 @@ def calibrate(net, X, Y, recall=0.995):
     return thr, frac
 
 
-def propose(net, X, thr):
-    """uint8 mask (same layout as X's spatial dims) of cells with p >= thr."""
-    return (predict(net, X) >= thr).to(torch.uint8).contiguous()
+def propose(net, X, thr, budget=None):
+    """uint8 mask (same layout as X's spatial dims) of cells with p >= thr;
+    with a budget, only the `budget` most probable of them."""
+    P = predict(net, X)
+    mask = P >= thr
+    if budget is not None and int(mask.sum().item()) > budget:
+        flat = torch.where(mask, P, torch.zeros_like(P)).reshape(-1)
+        top = torch.topk(flat, int(budget)).indices
+        mask = torch.zeros_like(flat, dtype=torch.bool)
+        mask[top] = True
+        mask = mask.view(P.shape)
+    return mask.to(torch.uint8).contiguous()
+
+
+def converted_q(smp, ndim, max_order, extent, out_order):
+    """Q of a sample set on the rectilinear output lattice (qsl_convert)."""
+    d = max_order - out_order
+    shape = [extent[a] >> d for a in range(ndim)][::-1]
+    out = torch.empty(int(np.prod(shape)), device=smp.key.device)
+    qsl.qsl_convert(smp.key[:smp.count], smp.q[:smp.count], ndim, max_order, list(extent), out_order, True, out)
+    return out.view(shape)

@@ -84,7 +84,7 @@ def test_batch_matches_oracle_sampled(qsl, oracle_mod):
         seeds = oracle_mod.plane_seeds(c, u, v, nu, nv)[idx]
         ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
         gd = {"q_perp": q[off + idx], "L": L[off + idx], "face_f": fc[off + idx, 0], "face_b": fc[off + idx, 1]}
-        compare_lines(gd, ref, 2.0 / (len(g.xc) - 1), (-1, -1, 0), (1, 1, 1))
+        compare_lines(gd, ref, 1.0 / (len(g.xc) - 1), (-1, -1, 0), (1, 1, 1))
         off += n
 
 
