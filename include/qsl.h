@@ -111,11 +111,15 @@ typedef struct qsl_opts {
   double domain_lo[3], domain_hi[3]; /* tracing box; lo >= hi on any axis: grid extent */
   double land_tol;         /* face landing tolerance in cells (FP32 stops at its resolution of the step) */
   double timeout_s;        /* device watchdog per launch; <= 0: none                    */
-} qsl_opts;
+  int32_t line_lanes;      /* lanes per line of QSL_DOPRI5_CELL: 1 = one lane per line,
+                              3 = a group of three lanes (one per axis), 0 = auto (three
+                              when the launch does not fill the GPU's resident warps)    */
+  int32_t reserved;        /* must be 0                                                 */
+} qsl_opts; /* 176 bytes */
 
 /* Fills the defaults: RKCK54, Q_PERP, FP32_MIXED, tol 1e-2/1e-2, h_init 0.1,
  * h_max 2, h_min 1e-15 cells, max_length 20 x diagonal, max_steps 1e6,
- * euler_h 0.2, retrace_q 1e6, land_tol 1e-12, no watchdog. */
+ * euler_h 0.2, retrace_q 1e6, land_tol 1e-12, no watchdog, line_lanes 0 (auto). */
 void qsl_opts_default(qsl_opts* opts);
 
 /* ---- per-line record (qsl_trace_seeds) --------------------------------------- */

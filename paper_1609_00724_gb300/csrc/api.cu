@@ -102,6 +102,9 @@ int validate_opts(const qsl_field* f, const qsl_opts* o) {
   if (o->warps_per_block < 0 || o->warps_per_block > 8) QSL_FAIL(QSL_EINVAL, "warps_per_block must be 0..8");
   if (o->blocks_per_sm < 0 || o->blocks_per_sm > 32) QSL_FAIL(QSL_EINVAL, "blocks_per_sm must be 0..32");
   if (o->refill_min < 0 || o->refill_min > 32) QSL_FAIL(QSL_EINVAL, "refill_min must be 0..32");
+  if (o->line_lanes != 0 && o->line_lanes != 1 && o->line_lanes != 3)
+    QSL_FAIL(QSL_EINVAL, "line_lanes must be 0, 1 or 3");
+  if (o->reserved != 0) QSL_FAIL(QSL_EINVAL, "reserved must be 0");
   return QSL_OK;
 }
 
@@ -117,6 +120,7 @@ int default_shape(const qsl_opts* o, int tangent, int precision, LaunchShape* s)
     if (s->blocks_per_sm < 1) s->blocks_per_sm = 1;
   }
   s->refill_min = o->refill_min > 0 ? o->refill_min : 1;
+  s->line_lanes = o->line_lanes;
   return QSL_OK;
 }
 
@@ -165,6 +169,8 @@ void qsl_opts_default(qsl_opts* o) {
   o->retrace_q = 1e6;
   o->land_tol = 1e-12;
   o->timeout_s = 0;
+  o->line_lanes = 0;
+  o->reserved = 0;
 }
 
 int qsl_load_field(const void* bx, const void* by, const void* bz, int dtype, int mem, int nx, int ny, int nz,

@@ -115,6 +115,7 @@ struct LaunchShape {
   int warps_per_block;
   int blocks_per_sm;
   int refill_min;
+  int line_lanes;  // cell-wise tracer: 1 or 3 lanes per line, 0 = auto
 };
 
 // Runs the tracer over `n_seeds` seeds of `src` (n_seeds may live on the

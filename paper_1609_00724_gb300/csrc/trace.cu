@@ -457,6 +457,16 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
     int64_t c = 2 * (*P.n_seeds_dev);
     total = c < total ? c : total;
   }
+  // lanes of each warp that take work: all 32 when the units fill every
+  // resident warp, fewer when they do not, so that a launch of few (and
+  // typically long) lines spreads them over all warps and a lane's path is not
+  // serialised behind the divergent paths of its neighbours
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t per_warp = (total + warps_total - 1) / warps_total;
+  const int lanes = per_warp >= 32 ? 32 : (per_warp < 1 ? 1 : (int)per_warp);
+  const bool usable = lane < lanes;
+  const unsigned umask = lanes == 32 ? FULL : ((1u << lanes) - 1u);
+  const int refill_min = P.refill_min < lanes ? P.refill_min : lanes;
   const Item<R>* E = &P.item0;
 
   bool active = false;
@@ -478,15 +488,15 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
   for (;;) {
     // ---- refill idle lanes from the global queue (one atomic per warp)
     if (!exhausted) {
-      unsigned need = __ballot_sync(FULL, !active);
+      unsigned need = __ballot_sync(FULL, usable && !active);
       int nneed = __popc(need);
-      if (nneed > 0 && (nneed >= P.refill_min || need == FULL)) {
+      if (nneed > 0 && (nneed >= refill_min || need == umask)) {
         int leader = __ffs(need) - 1;
         unsigned long long base = 0;
         if (lane == leader) base = atomicAdd(P.head, (unsigned long long)nneed);
         base = __shfl_sync(FULL, base, leader);
         if ((int64_t)(base + nneed) >= total) exhausted = true;
-        if (!active) {
+        if (usable && !active) {
           int64_t myu = (int64_t)base + __popc(need & lt_mask);
           if (myu < total) {
             unit = myu;
@@ -867,6 +877,16 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
     int64_t c = 2 * (*P.n_seeds_dev);
     total = c < total ? c : total;
   }
+  // lanes of each warp that take work: all 32 when the units fill every
+  // resident warp, fewer when they do not, so that a launch of few (and
+  // typically long) lines spreads them over all warps and a lane's path is not
+  // serialised behind the divergent paths of its neighbours
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t per_warp = (total + warps_total - 1) / warps_total;
+  const int lanes = per_warp >= 32 ? 32 : (per_warp < 1 ? 1 : (int)per_warp);
+  const bool usable = lane < lanes;
+  const unsigned umask = lanes == 32 ? FULL : ((1u << lanes) - 1u);
+  const int refill_min = P.refill_min < lanes ? P.refill_min : lanes;
   const Item<R>* E = &P.item0;
   R ih[3] = {R(1), R(1), R(1)}, hh3[3] = {R(1), R(1), R(1)};  // spacing of the lane's field
   const R band = R(16) * eps_of<R>();  // tolerance band of internal cell faces (cell units)
@@ -885,15 +905,15 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
 
   for (;;) {
     if (!exhausted) {
-      unsigned need = __ballot_sync(FULL, !active);
+      unsigned need = __ballot_sync(FULL, usable && !active);
       int nneed = __popc(need);
-      if (nneed > 0 && (nneed >= P.refill_min || need == FULL)) {
+      if (nneed > 0 && (nneed >= refill_min || need == umask)) {
         int leader = __ffs(need) - 1;
         unsigned long long base = 0;
         if (lane == leader) base = atomicAdd(P.head, (unsigned long long)nneed);
         base = __shfl_sync(FULL, base, leader);
         if ((int64_t)(base + nneed) >= total) exhausted = true;
-        if (!active) {
+        if (usable && !active) {
           int64_t myu = (int64_t)base + __popc(need & lt_mask);
           if (myu < total) {
             unit = myu;
@@ -1249,6 +1269,466 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
   if (lane == 0 && any_to && P.timeout_flag) atomicExch(P.timeout_flag, 1);
 }
 
+// ------------------------------------------------------------ cooperative cell-wise tracer
+// The cell-wise Dormand-Prince tracer with one line on a group of three lanes.
+// Lane c of a group (c = 0, 1, 2) carries axis c of the position and of both
+// deviations, interpolates component c of the field (value and gradient row c)
+// from the cell's 8 corners held in its registers, and looks for crossings of
+// the two planes of axis c; the group exchanges stage inputs with shuffles and
+// reduces the error norm and the earliest crossing. A step's dependent chain is
+// about a third of the one-lane kernel's, so launches of few (and typically
+// long) lines - refinement passes, FP64 retraces - finish sooner. Ten groups
+// per warp; lanes 30 and 31 take no work.
+template <class R>
+__device__ __forceinline__ R gbc(unsigned m, R v, int src) {
+  return __shfl_sync(m, v, src);
+}
+
+template <class R>
+__device__ __forceinline__ R sel3(int c, R a, R b, R d) {
+  return c == 0 ? a : (c == 1 ? b : d);
+}
+
+// Stage derivative of the lane's components: k[0] = d(x_c)/dlambda (cell
+// units), k[1], k[2] = row c of grad b applied to the two deviations.
+template <class R, int NC>
+__device__ __forceinline__ void coop_rhs(unsigned gm, int gb, const R* cv, bool raw, const R* ih, R ihc,
+                                         const R* y, R* k) {
+  R u = gbc(gm, y[0], gb), v = gbc(gm, y[0], gb + 1), w = gbc(gm, y[0], gb + 2);
+  R val, d0, d1, d2;
+  tri1<R>(cv[0], cv[1], cv[2], cv[3], cv[4], cv[5], cv[6], cv[7], u, v, w, val, d0, d1, d2);
+  d0 *= ih[0];
+  d1 *= ih[1];
+  d2 *= ih[2];
+  if (raw) {
+    // interpolate B, normalise at the point: grad b = (I - b b^T) grad B / |B|
+    R v0 = gbc(gm, val, gb), v1 = gbc(gm, val, gb + 1), v2 = gbc(gm, val, gb + 2);
+    R m = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+    R rm = (m > R(0)) ? R(1) / m : R(0);
+    R nv = val * rm;
+    R p0 = nv * d0, p1 = nv * d1, p2 = nv * d2;
+    R t0 = gbc(gm, p0, gb) + gbc(gm, p0, gb + 1) + gbc(gm, p0, gb + 2);
+    R t1 = gbc(gm, p1, gb) + gbc(gm, p1, gb + 1) + gbc(gm, p1, gb + 2);
+    R t2 = gbc(gm, p2, gb) + gbc(gm, p2, gb + 1) + gbc(gm, p2, gb + 2);
+    d0 = (d0 - nv * t0) * rm;
+    d1 = (d1 - nv * t1) * rm;
+    d2 = (d2 - nv * t2) * rm;
+    val = nv;
+  }
+  k[0] = val * ihc;
+  if constexpr (NC == 9) {
+    R a0 = gbc(gm, y[1], gb), a1 = gbc(gm, y[1], gb + 1), a2 = gbc(gm, y[1], gb + 2);
+    R b0 = gbc(gm, y[2], gb), b1 = gbc(gm, y[2], gb + 1), b2 = gbc(gm, y[2], gb + 2);
+    k[1] = d0 * a0 + d1 * a1 + d2 * a2;
+    k[2] = d0 * b0 + d1 * b1 + d2 * b2;
+  }
+}
+
+// End record of a group: lane c writes axis c, the group's first lane the rest.
+template <class R, int NC>
+__device__ __forceinline__ void write_end_coop(const TraceParams<R>& P, const Item<R>* E, int64_t unit, int c,
+                                               const R* y, int icc, R mu, int face, int status, int steps) {
+  EndRec<R>& e = P.ends[unit];
+  R xv = (R)((double)E->F.org[c] + ((double)icc + (double)y[0]) / (double)E->F.inv_h[c]);
+  if (status == QSL_LINE_OK && face != NO_FACE && (face >> 1) == c)
+    xv = (R)((face & 1) ? E->hi_d[c] : E->lo_d[c]);  // exactly on the face
+  e.x[c] = xv;
+  if constexpr (NC == 9) {
+    e.d1[c] = y[1];
+    e.d2[c] = y[2];
+  }
+  if (c == 0) {
+    e.mu = mu;
+    e.face = (status == QSL_LINE_OK) ? face : NO_FACE;
+    e.status = status;
+    e.steps = steps;
+  }
+}
+
+template <class R, int NC>
+__global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ TraceParams<R> P) {
+  constexpr int ND = NC / 3;  // components per lane
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / 3;          // 0..9 (10 for lanes 30, 31)
+  const int c = lane - 3 * grp;      // axis of this lane
+  const int gb = 3 * grp;            // first lane of the group
+  const unsigned gm = grp < 10 ? (7u << gb) : (3u << 30);  // lanes 30, 31 never take work
+  int64_t total = P.n_units;
+  if (P.n_seeds_dev) {
+    int64_t cnt = 2 * (*P.n_seeds_dev);
+    total = cnt < total ? cnt : total;
+  }
+  // groups of each warp that take work (spread over all resident warps when
+  // the units do not fill them)
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t per_warp = (total + warps_total - 1) / warps_total;
+  const int ngroups = per_warp >= 10 ? 10 : (per_warp < 1 ? 1 : (int)per_warp);
+  const bool usable = grp < ngroups;
+  unsigned lead_mask = 0;
+  for (int g = 0; g < ngroups; ++g) lead_mask |= 1u << (3 * g);
+  const int refill_min = P.refill_min < ngroups ? P.refill_min : ngroups;
+  const Item<R>* E = &P.item0;
+  R ih[3] = {R(1), R(1), R(1)};
+  R ihc = R(1), hhc = R(1);
+  const R band = R(16) * eps_of<R>();
+  R tiny = R(0);
+
+  bool active = false, exhausted = false, kvalid = false;
+  int64_t unit = 0;
+  R y[ND], k1[ND], cv[8];
+  int ic[3] = {0, 0, 0};
+  R mu = 0, muc = 0, h = 0, sgn = 1;
+  int steps = 0, zc = 0;
+  unsigned long long c_stage = 0, c_acc = 0, c_rej = 0, c_land = 0, c_lines = 0;
+  int iter = 0;
+  bool timed_out = false;
+  const unsigned long long t_start = P.timeout_ns ? globaltimer() : 0ull;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) cv[i] = R(0);
+
+  for (;;) {
+    if (!exhausted) {
+      unsigned need = __ballot_sync(FULL, usable && c == 0 && !active);
+      int nneed = __popc(need);
+      if (nneed > 0 && (nneed >= refill_min || need == lead_mask)) {
+        int leader = __ffs(need) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(P.head, (unsigned long long)nneed);
+        base = __shfl_sync(FULL, base, leader);
+        if ((int64_t)(base + nneed) >= total) exhausted = true;
+        if (usable && ((need >> gb) & 1u)) {
+          int64_t myu = (int64_t)base + __popc(need & ((1u << gb) - 1u));
+          if (myu < total) {
+            unit = myu;
+            active = true;
+            if (c == 0) c_lines += (myu & 1) == 0;
+            int64_t g;
+            double xd[3];
+            E = resolve_seed(P, unit >> 1, &g, xd);
+            sgn = (unit & 1) ? R(-1) : R(1);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) ih[a] = R(E->F.inv_h[a]);
+            ihc = sel3(c, ih[0], ih[1], ih[2]);
+            hhc = R(1) / ihc;
+            tiny = R(1e-4) * E->h_max;
+            R yf[NC];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              double fa = (xd[a] - (double)E->F.org[a]) * (double)E->F.inv_h[a];
+              double fl = floor(fmin(fmax(fa, 0.0), (double)(E->F.n[a] - 2)));
+              ic[a] = (int)fl;
+              yf[a] = (R)(fa - fl);
+            }
+            mu = 0;
+            muc = 0;
+            steps = 0;
+            zc = 0;
+            kvalid = false;
+            int lface = NO_FACE;
+            int status = ST_RUNNING;
+            bool outside = false;
+#pragma unroll
+            for (int f = 0; f < 6; ++f)
+              if (face_g<R, true>(E->lo, E->hi, ic, f, yf, (const R*)nullptr) > R(0)) outside = true;
+            if (outside || !isfinite(xd[0]) || !isfinite(xd[1]) || !isfinite(xd[2])) {
+              status = QSL_LINE_OUTSIDE;
+            } else {
+              Interp<R> I0;
+              interp<R, R, false, false, true>(E->F, yf[0], yf[1], yf[2], I0, ic);
+              R m0 = sqrt(I0.b[0] * I0.b[0] + I0.b[1] * I0.b[1] + I0.b[2] * I0.b[2]);
+              if (!(m0 > R(0))) {
+                status = QSL_LINE_NULL;
+              } else {
+                if constexpr (NC == 9) {
+                  // Eq. ic (same construction as the other tracers)
+                  R u0[3] = {I0.b[0] / m0, I0.b[1] / m0, I0.b[2] / m0};
+                  int ax = 0;
+                  if (fabs(u0[1]) < fabs(u0[ax])) ax = 1;
+                  if (fabs(u0[2]) < fabs(u0[ax])) ax = 2;
+                  R av[3];
+                  if (ax == 0) { av[0] = 0; av[1] = -u0[2]; av[2] = u0[1]; }
+                  else if (ax == 1) { av[0] = u0[2]; av[1] = 0; av[2] = -u0[0]; }
+                  else { av[0] = -u0[1]; av[1] = u0[0]; av[2] = 0; }
+                  R an = sqrt(av[0] * av[0] + av[1] * av[1] + av[2] * av[2]);
+                  av[0] /= an;
+                  av[1] /= an;
+                  av[2] /= an;
+                  yf[3] = av[0];
+                  yf[4] = av[1];
+                  yf[5] = av[2];
+                  yf[6] = u0[1] * av[2] - u0[2] * av[1];
+                  yf[7] = u0[2] * av[0] - u0[0] * av[2];
+                  yf[8] = u0[0] * av[1] - u0[1] * av[0];
+                }
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                  if (status == ST_RUNNING && face_g<R, true>(E->lo, E->hi, ic, f, yf, (const R*)nullptr) == R(0)) {
+                    R bn = I0.b[f >> 1] * sgn;
+                    R outw = (f & 1) ? bn : -bn;
+                    if (outw > R(0)) {
+                      status = QSL_LINE_OK;
+                      lface = f;
+                    }
+                  }
+                }
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < ND; ++i) y[i] = sel3(c, yf[3 * i], yf[3 * i + 1], yf[3 * i + 2]);
+            h = E->h_init;
+            if (status != ST_RUNNING) {
+              write_end_coop<R, NC>(P, E, unit, c, y, sel3(c, ic[0], ic[1], ic[2]), R(0), lface, status, 0);
+              active = false;
+            }
+          }
+        }
+      }
+    }
+    if (!__any_sync(FULL, active)) {
+      if (exhausted) break;
+      continue;
+    }
+    if (P.timeout_ns && ((++iter & 63) == 0)) {
+      // warp-uniform, so that the lanes of a group agree
+      if (__any_sync(FULL, globaltimer() - t_start > P.timeout_ns)) timed_out = true;
+    }
+    if (!active) continue;
+
+    int status = ST_RUNNING, lface = NO_FACE;
+    if (timed_out) status = QSL_LINE_TIMEOUT;
+    if (status == ST_RUNNING && steps >= P.max_steps) status = QSL_LINE_MAXSTEPS;
+    R room = E->max_len - mu;
+    if (status == ST_RUNNING && !(room > R(0))) status = QSL_LINE_MAXLEN;
+    if (status == ST_RUNNING) {
+      if (!kvalid) {
+        // component c of the cell's 8 vertices, into registers
+        const size_t sy = (size_t)E->F.n[0], sz = (size_t)E->F.n[0] * (size_t)E->F.n[1];
+        const R* p = reinterpret_cast<const R*>(E->F.v + (size_t)ic[2] * sz + (size_t)ic[1] * sy + (size_t)ic[0]) + c;
+        cv[0] = __ldg(p);
+        cv[1] = __ldg(p + 4);
+        cv[2] = __ldg(p + 4 * sy);
+        cv[3] = __ldg(p + 4 * sy + 4);
+        cv[4] = __ldg(p + 4 * sz);
+        cv[5] = __ldg(p + 4 * sz + 4);
+        cv[6] = __ldg(p + 4 * (sz + sy));
+        cv[7] = __ldg(p + 4 * (sz + sy) + 4);
+        coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, y, k1);
+        c_stage += (c == 0);
+        kvalid = true;
+      }
+      // the two planes of axis c (cell faces, or domain faces where they come first)
+      const int icc = sel3(c, ic[0], ic[1], ic[2]);
+      const R lr = E->lo[c] - R(icc), hr = E->hi[c] - R(icc);
+      const bool lo_dom = lr >= R(0), hi_dom = hr <= R(1);
+      const R lo_pl = lo_dom ? lr : R(0), hi_pl = hi_dom ? hr : R(1);
+      // step: controller size, capped a little beyond the first plane along k1
+      R tf = R(1e30);
+      {
+        R vel = sgn * k1[0];
+        if (vel > R(0)) tf = (hi_pl - y[0]) / vel;
+        else if (vel < R(0)) tf = (lo_pl - y[0]) / vel;
+      }
+      const R tface = fmin(fmin(gbc(gm, tf, gb), gbc(gm, tf, gb + 1)), gbc(gm, tf, gb + 2));
+      R hs = fmin(fmin(h, E->h_max), room);
+      bool capped = room <= fmin(h, E->h_max);
+      R hf = R(1.25) * fmax(tface, R(0)) + tiny;
+      if (hf < hs) {
+        hs = hf;
+        capped = false;
+      }
+      const R hh = sgn * hs;
+      R k2[ND], k3[ND], k4[ND], k5[ND], k6[ND], k7[ND], t[ND], dy[ND];
+#pragma unroll
+      for (int i = 0; i < ND; ++i) t[i] = fma(hh, R(DA21) * k1[i], y[i]);
+      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k2);
+#pragma unroll
+      for (int i = 0; i < ND; ++i) t[i] = fma(hh, R(DA31) * k1[i] + R(DA32) * k2[i], y[i]);
+      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k3);
+#pragma unroll
+      for (int i = 0; i < ND; ++i) t[i] = fma(hh, R(DA41) * k1[i] + R(DA42) * k2[i] + R(DA43) * k3[i], y[i]);
+      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k4);
+#pragma unroll
+      for (int i = 0; i < ND; ++i)
+        t[i] = fma(hh, R(DA51) * k1[i] + R(DA52) * k2[i] + R(DA53) * k3[i] + R(DA54) * k4[i], y[i]);
+      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k5);
+#pragma unroll
+      for (int i = 0; i < ND; ++i)
+        t[i] = fma(hh, R(DA61) * k1[i] + R(DA62) * k2[i] + R(DA63) * k3[i] + R(DA64) * k4[i] + R(DA65) * k5[i],
+                   y[i]);
+      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k6);
+#pragma unroll
+      for (int i = 0; i < ND; ++i) {
+        dy[i] = hh * (R(DB1) * k1[i] + R(DB3) * k3[i] + R(DB4) * k4[i] + R(DB5) * k5[i] + R(DB6) * k6[i]);
+        t[i] = y[i] + dy[i];
+      }
+      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k7);
+      c_stage += (c == 0) ? 6 : 0;
+      steps += 1;
+      R err = 0;
+      bool bad = false;
+#pragma unroll
+      for (int i = 0; i < ND; ++i) {
+        R e = fabs(hh * (R(DE1) * k1[i] + R(DE3) * k3[i] + R(DE4) * k4[i] + R(DE5) * k5[i] + R(DE6) * k6[i] +
+                         R(DE7) * k7[i]));
+        if (!isfinite(t[i])) bad = true;
+        R ya = fabs(y[i]), yb = fabs(t[i]);
+        if (i == 0) {
+          R base = R(E->F.org[c]) + R(icc) * hhc;
+          e *= hhc;
+          ya = fabs(base + y[0] * hhc);
+          yb = fabs(base + t[0] * hhc);
+        }
+        err = fmax(err, cdiv(e, P.tol_abs + P.tol_rel * fmax(ya, yb)));
+      }
+      err = fmax(fmax(gbc(gm, err, gb), gbc(gm, err, gb + 1)), gbc(gm, err, gb + 2));
+      bad = __any_sync(gm, bad);
+      if (bad) {
+        status = QSL_LINE_NONFINITE;
+      } else if (err > R(1)) {
+        c_rej += (c == 0);
+        h = hs * fmax(R(0.2), R(0.9) * cpow(err, R(-0.25)));
+        if (h < E->h_min) status = QSL_LINE_STALL;
+      } else {
+        c_acc += (c == 0);
+        R hnext = hs * ((err == R(0)) ? R(5) : fmin(R(5), R(0.9) * cpow(err, R(-0.2))));
+        // first crossing of this axis's planes within the step, on the dense
+        // output (same bracket and safeguarded Newton as cell_kernel, with the
+        // root t = 0 divided out when the step starts on the plane)
+        R thc = R(2);
+        int upc = 0;
+        const R c4 = hh * (R(DD1) * k1[0] + R(DD3) * k3[0] + R(DD4) * k4[0] + R(DD5) * k5[0] + R(DD6) * k6[0] +
+                           R(DD7) * k7[0]);
+        const R dya = dy[0];
+        const R bspl = hh * k1[0] - dya;
+        const R c3 = dya - hh * k7[0] - bspl;
+#pragma unroll
+        for (int up = 0; up < 2; ++up) {
+          const R target = up ? hi_pl : lo_pl;
+          const bool dom = up ? hi_dom : lo_dom;
+          const R r = target - y[0];
+          const R over = up ? (dya - r) : (r - dya);
+          if (!(over > (dom ? R(0) : band))) continue;
+          const R sg = up ? R(1) : R(-1);
+          const bool defl = (r == R(0));
+          R ta = R(0), tb = R(1);
+#pragma unroll
+          for (int q = 1; q < 4; ++q) {
+            R tq = R(0.25) * R(q);
+            R s1 = R(1) - tq;
+            R pq = dya + s1 * (bspl + tq * (c3 + s1 * c4));
+            R f = defl ? pq : tq * pq - r;
+            if (sg * f > R(0) && tb == R(1)) tb = tq;
+            else if (tb == R(1)) ta = tq;
+          }
+          R tt = ta + (tb - ta) * R(0.5);
+          if (!defl) {
+            R tl = r / dya;
+            if (tl > ta && tl < tb) tt = tl;
+          }
+          for (int it = 0; it < 30; ++it) {
+            R s1 = R(1) - tt;
+            R inner = c3 + s1 * c4;
+            R mid = bspl + tt * inner;
+            R pv = dya + s1 * mid;
+            R f = defl ? pv : tt * pv - r;
+            if (fabs(f) <= R(4) * eps_of<R>() * (fabs(r) + fabs(dya)) || !(tb - ta > R(2) * eps_of<R>())) break;
+            if (sg * f > R(0)) tb = tt;
+            else ta = tt;
+            R dmid = inner - tt * c4;
+            R dp = s1 * dmid - mid;
+            R df = defl ? dp : pv + tt * dp;
+            R tn = tt - f / df;
+            tt = (tn > ta && tn < tb) ? tn : R(0.5) * (ta + tb);
+          }
+          if (tt < thc) {
+            thc = tt;
+            upc = up;
+          }
+        }
+        // earliest crossing over the group; ties go to the lower plane id
+        const R q0 = gbc(gm, thc, gb), q1 = gbc(gm, thc, gb + 1), q2 = gbc(gm, thc, gb + 2);
+        const int u0 = __shfl_sync(gm, upc, gb), u1 = __shfl_sync(gm, upc, gb + 1), u2 = __shfl_sync(gm, upc, gb + 2);
+        R th = R(2);
+        int ax_c = -1, up_c = 0;
+        if (q0 < th) { th = q0; ax_c = 0; up_c = u0; }
+        if (q1 < th) { th = q1; ax_c = 1; up_c = u1; }
+        if (q2 < th) { th = q2; ax_c = 2; up_c = u2; }
+        if (ax_c < 0) {
+          // the step stays in the cell: accept it; k7 is the next k1
+#pragma unroll
+          for (int i = 0; i < ND; ++i) {
+            y[i] += dy[i];
+            k1[i] = k7[i];
+          }
+          R t1 = hs - muc, t2 = mu + t1;
+          muc = (t2 - mu) - t1;
+          mu = t2;
+          h = hnext;
+          zc = 0;
+          if (capped) status = QSL_LINE_MAXLEN;
+        } else {
+          // advance to the plane on the dense output and snap onto it
+#pragma unroll
+          for (int i = 0; i < ND; ++i)
+            y[i] += y_at<R>(th, dy[i], hh * k1[i], hh * k7[i],
+                            hh * (R(DD1) * k1[i] + R(DD3) * k3[i] + R(DD4) * k4[i] + R(DD5) * k5[i] +
+                                  R(DD6) * k6[i] + R(DD7) * k7[i]));
+          const int my_dom = up_c ? hi_dom : lo_dom;
+          const bool dom = __shfl_sync(gm, my_dom, gb + ax_c) != 0;
+          if (c == ax_c) y[0] = up_c ? hi_pl : lo_pl;
+          R dl = th * hs;
+          R t1 = dl - muc, t2 = mu + t1;
+          muc = (t2 - mu) - t1;
+          mu = t2;
+          c_land += (c == 0);
+          if (dom) {
+            status = QSL_LINE_OK;
+            lface = 2 * ax_c + up_c;
+          } else {
+            // enter the neighbouring cell
+            zc = (dl < tiny) ? zc + 1 : 0;
+            int na = sel3(ax_c, ic[0], ic[1], ic[2]) + (up_c ? 1 : -1);
+            if (zc > 3 || na < 0 || na > E->F.n[ax_c] - 2) {
+              // grazing a face back and forth: stay in this cell for one step
+              zc = 0;
+            } else {
+              if (ax_c == 0) ic[0] = na;
+              else if (ax_c == 1) ic[1] = na;
+              else ic[2] = na;
+              if (c == ax_c) y[0] = up_c ? R(0) : R(1);
+              kvalid = false;
+            }
+            h = fmax(hnext, hs);
+          }
+        }
+      }
+    }
+    if (status != ST_RUNNING) {
+      write_end_coop<R, NC>(P, E, unit, c, y, sel3(c, ic[0], ic[1], ic[2]), mu, lface, status, steps);
+      active = false;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c_stage += __shfl_down_sync(FULL, c_stage, o);
+    c_acc += __shfl_down_sync(FULL, c_acc, o);
+    c_rej += __shfl_down_sync(FULL, c_rej, o);
+    c_land += __shfl_down_sync(FULL, c_land, o);
+    c_lines += __shfl_down_sync(FULL, c_lines, o);
+  }
+  unsigned any_to = __ballot_sync(FULL, timed_out);
+  if (lane == 0 && P.stats) {
+    atomicAdd(&P.stats->stage_evals, c_stage);
+    atomicAdd(&P.stats->accepted, c_acc);
+    atomicAdd(&P.stats->rejected, c_rej);
+    atomicAdd(&P.stats->landing, c_land);
+    atomicAdd(&P.stats->lines, c_lines);
+    if (any_to) atomicAdd(&P.stats->timeouts, 1ull);
+  }
+  if (lane == 0 && any_to && P.timeout_flag) atomicExch(P.timeout_flag, 1);
+}
+
 // ------------------------------------------------------------ assembly (FP64)
 __device__ __forceinline__ double dot3(const double* a, const double* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
@@ -1507,9 +1987,27 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
   int threads = 32 * shape.warps_per_block;
   // persistent kernel: never launch more blocks than can be resident at once
   const bool use_cell = loc && cfg.integrator == QSL_DOPRI5_CELL;
-  size_t smem = use_cell ? (size_t)24 * threads * sizeof(R) : 0;
+  bool coop = false;
+  if (use_cell) {
+    if (shape.line_lanes == 3) {
+      coop = true;
+    } else if (shape.line_lanes == 0) {
+      // auto: three lanes per line when every line of the launch gets a group
+      // of a resident warp at once (a device-side count is a retrace list,
+      // short by construction)
+      int rc_ = 0;
+      QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rc_, cell_coop_kernel<R, NC>, threads, 0));
+      int b_ = shape.blocks_per_sm < rc_ ? shape.blocks_per_sm : rc_;
+      if (b_ < 1) b_ = 1;
+      int64_t cap = (int64_t)sms * b_ * shape.warps_per_block * 10;
+      coop = n_seeds_dev != nullptr || 2 * n_seeds <= cap;
+    }
+  }
+  size_t smem = (use_cell && !coop) ? (size_t)24 * threads * sizeof(R) : 0;
   int resident = 0;
-  if (use_cell)
+  if (coop)
+    QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_coop_kernel<R, NC>, threads, 0));
+  else if (use_cell)
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_kernel<R, NC>, threads, smem));
   else if (loc)
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, trace_kernel<R, NC, true>, threads, 0));
@@ -1518,13 +2016,18 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
   int bps = shape.blocks_per_sm < resident ? shape.blocks_per_sm : resident;
   if (bps < 1) bps = 1;
   int blocks = sms * bps;
-  int64_t max_warps_needed = (2 * n_seeds + 31) / 32;
+  // one unit per warp at the least (the kernels use fewer lanes per warp when
+  // the units do not fill every resident warp)
+  int64_t max_warps_needed = 2 * n_seeds;
   if ((int64_t)blocks * shape.warps_per_block > max_warps_needed && !n_seeds_dev)
     blocks = (int)((max_warps_needed + shape.warps_per_block - 1) / shape.warps_per_block);
   if (blocks < 1) blocks = 1;
   if (ev) QSL_CHECK_CUDA(cudaEventRecord(ev[0], stream));
   if (n_seeds > 0) {
-    if (use_cell) {
+    if (coop) {
+      cell_coop_kernel<R, NC><<<blocks, threads, 0, stream>>>(P);
+      qsl::count_launch();
+    } else if (use_cell) {
       cell_kernel<R, NC><<<blocks, threads, smem, stream>>>(P);
       qsl::count_launch();
     } else if (loc) {

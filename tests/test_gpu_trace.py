@@ -36,8 +36,11 @@ def _rec_to_dict(rec):
             "st_f": rec["status_f"], "st_b": rec["status_b"]}
 
 
-@pytest.mark.parametrize("mode,integ,tol", [(0, 0, GPU_TOL), (1, 0, GPU_TOL), (0, 2, GPU_TOL), (1, 2, GPU_TOL)])
-def test_trace_seeds_charge_field(qsl, oracle_mod, mode, integ, tol):
+@pytest.mark.parametrize("mode,integ,lanes", [(0, 0, 0), (1, 0, 0), (0, 2, 1), (1, 2, 1), (0, 2, 3), (1, 2, 3)])
+def test_trace_seeds_charge_field(qsl, oracle_mod, mode, integ, lanes):
+    """lanes: 1 = one lane per line (cell_kernel), 3 = a group of three lanes
+    per line (cell_coop_kernel)."""
+    tol = GPU_TOL
     ch = inputs.random_charges(4, 2)
     gf = inputs.charge_field(ch, 64, dtype=torch.float32)
     F = _gpu_field(qsl, gf, mode)
@@ -45,7 +48,7 @@ def test_trace_seeds_charge_field(qsl, oracle_mod, mode, integ, tol):
     seeds = inputs.random_seeds(600, 17)
     seeds[:150, 2] = 0.0     # footpoints on the bottom face
     seeds[150:160, 0] = 1.0  # on the x+ face
-    o = qsl.qsl_opts_default(tol_abs=tol, tol_rel=tol, integrator=integ)
+    o = qsl.qsl_opts_default(tol_abs=tol, tol_rel=tol, integrator=integ, line_lanes=lanes)
     rec = qsl.lines_to_numpy(qsl.qsl_trace_seeds(F, torch.as_tensor(seeds).cuda(), o))
     ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
     g = _rec_to_dict(rec)
@@ -119,14 +122,15 @@ def test_volume_map_matches_oracle(qsl, oracle_mod, integ, tol):
     compare_lines(g, ref, 1.0 / 47, BOX_LO, BOX_HI)
 
 
-@pytest.mark.parametrize("integ", [0, 2])
-def test_fp64_precision_matches_oracle_tightly(qsl, oracle_mod, integ):
+@pytest.mark.parametrize("integ,lanes", [(0, 0), (2, 1), (2, 3)])
+def test_fp64_precision_matches_oracle_tightly(qsl, oracle_mod, integ, lanes):
     ch = inputs.random_charges(4, 5)
     gf = inputs.charge_field(ch, 32, dtype=torch.float64)
     F = _gpu_field(qsl, gf, 1)
     Fo = _oracle_field(oracle_mod, gf, 1)
     seeds = inputs.random_seeds(200, 23)
-    o = qsl.qsl_opts_default(tol_abs=1e-10, tol_rel=1e-10, precision=qsl.QSL_FP64, integrator=integ)
+    o = qsl.qsl_opts_default(tol_abs=1e-10, tol_rel=1e-10, precision=qsl.QSL_FP64, integrator=integ,
+                             line_lanes=lanes)
     rec = qsl.qsl_trace_seeds(F, seeds, o)
     ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
     # lengths are stored as float32 in the record: 3e-7 covers their rounding
@@ -238,8 +242,8 @@ def test_config3_volume_full_size_sampled(qsl, oracle_mod):
     assert np.allclose(Sb, want, rtol=1e-4, atol=1e-4 * want.max())
 
 
-@pytest.mark.parametrize("integ,prec", [(0, 0), (2, 0), (0, 1), (2, 1)])
-def test_loops_from_the_bottom_face(qsl, oracle_mod, integ, prec):
+@pytest.mark.parametrize("integ,prec,lanes", [(0, 0, 0), (2, 0, 1), (2, 0, 3), (0, 1, 0), (2, 1, 1), (2, 1, 3)])
+def test_loops_from_the_bottom_face(qsl, oracle_mod, integ, prec, lanes):
     """Seeds on z = 0 whose lines curve back out through z = 0 within a fraction
     of a cell (chosen by the oracle): the end is the re-crossing, not the seed.
     Both kernels, FP32 and FP64."""
@@ -256,7 +260,7 @@ def test_loops_from_the_bottom_face(qsl, oracle_mod, integ, prec):
     assert len(seeds) >= 8
     F = _gpu_field(qsl, gf, 0)
     tol = 1e-10 if prec else GPU_TOL
-    o = qsl.qsl_opts_default(tol_abs=tol, tol_rel=tol, integrator=integ, precision=prec)
+    o = qsl.qsl_opts_default(tol_abs=tol, tol_rel=tol, integrator=integ, precision=prec, line_lanes=lanes)
     rec = qsl.qsl_trace_seeds(F, seeds, o)
     ref = oracle_mod.trace_seeds(Fo, seeds, oo)
     assert np.all(rec["length"] > 0)
