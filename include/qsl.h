@@ -240,6 +240,22 @@ typedef struct qsl_samples {
 int qsl_refine(const qsl_field* field, const qsl_refine_spec* spec, const qsl_opts* opts, qsl_samples* samples,
                float* q_grid, float* l_grid, int mem, void* stream);
 
+/* Time accounting of the last qsl_refine on this thread (no paper counterpart;
+ * CUDA events on the call's stream). total_ms spans the whole call on the
+ * device; coarse_ms the tracing of the coarse pass (and of a proposal);
+ * passes_ms the tracing of the refinement passes (FP32 trace, FP64 assembly
+ * and FP64 retrace of each pass); the rest is sorting, merging, flagging,
+ * conversion and host round trips. Synchronises that stream. QSL_EINVAL
+ * before the first qsl_refine. */
+typedef struct qsl_refine_stats {
+  double total_ms, coarse_ms, passes_ms;
+  int64_t coarse_lines, pass_lines; /* seeds traced                                      */
+  int64_t coarse_stage_evals, pass_stage_evals; /* FP32 tracer stage evaluations (the
+                                       first 512 trace calls of the refine)              */
+  int32_t passes, iters;            /* refinement trace calls, iterations                */
+} qsl_refine_stats; /* 64 bytes */
+int qsl_last_refine_stats(qsl_refine_stats* out);
+
 /* ---- batches of fields and cuts: one persistent launch, captured plans ---------
  * Many planar cuts of many fields (each its own grid size) traced in one
  * persistent launch: the work queue spans all items, so uneven line lengths
@@ -320,6 +336,7 @@ typedef struct qsl_tune_report {
   double face_mismatch;  /* fraction of sample lines with different end faces */
   double sample_ms;      /* time of the chosen shape on the sample            */
   int64_t sample_seeds;
+  double h_max;          /* chosen step cap (units of the smallest spacing)   */
 } qsl_tune_report;
 int qsl_autotune(const qsl_field* field, const double* seeds, int64_t S, qsl_opts* opts, qsl_tune_report* report,
                  void* stream);

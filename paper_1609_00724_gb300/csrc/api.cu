@@ -308,6 +308,10 @@ namespace qsl {
 
 // Common driver of qsl_trace_seeds / qsl_q_map_2d / qsl_q_volume_3d: the
 // FP32 (or FP64) trace, then the FP64 retrace of lines above retrace_q.
+// Device statistics of the last run_lines on this thread (valid after it
+// returns; the stream orders readers after its kernels).
+const DeviceStats* last_run_stats_dev() { return g_last.dev; }
+
 int run_lines(const qsl_field* f, const SeedSource& src, int64_t S, const qsl_opts* o, const LineOutputs& out,
               cudaStream_t stream) {
   TraceConfig cfg;

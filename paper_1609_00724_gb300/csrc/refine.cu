@@ -15,6 +15,7 @@
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "hilbert_dev.cuh"
@@ -23,6 +24,7 @@
 namespace qsl {
 int run_lines(const qsl_field* f, const SeedSource& src, int64_t S, const qsl_opts* o, const LineOutputs& out,
               cudaStream_t stream);
+const DeviceStats* last_run_stats_dev();
 }
 
 namespace qsl {
@@ -183,13 +185,12 @@ __global__ void shift_keys_kernel(const uint64_t* __restrict__ keys, int64_t n, 
 }
 
 // Pass B flags along the shifted curve; candidates are keys on the original curve.
-__global__ void flag_shifted_kernel(const uint64_t* __restrict__ skeys, const int64_t* __restrict__ perm,
-                                    const float* __restrict__ L, int64_t n, double tau, int nd, int bits, uint32_t S,
-                                    Region sreg, uint64_t* cand) {
+__global__ void flag_shifted_kernel(const uint64_t* __restrict__ skeys, const float* __restrict__ sL, int64_t n,
+                                    double tau, int nd, int bits, uint32_t S, Region sreg, uint64_t* cand) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + 1 < n; i += (int64_t)gridDim.x * blockDim.x) {
     uint64_t a = skeys[i], b = skeys[i + 1];
     uint64_t out = NONE;
-    if (b - a > 1 && fabs((double)L[perm[i + 1]] - (double)L[perm[i]]) > tau) {
+    if (b - a > 1 && fabs((double)sL[i + 1] - (double)sL[i]) > tau) {
       uint64_t got;
       if (nearest_in_region(a + (b - a) / 2, a, b, nd, bits + 1, sreg, &got)) {
         uint32_t c[3] = {0, 0, 0};
@@ -221,18 +222,74 @@ __global__ void iota_kernel(int64_t* p, int64_t n) {
     p[i] = i;
 }
 
-__global__ void gather_kernel(const int64_t* __restrict__ perm, int64_t n, const float* q, const float* L,
-                              const uint8_t* fa, const uint8_t* st, float* q2, float* L2, uint8_t* fa2,
-                              uint8_t* st2) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t s = perm[i];
-    q2[i] = q[s];
-    L2[i] = L[s];
-    fa2[2 * i] = fa[2 * s];
-    fa2[2 * i + 1] = fa[2 * s + 1];
-    st2[i] = st[s];
+// Insertion of a sorted batch of new samples into the sorted sample set. Keys
+// are distinct, so an entry's place in the merged order is its index plus the
+// number of entries of the other array with a smaller key.
+__device__ __forceinline__ int64_t count_below(const uint64_t* __restrict__ a, int64_t n, uint64_t k) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < k) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Main order: rows [0, n) of the arrays are sorted; rows [n, n + m) are new,
+// nkey their keys sorted and row n + nperm[j] (nperm null: n + j) the data of
+// nkey[j]. Output to o*.
+__global__ void merge_samples_kernel(const uint64_t* __restrict__ key, const float* __restrict__ q,
+                                     const float* __restrict__ L, const uint8_t* __restrict__ fa,
+                                     const uint8_t* __restrict__ st, int64_t n, const uint64_t* __restrict__ nkey,
+                                     const int64_t* __restrict__ nperm, int64_t m, uint64_t* okey, float* oq,
+                                     float* oL, uint8_t* ofa, uint8_t* ost) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n + m; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p, src;
+    uint64_t k;
+    if (i < n) {
+      k = key[i];
+      p = i + count_below(nkey, m, k);
+      src = i;
+    } else {
+      int64_t j = i - n;
+      k = nkey[j];
+      p = j + count_below(key, n, k);
+      src = n + (nperm ? nperm[j] : j);
+    }
+    okey[p] = k;
+    oq[p] = q[src];
+    oL[p] = L[src];
+    ofa[2 * p] = fa[2 * src];
+    ofa[2 * p + 1] = fa[2 * src + 1];
+    ost[p] = st[src];
   }
 }
+
+// A shifted-curve order (shifted key, length), sorted; new entries nskey
+// (sorted) with lengths nL[nperm[j]].
+__global__ void merge_order_kernel(const uint64_t* __restrict__ skey, const float* __restrict__ sL, int64_t n,
+                                   const uint64_t* __restrict__ nskey, const int64_t* __restrict__ nperm,
+                                   const float* __restrict__ nL, int64_t m, uint64_t* oskey, float* osL) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n + m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      int64_t p = i + count_below(nskey, m, skey[i]);
+      oskey[p] = skey[i];
+      osL[p] = sL[i];
+    } else {
+      int64_t j = i - n;
+      int64_t p = j + count_below(skey, n, nskey[j]);
+      oskey[p] = nskey[j];
+      osL[p] = nL[nperm[j]];
+    }
+  }
+}
+
+__global__ void gather_f_kernel(const int64_t* __restrict__ perm, int64_t n, const float* __restrict__ in,
+                                float* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[perm[i]];
+}
+
 
 // Converter: one thread per output cell.
 __global__ void convert_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ vals, int64_t n, int nd,
@@ -349,8 +406,73 @@ int convert_device(const uint64_t* keys, const float* vals, int64_t n, int nd, i
 }
 
 // The refinement driver (device arrays). `smp` arrays are device pointers.
+int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o, qsl_samples* smp,
+                float* q_grid, float* l_grid, int mem_proposal, cudaStream_t s);
+
+// Event pairs of the last qsl_refine on this thread: [0] spans the call,
+// then one pair per trace call (kind 0: coarse or proposal, 1: pass).
+struct RefineClock {
+  std::vector<cudaEvent_t> ev;  // pool, grown on demand, kept until exit
+  std::vector<int> kind;
+  std::vector<int64_t> lines;
+  size_t used = 0;
+  int iters = 0;
+  static constexpr int kSnaps = 512;
+  DeviceStats* snap = nullptr;  // device, one per trace call (the first kSnaps)
+  cudaStream_t stream = nullptr;
+  bool valid = false;
+  int device = -1;
+  int take(cudaEvent_t* a, cudaEvent_t* b) {
+    while (ev.size() < used + 2) {
+      cudaEvent_t e;
+      QSL_CHECK_CUDA(cudaEventCreate(&e));
+      ev.push_back(e);
+    }
+    *a = ev[used];
+    *b = ev[used + 1];
+    used += 2;
+    return QSL_OK;
+  }
+};
+thread_local RefineClock g_rclock;
+
 int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o, qsl_samples* smp,
                   float* q_grid, float* l_grid, int mem_proposal, cudaStream_t s) {
+  RefineClock& rk = g_rclock;
+  {
+    int dev = 0;
+    QSL_CHECK_CUDA(cudaGetDevice(&dev));
+    if (rk.device != dev) {
+      // events and the snapshot buffer belong to a device: new ones for a new one
+      rk.ev.clear();
+      rk.snap = nullptr;
+      rk.device = dev;
+    }
+    if (!rk.snap) QSL_CHECK_CUDA(cudaMalloc((void**)&rk.snap, sizeof(DeviceStats) * RefineClock::kSnaps));
+  }
+  rk.used = 0;
+  rk.kind.clear();
+  rk.lines.clear();
+  rk.iters = 0;
+  rk.stream = s;
+  rk.valid = false;
+  cudaEvent_t call0, call1;
+  {
+    int r0 = rk.take(&call0, &call1);
+    if (r0) return r0;
+  }
+  QSL_CHECK_CUDA(cudaEventRecord(call0, s));
+  int rc_all = refine_body(f, sp, o, smp, q_grid, l_grid, mem_proposal, s);
+  QSL_CHECK_CUDA(cudaEventRecord(call1, s));
+  rk.iters = smp->iters;
+  rk.valid = true;
+  return rc_all;
+}
+
+int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o, qsl_samples* smp,
+                float* q_grid, float* l_grid, int mem_proposal, cudaStream_t s) {
+  RefineClock& rk = g_rclock;
+  int trace_kind = 0;  // 0 until the refinement iterations start
   const int nd = sp->ndim, p = sp->max_order, p0 = sp->coarse_order;
   const int R = 1 << (p - p0);
   int ext[3] = {1, 1, 1};
@@ -401,8 +523,29 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
       (rc = sc.alloc(&L2, cap)) || (rc = sc.alloc(&fa2, 2 * cap)) || (rc = sc.alloc(&st2, cap)))
     return rc;
 
-  // trace samples [off, off + m) (keys already written) and merge everything
-  auto trace_and_merge = [&](int64_t off, int64_t m) -> int {
+  // Shifted-curve orders (shifted key, length) for the two alternating
+  // shifts of pass B, built on first use and then kept sorted by merging each
+  // batch of new samples (as the main order is), so no pass re-sorts the set.
+  const uint32_t half = 1u << (p - 1 >= 0 ? p - 1 : 0);
+  const uint32_t dsh = (uint32_t)(R / 2 > 1 ? R / 2 : 1);
+  const uint32_t shiftS[2] = {half + dsh, half - (dsh < half ? dsh : half)};
+  uint64_t* ord_key[2] = {nullptr, nullptr};
+  float* ord_L[2] = {nullptr, nullptr};
+  uint64_t* ord_ktmp = nullptr;
+  float* ord_Ltmp = nullptr;
+  bool ord_built[2] = {false, false};
+  int64_t* nperm = nullptr;
+  uint64_t* nkey = nullptr;
+  if (sp->shift) {
+    if ((rc = sc.alloc(&ord_key[0], cap)) || (rc = sc.alloc(&ord_key[1], cap)) || (rc = sc.alloc(&ord_L[0], cap)) ||
+        (rc = sc.alloc(&ord_L[1], cap)) || (rc = sc.alloc(&ord_ktmp, cap)) || (rc = sc.alloc(&ord_Ltmp, cap)))
+      return rc;
+  }
+  if ((rc = sc.alloc(&nperm, cap)) || (rc = sc.alloc(&nkey, cap))) return rc;
+
+  // trace samples [off, off + m) (keys already written; `sorted`: in key
+  // order) and merge them into the sorted set and into the built orders
+  auto trace_and_merge = [&](int64_t off, int64_t m, bool sorted) -> int {
     if (m <= 0) return QSL_OK;
     SeedSource s2 = src;
     s2.keys = smp->key + off;
@@ -413,17 +556,48 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
     lo.status = smp->status + off;
     lo.q_form = o->q_form;
     lo.skip_open = o->skip_open;
-    int r = run_lines(f, s2, m, o, lo, s);
+    cudaEvent_t e0, e1;
+    int r = rk.take(&e0, &e1);
     if (r) return r;
+    QSL_CHECK_CUDA(cudaEventRecord(e0, s));
+    r = run_lines(f, s2, m, o, lo, s);
+    if (r) return r;
+    QSL_CHECK_CUDA(cudaEventRecord(e1, s));
+    if (rk.kind.size() < (size_t)RefineClock::kSnaps)
+      QSL_CHECK_CUDA(cudaMemcpyAsync(rk.snap + rk.kind.size(), last_run_stats_dev(), sizeof(DeviceStats),
+                                     cudaMemcpyDeviceToDevice, s));
+    rk.kind.push_back(trace_kind);
+    rk.lines.push_back(m);
     traced += m;
+    // the batch in key order
+    const uint64_t* bkey = smp->key + off;
+    const int64_t* bperm = nullptr;
+    if (!sorted) {
+      iota_kernel<<<grid_for(m), 256, 0, s>>>(perm, m);
+      qsl::count_launch();
+      if ((r = sort_pairs(smp->key + off, nkey, perm, nperm, m, nd * p, s))) return r;
+      bkey = nkey;
+      bperm = nperm;
+    }
+    // shifted orders
+    for (int b = 0; b < 2; ++b) {
+      if (!ord_built[b]) continue;
+      shift_keys_kernel<<<grid_for(m), 256, 0, s>>>(smp->key + off, m, nd, p, shiftS[b], sk, perm);
+      qsl::count_launch();
+      QSL_CHECK_CUDA(cudaGetLastError());
+      if ((r = sort_pairs(sk, sk2, perm, perm2, m, nd * (p + 1), s))) return r;
+      merge_order_kernel<<<grid_for(off + m), 256, 0, s>>>(ord_key[b], ord_L[b], off, sk2, perm2, smp->length + off,
+                                                            m, ord_ktmp, ord_Ltmp);
+      qsl::count_launch();
+      QSL_CHECK_CUDA(cudaGetLastError());
+      std::swap(ord_key[b], ord_ktmp);
+      std::swap(ord_L[b], ord_Ltmp);
+    }
+    // main order
     int64_t tot = off + m;
-    iota_kernel<<<grid_for(tot), 256, 0, s>>>(perm, tot);
+    merge_samples_kernel<<<grid_for(tot), 256, 0, s>>>(smp->key, smp->q, smp->length, smp->faces, smp->status, off,
+                                                        bkey, bperm, m, kA, q2, L2, fa2, st2);
     qsl::count_launch();
-    QSL_CHECK_CUDA(cudaGetLastError());
-    if ((r = sort_pairs(smp->key, kA, perm, perm2, tot, nd * p, s))) return r;
-    gather_kernel<<<grid_for(tot), 256, 0, s>>>(perm2, tot, smp->q, smp->length, smp->faces, smp->status, q2, L2,
-                                                fa2, st2);
-                                                qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
     QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, kA, tot * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     QSL_CHECK_CUDA(cudaMemcpyAsync(smp->q, q2, tot * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -473,7 +647,7 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
     qsl::count_launch();
     if ((rc = sort_pairs(smp->key, kA, perm, perm2, m, nd * p, s))) return rc;
     QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, kA, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-    if ((rc = trace_and_merge(0, m))) return rc;
+    if ((rc = trace_and_merge(0, m, true))) return rc;
     n = m;
   }
   // optional proposal (fresh runs and resumed ones): every effective cell of
@@ -523,44 +697,50 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
         qsl::count_launch();
         if ((rc = sort_pairs(smp->key + n, kA, perm, perm2, got, nd * p, s))) return rc;
         QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key + n, kA, got * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-        if ((rc = trace_and_merge(n, got))) return rc;
+        if ((rc = trace_and_merge(n, got, true))) return rc;
         n += got;
       }
     }
   }
 
   int it = 0;
+  trace_kind = 1;
   for (; it < sp->max_iters && !cap_hit; ++it) {
     int64_t added_total = 0, added = 0;
-    // (A) along the curve
+    // (A) along the curve (candidates come out in key order)
     if (n > 1) {
       flag_pairs_kernel<<<grid_for(n - 1), 256, 0, s>>>(smp->key, smp->length, n, sp->tau, nd, p, reg, cand);
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((rc = compact(n - 1, &added))) return rc;
-      if ((rc = trace_and_merge(n, added))) return rc;
+      if ((rc = trace_and_merge(n, added, true))) return rc;
       n += added;
       added_total += added;
     }
     // (B) along the shifted curve
     if (sp->shift && n > 1 && !cap_hit) {
-      uint32_t half = 1u << (p - 1 >= 0 ? p - 1 : 0);
-      uint32_t dsh = (uint32_t)(R / 2 > 1 ? R / 2 : 1);
-      uint32_t S = (it % 2 == 0) ? half + dsh : half - (dsh < half ? dsh : half);
-      shift_keys_kernel<<<grid_for(n), 256, 0, s>>>(smp->key, n, nd, p, S, sk, perm);
-      qsl::count_launch();
-      QSL_CHECK_CUDA(cudaGetLastError());
-      if ((rc = sort_pairs(sk, sk2, perm, perm2, n, nd * (p + 1), s))) return rc;
+      const int b = it % 2;
+      const uint32_t S = shiftS[b];
+      if (!ord_built[b]) {
+        shift_keys_kernel<<<grid_for(n), 256, 0, s>>>(smp->key, n, nd, p, S, sk, perm);
+        qsl::count_launch();
+        QSL_CHECK_CUDA(cudaGetLastError());
+        if ((rc = sort_pairs(sk, ord_key[b], perm, perm2, n, nd * (p + 1), s))) return rc;
+        gather_f_kernel<<<grid_for(n), 256, 0, s>>>(perm2, n, smp->length, ord_L[b]);
+        qsl::count_launch();
+        QSL_CHECK_CUDA(cudaGetLastError());
+        ord_built[b] = true;
+      }
       Region sreg;
       for (int a = 0; a < 3; ++a) {
         sreg.lo[a] = reg.lo[a] + (a < nd ? S : 0);
         sreg.hi[a] = reg.hi[a] + (a < nd ? S : 0);
       }
-      flag_shifted_kernel<<<grid_for(n - 1), 256, 0, s>>>(sk2, perm2, smp->length, n, sp->tau, nd, p, S, sreg, cand);
+      flag_shifted_kernel<<<grid_for(n - 1), 256, 0, s>>>(ord_key[b], ord_L[b], n, sp->tau, nd, p, S, sreg, cand);
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((rc = compact(n - 1, &added))) return rc;
-      if ((rc = trace_and_merge(n, added))) return rc;
+      if ((rc = trace_and_merge(n, added, false))) return rc;
       n += added;
       added_total += added;
     }
@@ -584,6 +764,43 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
 using namespace qsl;
 
 extern "C" {
+
+int qsl_last_refine_stats(qsl_refine_stats* out) {
+  if (!out) {
+    set_error("out is NULL");
+    return QSL_EINVAL;
+  }
+  memset(out, 0, sizeof(*out));
+  RefineClock& rk = g_rclock;
+  if (!rk.valid) {
+    set_error("no qsl_refine on this thread yet");
+    return QSL_EINVAL;
+  }
+  QSL_CHECK_CUDA(cudaStreamSynchronize(rk.stream));
+  float t = 0;
+  QSL_CHECK_CUDA(cudaEventElapsedTime(&t, rk.ev[0], rk.ev[1]));
+  out->total_ms = t;
+  for (size_t i = 0; i < rk.kind.size(); ++i) {
+    QSL_CHECK_CUDA(cudaEventElapsedTime(&t, rk.ev[2 + 2 * i], rk.ev[3 + 2 * i]));
+    if (rk.kind[i] == 0) {
+      out->coarse_ms += t;
+      out->coarse_lines += rk.lines[i];
+    } else {
+      out->passes_ms += t;
+      out->pass_lines += rk.lines[i];
+      out->passes += 1;
+    }
+  }
+  size_t ns = rk.kind.size() < (size_t)RefineClock::kSnaps ? rk.kind.size() : (size_t)RefineClock::kSnaps;
+  std::vector<DeviceStats> h(ns);
+  if (ns) QSL_CHECK_CUDA(cudaMemcpy(h.data(), rk.snap, sizeof(DeviceStats) * ns, cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < ns; ++i) {
+    if (rk.kind[i] == 0) out->coarse_stage_evals += (int64_t)h[i].stage_evals;
+    else out->pass_stage_evals += (int64_t)h[i].stage_evals;
+  }
+  out->iters = rk.iters;
+  return QSL_OK;
+}
 
 int qsl_hilbert_encode(const uint32_t* coords, int64_t n, int ndim, int bits, uint64_t* keys, int mem,
                        void* stream_) {

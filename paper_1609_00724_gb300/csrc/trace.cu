@@ -1126,18 +1126,23 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
         // earliest crossing wins.
         R th = R(2);
         int ax_c = -1, up_c = 0;
+        // planes the step ends beyond (bit 2a: lower plane of axis a, 2a+1: upper)
+        unsigned cmask = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if ((lo_pl[a] - y[a]) - dy[a] > (lo_dom[a] ? R(0) : band)) cmask |= 1u << (2 * a);
+          if (dy[a] - (hi_pl[a] - y[a]) > (hi_dom[a] ? R(0) : band)) cmask |= 2u << (2 * a);
+        }
 #pragma unroll 1
-        for (int pl = 0; pl < 6; ++pl) {
+        while (cmask) {
+          const int pl = __ffs(cmask) - 1;
+          cmask &= cmask - 1;
           int a = pl >> 1, up = pl & 1;
           R ya = a == 0 ? y[0] : (a == 1 ? y[1] : y[2]);
           R dya = a == 0 ? dy[0] : (a == 1 ? dy[1] : dy[2]);
           R target = up ? (a == 0 ? hi_pl[0] : (a == 1 ? hi_pl[1] : hi_pl[2]))
                         : (a == 0 ? lo_pl[0] : (a == 1 ? lo_pl[1] : lo_pl[2]));
-          bool dom = up ? (a == 0 ? hi_dom[0] : (a == 1 ? hi_dom[1] : hi_dom[2]))
-                        : (a == 0 ? lo_dom[0] : (a == 1 ? lo_dom[1] : lo_dom[2]));
           R r = target - ya;  // exact near the plane
-          R over = up ? (dya - r) : (r - dya);
-          if (!(over > (dom ? R(0) : band))) continue;
           R sg = up ? R(1) : R(-1);  // sg * f > 0 beyond the plane
           R k1a = a == 0 ? k1[0] : (a == 1 ? k1[1] : k1[2]);
           R k7a = a == 0 ? k7[0] : (a == 1 ? k7[1] : k7[2]);

@@ -1,9 +1,12 @@
-// Autotuner of the tracer: picks the launch shape (warps per block, resident
-// blocks per SM, refill threshold of the work queue) and the loosest step
-// tolerance whose Q and length stay within stated bounds of an FP64
-// reference traced at tol 1e-10 on the same sample of seeds. Each candidate is
-// timed with CUDA events on the caller's stream. Results are cached per
-// (grid size, interpolation mode, integrator, q_form, length_only).
+// Autotuner of the tracer: picks the loosest step tolerance whose Q and length
+// stay within stated bounds of an FP64 reference traced at tol 1e-10 on the
+// same sample of seeds, then the launch shape (warps per block, resident
+// blocks per SM, refill threshold of the work queue) and the step cap (the
+// requested one, or 4 smallest spacings when that also meets the bounds; the
+// cell-wise stepper otherwise often stops just short of a face on anisotropic
+// grids). Each candidate is timed with CUDA events on the caller's stream.
+// Results are cached per (grid size, interpolation mode, integrator, q_form,
+// length_only, requested tolerance decade).
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -90,6 +93,7 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
       opts->blocks_per_sm = it->second.blocks_per_sm;
       opts->refill_min = it->second.refill_min;
       opts->tol_abs = opts->tol_rel = it->second.tol;
+      opts->h_max = it->second.h_max;
       if (report) {
         *report = it->second;
         report->cached = 1;
@@ -124,31 +128,49 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
       break;
     }
   }
-  // launch shape: fastest of the candidates at the chosen tolerance (best of 2)
+  // step cap: a larger one where it meets the same bounds at the chosen tolerance
+  double hmaxes[2] = {opts->h_max, opts->h_max};
+  int n_hmax = 1;
+  if (opts->h_max < 4.0) {
+    qsl_opts c = base;
+    c.tol_abs = c.tol_rel = chosen_tol;
+    c.h_max = 4.0;
+    double eq4 = 0, el4 = 0, fm4 = 0;
+    if ((rc = time_trace(f, seeds, S, &c, d.p, s, &ms))) return rc;
+    QSL_CHECK_CUDA(cudaMemcpy(got.data(), d.p, sizeof(qsl_line) * S, cudaMemcpyDeviceToHost));
+    errors(got, ref, opts->q_form, f->cell, &eq4, &el4, &fm4);
+    if (eq4 <= 2e-4 && el4 <= 2e-6 && fm4 <= 1e-3) hmaxes[n_hmax++] = 4.0;
+  }
+  // launch shape and step cap: fastest of the candidates at the chosen
+  // tolerance (best of 2)
   const int wpb[] = {2, 4, 8};
   const int bps[] = {32, 2};
   const int refill[] = {1, 8};
   double best = 1e30;
   int bw = 4, bb = 32, br = 1;
-  for (int w : wpb)
-    for (int b : bps)
-      for (int rf : refill) {
-        qsl_opts c = base;
-        c.tol_abs = c.tol_rel = chosen_tol;
-        c.warps_per_block = w;
-        c.blocks_per_sm = b;
-        c.refill_min = rf;
-        double t1 = 0, t2 = 0;
-        if ((rc = time_trace(f, seeds, S, &c, d.p, s, &t1))) return rc;
-        if ((rc = time_trace(f, seeds, S, &c, d.p, s, &t2))) return rc;
-        double t = fmin(t1, t2);
-        if (t < best) {
-          best = t;
-          bw = w;
-          bb = b;
-          br = rf;
+  double bh = opts->h_max;
+  for (int k = 0; k < n_hmax; ++k)
+    for (int w : wpb)
+      for (int b : bps)
+        for (int rf : refill) {
+          qsl_opts c = base;
+          c.tol_abs = c.tol_rel = chosen_tol;
+          c.h_max = hmaxes[k];
+          c.warps_per_block = w;
+          c.blocks_per_sm = b;
+          c.refill_min = rf;
+          double t1 = 0, t2 = 0;
+          if ((rc = time_trace(f, seeds, S, &c, d.p, s, &t1))) return rc;
+          if ((rc = time_trace(f, seeds, S, &c, d.p, s, &t2))) return rc;
+          double t = fmin(t1, t2);
+          if (t < best) {
+            best = t;
+            bw = w;
+            bb = b;
+            br = rf;
+            bh = hmaxes[k];
+          }
         }
-      }
   qsl_tune_report rep;
   memset(&rep, 0, sizeof rep);
   rep.warps_per_block = bw;
@@ -160,6 +182,7 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
   rep.face_mismatch = fm;
   rep.sample_ms = best;
   rep.sample_seeds = S;
+  rep.h_max = bh;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = rep;
@@ -168,6 +191,7 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
   opts->blocks_per_sm = bb;
   opts->refill_min = br;
   opts->tol_abs = opts->tol_rel = chosen_tol;
+  opts->h_max = bh;
   if (report) *report = rep;
   return QSL_OK;
 }

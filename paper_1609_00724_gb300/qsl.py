@@ -57,6 +57,12 @@ class qsl_stats(C.Structure):
                 ("pad", C.c_int32)]
 
 
+class qsl_refine_stats(C.Structure):
+    _fields_ = [("total_ms", C.c_double), ("coarse_ms", C.c_double), ("passes_ms", C.c_double),
+                ("coarse_lines", C.c_int64), ("pass_lines", C.c_int64), ("coarse_stage_evals", C.c_int64),
+                ("pass_stage_evals", C.c_int64), ("passes", C.c_int32), ("iters", C.c_int32)]
+
+
 class qsl_refine_spec(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("coarse_order", C.c_int32), ("max_order", C.c_int32),
                 ("max_iters", C.c_int32), ("extent", C.c_int32 * 3), ("shift", C.c_int32),
@@ -79,7 +85,8 @@ class qsl_batch_item(C.Structure):
 class qsl_tune_report(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_min", C.c_int32),
                 ("cached", C.c_int32), ("tol", C.c_double), ("q_err", C.c_double), ("l_err", C.c_double),
-                ("face_mismatch", C.c_double), ("sample_ms", C.c_double), ("sample_seeds", C.c_int64)]
+                ("face_mismatch", C.c_double), ("sample_ms", C.c_double), ("sample_seeds", C.c_int64),
+                ("h_max", C.c_double)]
 
 
 _lib = None
@@ -419,9 +426,16 @@ def qsl_last_stats():
     return {k: getattr(s, k) for k, _ in s._fields_ if k != "pad"}
 
 
+def qsl_last_refine_stats():
+    """Time accounting of the last qsl_refine on this thread (dict)."""
+    s = qsl_refine_stats()
+    _check(lib().qsl_last_refine_stats(C.byref(s)))
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
 EXPORTS = ["qsl_opts_default", "qsl_load_field", "qsl_free_field", "qsl_trace_seeds", "qsl_q_map_2d",
            "qsl_q_volume_3d", "qsl_fledge", "qsl_refine", "qsl_hilbert_encode", "qsl_hilbert_decode", "qsl_convert",
            "qsl_last_error", "qsl_last_stats", "qsl_trace_seeds_noalloc", "qsl_kernel_launches", "qsl_q_map_batch",
            "qsl_plan_q_map_batch", "qsl_plan_launch", "qsl_plan_stats", "qsl_plan_free", "qsl_autotune",
            "qsl_cnn_create", "qsl_cnn_params", "qsl_cnn_forward", "qsl_cnn_loss_grad", "qsl_cnn_adam_step",
-           "qsl_cnn_free", "qsl_cnn_nparams"]
+           "qsl_cnn_free", "qsl_cnn_nparams", "qsl_last_refine_stats"]

@@ -217,3 +217,22 @@ def test_refine_resume_capacity_and_host_path(qsl, oracle_mod):
     assert nh == n_full and ith == it_full
     assert np.array_equal(h["key"][:nh], full["key"].cpu().numpy()[:n_full])
     assert np.array_equal(h["L"][:nh], full["L"].cpu().numpy()[:n_full])
+
+
+def test_refine_time_accounting(qsl, oracle_mod):
+    """qsl_last_refine_stats: the parts of the last refine add up, and the line
+    counts agree with what qsl_refine reports."""
+    F, _ = _fields(qsl, oracle_mod, n=40, seed=3)
+    sp = qsl.refine_spec(ndim=2, coarse_order=5, max_order=7, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), tau=0.05)
+    b = _alloc(128 * 128)
+    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL, integrator=qsl.QSL_DOPRI5_CELL)
+    n, iters, traced, rc = qsl.qsl_refine(F, sp, o, b["key"], b["q"], b["L"], b["faces"], b["st"])
+    assert rc == qsl.QSL_OK
+    st = qsl.qsl_last_refine_stats()
+    assert st["iters"] == iters
+    assert st["coarse_lines"] == 32 * 32
+    assert st["coarse_lines"] + st["pass_lines"] == traced == n
+    assert 1 <= st["passes"] <= 2 * max(iters, 1)
+    assert st["total_ms"] > 0 and st["coarse_ms"] > 0
+    assert st["coarse_ms"] + st["passes_ms"] <= st["total_ms"] * 1.001
+    assert st["coarse_stage_evals"] > 0 and (st["pass_stage_evals"] > 0) == (st["pass_lines"] > 0)
