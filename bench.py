@@ -64,6 +64,11 @@ def parse():
     ap.add_argument("--config", default="refine2d", choices=["refine2d", "volume", "batch64", "learned"],
                     help="refine2d: 1024^2 map refined to 4096^2 (default); volume: 512x512x256 Q/FLL/FLEDGE volume "
                          "of an 8-charge field on 384^3")
+    ap.add_argument("--shape", default=None,
+                    help="fixed launch shape 'warps_per_block,blocks_per_sm,refill_min' (skips the autotuner)")
+    ap.add_argument("--hmax", type=float, default=None, help="fixed step cap in smallest spacings")
+    ap.add_argument("--profile-refine", action="store_true",
+                    help="one qsl_refine of the bench workload and its time accounting (for ncu captures)")
     ap.add_argument("--profile-map", action="store_true",
                     help="only run the coarse Q map (the tracer kernel) --steps times, for ncu captures")
     return ap.parse_args()
@@ -537,6 +542,18 @@ def main():
         return
     field_seed = FIELD_SEED + 1000 * rank
     gf = make_field(field_seed, dev, args.grid)
+    if args.shape:
+        RUN["shape"] = tuple(int(v) for v in args.shape.split(","))
+    if args.hmax:
+        RUN["h_max"] = args.hmax
+    if args.profile_refine:
+        bufs = alloc(torch, args.coarse, dev)
+        for _ in range(args.steps):
+            tr, info = gpu_step(qsl, gf, bufs, args.coarse)
+        rs = qsl.qsl_last_refine_stats()
+        print(json.dumps({"profile_refine": True, "grid": args.grid, "coarse": args.coarse, "tol": RUN["tol"],
+                          "shape": RUN.get("shape"), "h_max": RUN.get("h_max"), "q_points": tr, **info, **rs}))
+        return
     if args.profile_map:
         F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
         N = args.coarse * args.coarse
@@ -556,7 +573,8 @@ def main():
     sd = np.column_stack([-1 + (ii + 0.5) * 2 / c, -1 + (jj + 0.5) * 2 / c, np.zeros(len(pick))])
     F0 = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
     tuned = opts(qsl)
-    tune_rep = qsl.qsl_autotune(F0, torch.as_tensor(sd).to(dev), tuned) if not args.no_tune else None
+    tune_rep = (qsl.qsl_autotune(F0, torch.as_tensor(sd).to(dev), tuned)
+                if not (args.no_tune or args.shape) else None)
     del F0
     if tune_rep:
         RUN["tol"] = tuned.tol_rel

@@ -113,7 +113,9 @@ typedef struct qsl_opts {
   double timeout_s;        /* device watchdog per launch; <= 0: none                    */
   int32_t line_lanes;      /* lanes per line of QSL_DOPRI5_CELL: 1 = one lane per line,
                               3 = a group of three lanes (one per axis), 0 = auto (three
-                              when the launch does not fill the GPU's resident warps)    */
+                              up to 512 line directions per SM, where a launch is bound
+                              by the latency of its longest lines; results agree to
+                              rounding)                                                  */
   int32_t reserved;        /* must be 0                                                 */
 } qsl_opts; /* 176 bytes */
 

@@ -77,6 +77,7 @@ struct SeedSource {
   int bits;                 // Hilbert bits per axis (SEEDS_KEYS*)
   int n[3];                 // plane: (nu, nv, 1); volume and keys: lattice extent
   double c[3], u[3], v[3];  // plane: centre + axes; volume/keys3: lo (c) and hi (u)
+  double inv_n[3];          // 1 / n[a] (filled where a launch item is made)
   const double* xyz;        // SEEDS_ARRAY: S x 3
   const uint64_t* keys;     // SEEDS_KEYS*: Hilbert keys
 };

@@ -279,7 +279,7 @@ __device__ __forceinline__ void seed_position(const SeedSource& s, int64_t g, do
       break;
     case SEEDS_PLANE: {
       int64_t i = g % s.n[0], j = g / s.n[0];
-      double a = (i + 0.5) / s.n[0] - 0.5, b = (j + 0.5) / s.n[1] - 0.5;
+      double a = (i + 0.5) * s.inv_n[0] - 0.5, b = (j + 0.5) * s.inv_n[1] - 0.5;
       for (int k = 0; k < 3; ++k) x[k] = s.c[k] + a * s.u[k] + b * s.v[k];
       break;
     }
@@ -287,7 +287,7 @@ __device__ __forceinline__ void seed_position(const SeedSource& s, int64_t g, do
       int64_t i = g % s.n[0], r = g / s.n[0];
       int64_t j = r % s.n[1], k = r / s.n[1];
       int64_t id[3] = {i, j, k};
-      for (int a = 0; a < 3; ++a) x[a] = s.c[a] + (id[a] + 0.5) / s.n[a] * (s.u[a] - s.c[a]);
+      for (int a = 0; a < 3; ++a) x[a] = s.c[a] + (id[a] + 0.5) * s.inv_n[a] * (s.u[a] - s.c[a]);
       break;
     }
     default:
@@ -301,10 +301,10 @@ __device__ __forceinline__ void seed_of(const SeedSource& s, int64_t gi, double*
     uint32_t c[3] = {0, 0, 0};
     hilbert_coords_dev(s.keys[gi], nd, s.bits, c);
     if (nd == 2) {
-      double a = (c[0] + 0.5) / s.n[0] - 0.5, b = (c[1] + 0.5) / s.n[1] - 0.5;
+      double a = (c[0] + 0.5) * s.inv_n[0] - 0.5, b = (c[1] + 0.5) * s.inv_n[1] - 0.5;
       for (int k = 0; k < 3; ++k) x[k] = s.c[k] + a * s.u[k] + b * s.v[k];
     } else {
-      for (int a = 0; a < 3; ++a) x[a] = s.c[a] + (c[a] + 0.5) / s.n[a] * (s.u[a] - s.c[a]);
+      for (int a = 0; a < 3; ++a) x[a] = s.c[a] + (c[a] + 0.5) * s.inv_n[a] * (s.u[a] - s.c[a]);
     }
     return;
   }
@@ -329,6 +329,7 @@ struct Item {
   R lo[3], hi[3];              // domain bounds: domain units (global frame) or grid-index units (local frame)
   double lo_d[3], hi_d[3];     // domain bounds in domain units
   R max_len, h_init, h_max, h_min, euler_h, land_tol;  // domain units
+  double org_d[3], h_d[3], inv_h_d[3];  // uniform grids: first vertex, spacing, 1 / spacing (FP64)
   int64_t seed_start;          // global id of the item's first seed (outputs are concatenated in item order)
 };
 
@@ -427,7 +428,7 @@ __device__ __forceinline__ void write_end(const TraceParams<R>& P, const Item<R>
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (LOC)
-      e.x[a] = (R)((double)E->F.org[a] + ((double)ic[a] + (double)y[a]) / (double)E->F.inv_h[a]);
+      e.x[a] = (R)(E->org_d[a] + ((double)ic[a] + (double)y[a]) * E->h_d[a]);
     else
       e.x[a] = y[a];
   }
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
             if (LOC) {
 #pragma unroll
               for (int a = 0; a < 3; ++a) {
-                double fa = (xd[a] - (double)E->F.org[a]) * (double)E->F.inv_h[a];
+                double fa = (xd[a] - E->org_d[a]) * E->inv_h_d[a];
                 double fl = floor(fmin(fmax(fa, 0.0), (double)(E->F.n[a] - 2)));
                 ic[a] = (int)fl;
                 y[a] = (R)(fa - fl);
@@ -931,7 +932,7 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
             tiny = R(1e-4) * E->h_max;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              double fa = (xd[a] - (double)E->F.org[a]) * (double)E->F.inv_h[a];
+              double fa = (xd[a] - E->org_d[a]) * E->inv_h_d[a];
               double fl = floor(fmin(fmax(fa, 0.0), (double)(E->F.n[a] - 2)));
               ic[a] = (int)fl;
               y[a] = (R)(fa - fl);
@@ -1334,7 +1335,7 @@ template <class R, int NC>
 __device__ __forceinline__ void write_end_coop(const TraceParams<R>& P, const Item<R>* E, int64_t unit, int c,
                                                const R* y, int icc, R mu, int face, int status, int steps) {
   EndRec<R>& e = P.ends[unit];
-  R xv = (R)((double)E->F.org[c] + ((double)icc + (double)y[0]) / (double)E->F.inv_h[c]);
+  R xv = (R)(E->org_d[c] + ((double)icc + (double)y[0]) * E->h_d[c]);
   if (status == QSL_LINE_OK && face != NO_FACE && (face >> 1) == c)
     xv = (R)((face & 1) ? E->hi_d[c] : E->lo_d[c]);  // exactly on the face
   e.x[c] = xv;
@@ -1420,7 +1421,7 @@ __global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ 
             R yf[NC];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              double fa = (xd[a] - (double)E->F.org[a]) * (double)E->F.inv_h[a];
+              double fa = (xd[a] - E->org_d[a]) * E->inv_h_d[a];
               double fl = floor(fmin(fmax(fa, 0.0), (double)(E->F.n[a] - 2)));
               ic[a] = (int)fl;
               yf[a] = (R)(fa - fl);
@@ -1935,6 +1936,11 @@ Item<R> make_item(const qsl_field* f, const SeedSource& src, const TraceConfig& 
   it.src = src;
   it.seed_start = seed_start;
   for (int a = 0; a < 3; ++a) {
+    // reciprocals once here, so seeding multiplies instead of dividing in FP64
+    it.src.inv_n[a] = src.n[a] > 0 ? 1.0 / (double)src.n[a] : 0.0;
+    it.org_d[a] = f->org[a];
+    it.h_d[a] = f->h[a];
+    it.inv_h_d[a] = f->h[a] > 0 ? 1.0 / f->h[a] : 0.0;
     it.lo_d[a] = cfg.lo[a];
     it.hi_d[a] = cfg.hi[a];
     // the local frame measures positions in grid-index units
@@ -1997,15 +2003,11 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
     if (shape.line_lanes == 3) {
       coop = true;
     } else if (shape.line_lanes == 0) {
-      // auto: three lanes per line when every line of the launch gets a group
-      // of a resident warp at once (a device-side count is a retrace list,
-      // short by construction)
-      int rc_ = 0;
-      QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rc_, cell_coop_kernel<R, NC>, threads, 0));
-      int b_ = shape.blocks_per_sm < rc_ ? shape.blocks_per_sm : rc_;
-      if (b_ < 1) b_ = 1;
-      int64_t cap = (int64_t)sms * b_ * shape.warps_per_block * 10;
-      coop = n_seeds_dev != nullptr || 2 * n_seeds <= cap;
+      // auto: three lanes per line up to 512 units (line directions) per SM,
+      // where the launch is bound by the latency of its longest lines rather
+      // than by issue rate (measured crossover on GB300: about 640 per SM); a
+      // device-side count is a retrace list, short by construction
+      coop = n_seeds_dev != nullptr || 2 * n_seeds <= (int64_t)512 * sms;
     }
   }
   size_t smem = (use_cell && !coop) ? (size_t)24 * threads * sizeof(R) : 0;
