@@ -335,6 +335,93 @@ __global__ void convert_kernel(const uint64_t* __restrict__ keys, const float* _
   }
 }
 
+// Converter for an output lattice equal to the sample lattice (one lattice
+// cell per output cell): same rule as convert_kernel, tiled along the curve.
+// A block takes CK consecutive curve keys, finds its samples (and one
+// neighbour on each side) with one binary search, stages their keys, values,
+// log10 values and key-gap reciprocals in shared memory, then resolves each
+// key with a short search there. Keys outside the extent are skipped.
+constexpr int CK = 1024;
+constexpr int CS = CK + 2;
+
+__global__ void __launch_bounds__(256) convert_tiled_kernel(const uint64_t* __restrict__ keys,
+                                                            const float* __restrict__ vals, int64_t n, int nd,
+                                                            int bits, int e0, int e1, int e2, int log_interp,
+                                                            uint64_t nkeys, float* out) {
+  __shared__ uint64_t sk[CS];
+  __shared__ float sv[CS];
+  __shared__ double sl[CS];
+  __shared__ double sinv[CS];
+  __shared__ int64_t s_lo;
+  __shared__ int s_cnt;
+  for (uint64_t c0 = (uint64_t)blockIdx.x * CK; c0 < nkeys; c0 += (uint64_t)gridDim.x * CK) {
+    const uint64_t c1 = c0 + CK < nkeys ? c0 + CK : nkeys;
+    if (threadIdx.x == 0) {
+      int64_t lo = 0, hi = n;
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < c0) lo = mid + 1;
+        else hi = mid;
+      }
+      int64_t a = lo;
+      hi = n;
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < c1) lo = mid + 1;
+        else hi = mid;
+      }
+      int64_t b = lo;
+      if (a > 0) a -= 1;  // predecessor of the chunk
+      if (b < n) b += 1;  // successor of the chunk
+      s_lo = a;
+      s_cnt = (int)(b - a);
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    const int64_t base = s_lo;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      sk[i] = keys[base + i];
+      sv[i] = vals[base + i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      if (log_interp) sl[i] = log10((double)sv[i]);
+      if (i + 1 < cnt) sinv[i] = 1.0 / ((double)sk[i + 1] - (double)sk[i]);
+    }
+    __syncthreads();
+    for (uint64_t k = c0 + threadIdx.x; k < c1; k += blockDim.x) {
+      uint32_t c[3] = {0, 0, 0};
+      hilbert_coords_dev(k, nd, bits, c);
+      if ((int)c[0] >= e0 || (int)c[1] >= e1 || (nd == 3 && (int)c[2] >= e2)) continue;
+      float res = __int_as_float(0x7fc00000);
+      if (cnt > 0) {
+        int lo = 0, hi = cnt;  // j: last staged sample with key <= k
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (sk[mid] <= k) lo = mid + 1;
+          else hi = mid;
+        }
+        const int j = lo - 1;
+        if (j >= 0 && sk[j] == k) {
+          res = sv[j];
+        } else if (j + 1 >= cnt) {
+          res = sv[j];  // after the last sample
+        } else if (j < 0) {
+          res = sv[0];  // before the first sample
+        } else {
+          const double t = ((double)k - (double)sk[j]) * sinv[j];
+          if (log_interp)
+            res = (float)exp10((1 - t) * sl[j] + t * sl[j + 1]);
+          else
+            res = (float)((1 - t) * (double)sv[j] + t * (double)sv[j + 1]);
+        }
+      }
+      out[(int64_t)c[0] + (int64_t)e0 * ((int64_t)c[1] + (int64_t)e1 * (int64_t)c[2])] = res;
+    }
+    __syncthreads();
+  }
+}
+
 int grid_for(int64_t n) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -397,7 +484,17 @@ int convert_device(const uint64_t* keys, const float* vals, int64_t n, int nd, i
   int eo[3] = {1, 1, 1};
   for (int a = 0; a < nd; ++a) eo[a] = extent[a] >> d;
   int64_t N = (int64_t)eo[0] * eo[1] * eo[2];
-  if (N > 0) {
+  if (N > 0 && d == 0) {
+    const uint64_t nkeys = 1ull << (nd * p);
+    int dev = 0, sms = 0;
+    QSL_CHECK_CUDA(cudaGetDevice(&dev));
+    QSL_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    uint64_t chunks = (nkeys + CK - 1) / CK;
+    int blocks = chunks < (uint64_t)sms * 8 ? (int)chunks : sms * 8;
+    convert_tiled_kernel<<<blocks, 256, 0, s>>>(keys, vals, n, nd, p, eo[0], eo[1], eo[2], log_interp, nkeys, out);
+    qsl::count_launch();
+    QSL_CHECK_CUDA(cudaGetLastError());
+  } else if (N > 0) {
     convert_kernel<<<grid_for(N), 256, 0, s>>>(keys, vals, n, nd, p, d, eo[0], eo[1], eo[2], log_interp, out);
     qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
