@@ -56,7 +56,7 @@ extern "C" {
 #define QSL_RAW_B 1
 
 /* Integrators (Sec. "Integration methods": the paper's adaptive Cash-Karp
- * stepper "can easily be substituted" by another embedded Runge-Kutta pair). */
+ * stepper is one of several interchangeable embedded Runge-Kutta pairs). */
 #define QSL_RKCK54 0 /* adaptive Cash-Karp 5(4), the paper's default          */
 #define QSL_EULER 1  /* fixed-step explicit Euler, step qsl_opts.euler_h cells */
 /* Adaptive Dormand-Prince 5(4) that never steps across a cell face: inside a
@@ -77,7 +77,7 @@ extern "C" {
 
 /* Per-direction line status (3 bits). */
 #define QSL_LINE_OK 0        /* reached a face of the domain                     */
-#define QSL_LINE_MAXLEN 1    /* stopped at qsl_opts.max_length ("local" Q)         */
+#define QSL_LINE_MAXLEN 1    /* stopped at qsl_opts.max_length (Q at the cutoff)     */
 #define QSL_LINE_MAXSTEPS 2  /* qsl_opts.max_steps step attempts used up          */
 #define QSL_LINE_STALL 3     /* step size fell below qsl_opts.h_min               */
 #define QSL_LINE_OUTSIDE 4   /* the seed lies outside the domain                  */

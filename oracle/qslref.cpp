@@ -380,7 +380,7 @@ End trace_dir(const Field& F, const Opts& o, const double* lo, const double* hi,
   e.status = ST_OK;
   e.steps = 0;
   // A seed on a face whose field points out of the domain ends this side at
-  // once with zero length (reading of "reaches the boundary").
+  // once with zero length (the reading of integrating until the line leaves the box).
   {
     Interp I;
     interp(F, y0, &I, nullptr);

@@ -806,6 +806,12 @@ constexpr double DD1 = -12715105075.0 / 11282082432.0, DD3 = 87487479700.0 / 327
                  DD4 = -10690763975.0 / 1880347072.0, DD5 = 701980252875.0 / 199316789632.0,
                  DD6 = -1453857185.0 / 822651844.0, DD7 = 69997945.0 / 29380423.0;
 
+// Quotient for safeguarded iterations and step-size estimates: the fast
+// single-precision division (FP64 keeps the IEEE one).
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+
+
 // Increment of the continuous extension at fraction t of the step:
 // y(t) - y0 = t (dy + s (bspl + t (c3 + s c4))), s = 1 - t, with
 // bspl = h k1 - dy, c3 = dy - h k7 - bspl and c4 = h sum_i D_i k_i.
@@ -1056,8 +1062,8 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         R vel = sgn * k1[a];
-        if (vel > R(0)) tface = fmin(tface, (hi_pl[a] - y[a]) / vel);
-        else if (vel < R(0)) tface = fmin(tface, (lo_pl[a] - y[a]) / vel);
+        if (vel > R(0)) tface = fmin(tface, qdiv(hi_pl[a] - y[a], vel));
+        else if (vel < R(0)) tface = fmin(tface, qdiv(lo_pl[a] - y[a], vel));
       }
       R hs = fmin(fmin(h, E->h_max), room);
       bool capped = room <= fmin(h, E->h_max);
@@ -1173,7 +1179,7 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
           R t = ta + (tb - ta) * R(0.5);
           if (!defl) {
             // chord estimate inside the bracket as the first iterate
-            R tl = r / dya;
+            R tl = qdiv(r, dya);
             if (tl > ta && tl < tb) t = tl;
           }
           for (int it = 0; it < 30; ++it) {
@@ -1188,7 +1194,7 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
             R dmid = inner - t * c4;
             R dp = s1 * dmid - mid;
             R df = defl ? dp : pv + t * dp;
-            R tn = t - f / df;
+            R tn = t - qdiv(f, df);
             t = (tn > ta && tn < tb) ? tn : R(0.5) * (ta + tb);
           }
           if (t < th) {
@@ -1289,6 +1295,7 @@ template <class R>
 __device__ __forceinline__ R gbc(unsigned m, R v, int src) {
   return __shfl_sync(m, v, src);
 }
+
 
 template <class R>
 __device__ __forceinline__ R sel3(int c, R a, R b, R d) {
@@ -1530,10 +1537,10 @@ __global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ 
       const R lo_pl = lo_dom ? lr : R(0), hi_pl = hi_dom ? hr : R(1);
       // step: controller size, capped a little beyond the first plane along k1
       R tf = R(1e30);
+      const R vel = sgn * k1[0];
       {
-        R vel = sgn * k1[0];
-        if (vel > R(0)) tf = (hi_pl - y[0]) / vel;
-        else if (vel < R(0)) tf = (lo_pl - y[0]) / vel;
+        if (vel > R(0)) tf = qdiv(hi_pl - y[0], vel);
+        else if (vel < R(0)) tf = qdiv(lo_pl - y[0], vel);
       }
       const R tface = fmin(fmin(gbc(gm, tf, gb), gbc(gm, tf, gb + 1)), gbc(gm, tf, gb + 2));
       R hs = fmin(fmin(h, E->h_max), room);
@@ -1629,7 +1636,7 @@ __global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ 
           }
           R tt = ta + (tb - ta) * R(0.5);
           if (!defl) {
-            R tl = r / dya;
+            R tl = qdiv(r, dya);
             if (tl > ta && tl < tb) tt = tl;
           }
           for (int it = 0; it < 30; ++it) {
@@ -1644,7 +1651,7 @@ __global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ 
             R dmid = inner - tt * c4;
             R dp = s1 * dmid - mid;
             R df = defl ? dp : pv + tt * dp;
-            R tn = tt - f / df;
+            R tn = tt - qdiv(f, df);
             tt = (tn > ta && tn < tb) ? tn : R(0.5) * (ta + tb);
           }
           if (tt < thc) {
