@@ -320,14 +320,19 @@ int qsl_cnn_nparams(void);
 /* ---- autotuner -----------------------------------------------------------------
  * Picks, on a sample of S seeds (device memory, S >= 1) of the caller's
  * workload:
- *  - the loosest tolerance in {1e-5, 1e-6, 1e-7, 1e-8} whose Q (relative error
- *    <= 2e-4 for Q < 1e6), lengths (<= 2e-6) and end faces (<= 0.1 % of lines
+ *  - the loosest tolerance in {1e-5, 1e-6, 1e-7} (FP32 tracing; FP64:
+ *    {1e-6, ..., 1e-9}) whose Q (relative error <= 2e-4 for Q < 1e6), lengths
+ *    (|dL| <= 2e-6 max(L, smallest spacing)) and end faces (<= 0.1 % of lines
  *    differ) agree with an FP64 trace of the same seeds at tol 1e-10 (a fifth
- *    of the 1e-3 / 1e-5 accuracy bar);
+ *    of the 1e-3 / 1e-5 accuracy bar). Candidates run the caller's precision
+ *    policy, FP64 retrace above retrace_q included. When none passes, the
+ *    tightest is taken and report->passed is 0;
+ *  - the step cap: the requested h_max, or 4 smallest spacings when that also
+ *    meets the bounds;
  *  - the fastest launch shape (warps per block 2/4/8, blocks per SM at most
- *    2 or as many as fit, refill threshold 1/8) at that tolerance, timed with
- *    CUDA events on `stream`.
- * Writes the choice into *opts (tol_abs = tol_rel, warps_per_block,
+ *    2 or as many as fit, refill threshold 1/8) and step cap at that
+ *    tolerance, timed with CUDA events on `stream`.
+ * Writes the choice into *opts (tol_abs = tol_rel, h_max, warps_per_block,
  * blocks_per_sm, refill_min) and into *report (optional). The result is cached
  * per (grid size, interpolation mode, integrator, q_form, length_only, input
  * tolerance); a cached call does no GPU work. Synchronous. */
@@ -339,6 +344,9 @@ typedef struct qsl_tune_report {
   double sample_ms;      /* time of the chosen shape on the sample            */
   int64_t sample_seeds;
   double h_max;          /* chosen step cap (units of the smallest spacing)   */
+  int32_t passed;        /* 1: the chosen tolerance met the bounds; 0: none of
+                            the candidates did and the tightest was taken      */
+  int32_t reserved;
 } qsl_tune_report;
 int qsl_autotune(const qsl_field* field, const double* seeds, int64_t S, qsl_opts* opts, qsl_tune_report* report,
                  void* stream);

@@ -112,19 +112,27 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
   double ms = 0;
   if ((rc = time_trace(f, seeds, S, &r, d.p, s, &ms))) return rc;
   QSL_CHECK_CUDA(cudaMemcpy(ref.data(), d.p, sizeof(qsl_line) * S, cudaMemcpyDeviceToHost));
-  // tolerance: the loosest candidate within a fifth of the parity bar
-  const double tols[] = {1e-5, 1e-6, 1e-7, 1e-8};
+  // tolerance: the loosest candidate within a fifth of the parity bar. The
+  // candidates run the caller's precision policy (FP64 retrace of lines above
+  // retrace_q included), and FP32 candidates stop at 1e-7: below that the
+  // error estimate is FP32 rounding and the controller only shrinks steps.
+  const double tols32[] = {1e-5, 1e-6, 1e-7};
+  const double tols64[] = {1e-6, 1e-7, 1e-8, 1e-9};
+  const bool fp64 = opts->precision == QSL_FP64;
+  const double* tols = fp64 ? tols64 : tols32;
+  const int n_tols = fp64 ? 4 : 3;
   qsl_opts base = *opts;
-  base.retrace_q = 0;
-  double chosen_tol = tols[3], eq = 0, el = 0, fm = 0;
-  for (double t : tols) {
+  double chosen_tol = tols[n_tols - 1], eq = 0, el = 0, fm = 0;
+  int passed = 0;
+  for (int k = 0; k < n_tols; ++k) {
     qsl_opts c = base;
-    c.tol_abs = c.tol_rel = t;
+    c.tol_abs = c.tol_rel = tols[k];
     if ((rc = time_trace(f, seeds, S, &c, d.p, s, &ms))) return rc;
     QSL_CHECK_CUDA(cudaMemcpy(got.data(), d.p, sizeof(qsl_line) * S, cudaMemcpyDeviceToHost));
     errors(got, ref, opts->q_form, f->cell, &eq, &el, &fm);
     if (eq <= 2e-4 && el <= 2e-6 && fm <= 1e-3) {
-      chosen_tol = t;
+      chosen_tol = tols[k];
+      passed = 1;
       break;
     }
   }
@@ -183,6 +191,7 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
   rep.sample_ms = best;
   rep.sample_seeds = S;
   rep.h_max = bh;
+  rep.passed = passed;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = rep;

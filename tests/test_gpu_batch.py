@@ -93,9 +93,11 @@ def test_autotune_picks_valid_shape_and_tolerance(qsl):
     seeds = torch.as_tensor(inputs.random_seeds(2000, 5)).cuda()
     o = qsl.qsl_opts_default(integrator=qsl.QSL_DOPRI5_CELL)
     rep = qsl.qsl_autotune(items[1][0], seeds, o)
-    assert rep["tol"] in (1e-5, 1e-6, 1e-7, 1e-8)
+    assert rep["tol"] in (1e-5, 1e-6, 1e-7)
+    assert rep["passed"] == 1
     assert rep["q_err"] <= 2e-4 and rep["l_err"] <= 2e-6 and rep["cached"] == 0
     assert o.tol_rel == rep["tol"] and o.warps_per_block == rep["warps_per_block"]
+    assert rep["h_max"] in (2.0, 4.0) and o.h_max == rep["h_max"]
     o2 = qsl.qsl_opts_default(integrator=qsl.QSL_DOPRI5_CELL)
     rep2 = qsl.qsl_autotune(items[1][0], seeds, o2)
-    assert rep2["cached"] == 1 and o2.refill_min == rep["refill_min"]
+    assert rep2["cached"] == 1 and o2.refill_min == rep["refill_min"] and o2.h_max == rep["h_max"]
