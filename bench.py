@@ -74,6 +74,22 @@ def parse():
     return ap.parse_args()
 
 
+def replica_seed(base, rank):
+    """Seed of replica `rank`: each rank traces its own field (weak scaling)."""
+    return base + 1000 * rank
+
+
+def reduce_timing(torch, ms, units, world, device):
+    """Whole-job figures over the replicas: the slowest rank's time and the sum
+    of all ranks' units (all_reduce MAX / SUM; no-op for one rank)."""
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    n = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(n, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -321,7 +337,7 @@ def run_volume(args, qsl, torch, dev, rank, world, local):
     cell-centre seeds (FP32 trace, FP64 assembly, FP64 retrace above 1e6) and
     the 3D FLEDGE of the length volume."""
     from paper_1609_00724_gb300 import inputs
-    ch = inputs.random_charges(8, 3 + 1000 * rank)
+    ch = inputs.random_charges(8, replica_seed(3, rank))
     gf = inputs.charge_field(ch, 384, dtype=torch.float32, device=dev, slab=32)
     F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
     nx, ny, nz = 512, 512, 256
@@ -350,11 +366,8 @@ def run_volume(args, qsl, torch, dev, rank, world, local):
         torch.cuda.synchronize()
     ms = start.elapsed_time(end)
     st = qsl.qsl_last_stats()
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * N * args.steps / (ms_max / 1000.0)
+    ms_max, units = reduce_timing(torch, ms, N * args.steps, world, dev)
+    value = units / (ms_max / 1000.0)
     fps = FLOP_PER_STAGE[RUN["integrator"]]
     ach = st["stage_evals"] * fps / (st["kernel_ms"] / 1000.0) / 1e12
     line = {"metric": "Q-points/s (3D Q/FLL/FLEDGE volume)", "value": value, "unit": UNIT, "n_gpus": world,
@@ -378,12 +391,12 @@ def run_batch(args, qsl, torch, dev, rank, world, local):
     (plan), with the launch shape and tolerance picked by the autotuner on a
     sample of the first cut."""
     from paper_1609_00724_gb300 import inputs
-    rng = np.random.Generator(np.random.PCG64(4 + 1000 * rank))
+    rng = np.random.Generator(np.random.PCG64(replica_seed(4, rank)))
     items, fields = [], []
     for i in range(64):
         n = int(rng.integers(64, 257))
         m = int(rng.integers(256, 1025))
-        gf = inputs.charge_field(inputs.random_charges(4, 4000 + i + 1000 * rank), n, dtype=torch.float32,
+        gf = inputs.charge_field(inputs.random_charges(4, replica_seed(4000 + i, rank)), n, dtype=torch.float32,
                                  device=dev, slab=64)
         F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
         del gf
@@ -415,11 +428,8 @@ def run_batch(args, qsl, torch, dev, rank, world, local):
         torch.cuda.synchronize()
     ms = start.elapsed_time(end)
     st = plan.stats()
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * N * args.steps / (ms_max / 1000.0)
+    ms_max, units = reduce_timing(torch, ms, N * args.steps, world, dev)
+    value = units / (ms_max / 1000.0)
     line = {"metric": "Q-points/s (64-field batch, one captured persistent launch)", "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -540,7 +550,7 @@ def main():
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    field_seed = FIELD_SEED + 1000 * rank
+    field_seed = replica_seed(FIELD_SEED, rank)
     gf = make_field(field_seed, dev, args.grid)
     if args.shape:
         RUN["shape"] = tuple(int(v) for v in args.shape.split(","))
@@ -606,13 +616,8 @@ def main():
     ms = start.elapsed_time(end)
     launches = qsl.qsl_kernel_launches() - launches0
     rs = qsl.qsl_last_refine_stats()  # the last timed step's qsl_refine
-    t = torch.tensor([ms], device=dev)
-    n_units = torch.tensor([float(traced_total)], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(n_units, op=torch.distributed.ReduceOp.SUM)
-    ms_max = float(t.item())
-    value = float(n_units.item()) / (ms_max / 1000.0)
+    ms_max, units = reduce_timing(torch, ms, traced_total, world, dev)
+    value = units / (ms_max / 1000.0)
 
     # --- dominant kernel (tracer) timing over one more step: CUDA events recorded
     # by the library around each tracer launch on the launching stream
