@@ -29,7 +29,8 @@ class RefineSpec(C.Structure):
     _fields_ = [("ndim", C.c_int), ("coarse_order", C.c_int), ("max_order", C.c_int), ("max_iters", C.c_int),
                 ("extent", C.c_int * 3), ("shift", C.c_int), ("q_form", C.c_int), ("out_order", C.c_int),
                 ("pad", C.c_int), ("center", C.c_double * 3), ("u", C.c_double * 3), ("v", C.c_double * 3),
-                ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("tau", C.c_double)]
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("tau", C.c_double), ("criterion", C.c_int),
+                ("pad2", C.c_int), ("q_threshold", C.c_double)]
 
 
 class Lines(C.Structure):

@@ -979,6 +979,9 @@ struct RefineSpec {
   double center[3], u[3], v[3];  // planar slice
   double lo[3], hi[3];           // volume
   double tau;                    // threshold on |L_i - L_{i+1}|
+  int criterion;                 // 0: FLL jump |L_i - L_{i+1}| > tau; 1: Q threshold
+  int pad2;
+  double q_threshold;            // criterion 1: refine a pair where a sample's Q exceeds it
 };
 
 struct Sample {
@@ -1127,6 +1130,16 @@ int qslref_sizeof_refine_spec(void) { return (int)sizeof(RefineSpec); }
 // 2^(p-1) - max(1, R/2) on odd ones, the same flag rule, new cells mapped back
 // by the inverse shift and kept when inside the lattice. Iterations stop when
 // neither pass adds a sample.
+// Refinement criterion of a pair of samples adjacent along the curve: the FLL
+// jump the paper uses, or the alternative it compares against (Sec. "Adaptive
+// refinements"): refine where Q exceeds a fixed threshold. A sample whose Q is
+// not finite (a NaN of an open or cut-off line) does not trigger the latter.
+static bool pair_flagged(const RefineSpec& s, const Sample& A, const Sample& B) {
+  if (s.criterion == 1)
+    return (std::isfinite(A.q) && A.q > s.q_threshold) || (std::isfinite(B.q) && B.q > s.q_threshold);
+  return std::fabs(B.L - A.L) > s.tau;
+}
+
 static int64_t refine_impl(const Evaluator& ev, const RefineSpec* sp, int64_t capacity, uint64_t* key,
                            double* q, double* L, int32_t* face_f, int32_t* face_b, int32_t* st_f,
                            int32_t* st_b, int32_t* iters_out, int64_t* traced_per_iter) {
@@ -1160,7 +1173,7 @@ static int64_t refine_impl(const Evaluator& ev, const RefineSpec* sp, int64_t ca
     std::vector<Sample> add;
     for (size_t i = 0; i + 1 < all.size(); ++i) {
       uint64_t gap = all[i + 1].key - all[i].key;
-      if (gap > 1 && std::fabs(all[i + 1].L - all[i].L) > s.tau) {
+      if (gap > 1 && pair_flagged(s, all[i], all[i + 1])) {
         uint64_t m = all[i].key + gap / 2;
         uint64_t got;
         if (!nearest_in_region(m, all[i].key, all[i + 1].key, nd, p, rlo, rhi, &got)) continue;
@@ -1193,7 +1206,7 @@ static int64_t refine_impl(const Evaluator& ev, const RefineSpec* sp, int64_t ca
         uint64_t gap = sk[i + 1].first - sk[i].first;
         const Sample& A = all[sk[i].second];
         const Sample& B = all[sk[i + 1].second];
-        if (gap > 1 && std::fabs(B.L - A.L) > s.tau) {
+        if (gap > 1 && pair_flagged(s, A, B)) {
           uint64_t m = sk[i].first + gap / 2;
           uint64_t slo[3], shi[3], got;
           for (int a = 0; a < 3; ++a) {

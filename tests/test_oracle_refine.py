@@ -117,3 +117,45 @@ def test_converter_on_refined_samples_keeps_sampled_values(oracle_mod):
     assert np.all(np.isfinite(grid))
     lo, hi = r["q"].min(), r["q"].max()
     assert np.all((grid >= lo * (1 - 1e-12)) & (grid <= hi * (1 + 1e-12)))
+
+
+def ring_q_map(x):
+    """Q: a ridge of height 1000 on the circle r = 0.5 (width 0.03) over Q = 2;
+    L is constant, so only the Q criterion can refine."""
+    r = np.hypot(x[:, 0] - 0.1, x[:, 1] + 0.05)
+    return 2.0 + 1000.0 * np.exp(-((r - 0.5) / 0.03) ** 2), np.ones(len(x))
+
+
+def test_q_threshold_criterion_refines_the_high_q_region(oracle_mod):
+    """Criterion 1 (the alternative the paper compares against): a pair of
+    curve-adjacent samples is refined when either sample's Q exceeds the
+    threshold. At termination no adjacent pair with key gap > 1 (on the curve,
+    with the shifted pass off) has a sample above the threshold; every cell on
+    the curve between two refined neighbours of a high-Q sample is traced; a
+    threshold above max Q keeps only the coarse samples; the FLL criterion on
+    the same constant-L map does not refine at all."""
+    p0, p = 3, 7
+    base = dict(ndim=2, coarse_order=p0, max_order=p, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), shift=0)
+    sp = oracle_mod.refine_spec(criterion=1, q_threshold=100.0, tau=0.05, **base)
+    r = oracle_mod.refine_fn(ring_q_map, sp)
+    keys, q = r["key"].astype(np.int64), r["q"]
+    assert len(keys) > 64 and r["iters"] > 0
+    gap = np.diff(keys)
+    hot = (q[:-1] > 100.0) | (q[1:] > 100.0)
+    assert not np.any(hot & (gap > 1))
+    # every traced cell with Q above the threshold has both curve neighbours traced
+    ks = set(int(k) for k in keys)
+    for k, qq in zip(keys, q):
+        if qq > 100.0:
+            assert (k == keys[0] or k - 1 in ks) and (k == keys[-1] or k + 1 in ks)
+    # the high-Q cells found lie on the ridge
+    xy = np.array([oracle_mod.hilbert_coords(int(k), 2, p) for k in keys[q > 100.0]])
+    pos = (xy + 0.5) / (1 << p) * 2 - 1
+    rr = np.hypot(pos[:, 0] - 0.1, pos[:, 1] + 0.05)
+    assert np.all(np.abs(rr - 0.5) < 0.03 * np.sqrt(np.log(1000.0 / 98.0)) + 1e-9)
+    # threshold above the maximum: coarse samples only
+    r2 = oracle_mod.refine_fn(ring_q_map, oracle_mod.refine_spec(criterion=1, q_threshold=2000.0, tau=0.05, **base))
+    assert len(r2["key"]) == (1 << p0) ** 2 and r2["iters"] == 0
+    # the FLL criterion ignores Q
+    r3 = oracle_mod.refine_fn(ring_q_map, oracle_mod.refine_spec(criterion=0, tau=0.05, **base))
+    assert len(r3["key"]) == (1 << p0) ** 2
