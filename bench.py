@@ -61,7 +61,7 @@ def parse():
                     help="cell: cell-wise Dormand-Prince (default); ck: the paper's plain Cash-Karp")
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (fixed tolerance and shape)")
-    ap.add_argument("--config", default="refine2d", choices=["refine2d", "volume", "batch64", "learned"],
+    ap.add_argument("--config", default="refine2d", choices=["refine2d", "volume", "batch64", "learned", "qcrit"],
                     help="refine2d: 1024^2 map refined to 4096^2 (default); volume: 512x512x256 Q/FLL/FLEDGE volume "
                          "of an 8-charge field on 384^3")
     ap.add_argument("--shape", default=None,
@@ -442,6 +442,58 @@ def run_batch(args, qsl, torch, dev, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_qcrit(args, qsl, torch, dev, rank, world, local):
+    """Refinement criteria compared (Sec. "Adaptive refinements"): the FLL jump
+    (tau 0.05) against a Q threshold (Q > 100), both refining the 1024^2 z = 0
+    map of the bench field to 4096^2 with the same tolerance, against a dense
+    4096^2 map traced at every effective cell: wall time, samples, iterations,
+    and recall / precision of the cells with Q >= 100 (QSL cells) on the
+    converted 4096^2 Q grids."""
+    eff = args.coarse << (P - P0)
+    gf = make_field(replica_seed(FIELD_SEED, rank), dev, args.grid)
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
+    o = opts(qsl)
+    qd = torch.empty(eff * eff, device=dev)
+    Ld = torch.empty(eff * eff, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qsl.qsl_q_map_2d(F, (0, 0, 0), (2, 0, 0), (0, 2, 0), eff, eff, o, q=qd, length=Ld)
+    torch.cuda.synchronize()
+    t_dense = time.perf_counter() - t0
+    qsl_dense = torch.nan_to_num(qd, nan=0.0) >= 100.0
+    bufs = alloc(torch, args.coarse, dev)
+    res = {"dense": {"seconds": t_dense, "samples": eff * eff, "qsl_cells": int(qsl_dense.sum().item())}}
+    p0 = int(np.log2(args.coarse))
+    for name, kw in (("fll_jump", dict(criterion=qsl.QSL_REFINE_FLL_JUMP)),
+                     ("q_threshold", dict(criterion=qsl.QSL_REFINE_Q_THRESHOLD, q_threshold=100.0))):
+        sp = qsl.refine_spec(ndim=2, coarse_order=p0, max_order=p0 + (P - P0), center=(0, 0, 0), u=(2, 0, 0),
+                             v=(0, 2, 0), tau=TAU, shift=1, max_iters=256, **kw)
+        best = None
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n, iters, traced, rc = qsl.qsl_refine(F, sp, o, bufs["key"], bufs["q"], bufs["L"], bufs["faces"],
+                                                  bufs["st"], 0, bufs["qg"], bufs["lg"])
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        got = torch.nan_to_num(bufs["qg"], nan=0.0) >= 100.0
+        tp = int((got & qsl_dense).sum().item())
+        res[name] = {"seconds": best, "samples": int(n), "iters": int(iters), "rc": int(rc),
+                     "qsl_recall": tp / max(1, int(qsl_dense.sum().item())),
+                     "qsl_precision": tp / max(1, int(got.sum().item()))}
+    line = {"metric": "refinement criteria: Q-threshold time / FLL-jump time (QSL-cell recall of each)",
+            "value": res["q_threshold"]["seconds"] / res["fll_jump"]["seconds"], "unit": "x",
+            "n_gpus": world, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "4-charge potential field %d^3 FP32, %d^2 z=0 map refined to %d^2; dense %d^2 "
+                                   "reference" % (args.grid, args.coarse, eff, eff), "tau": TAU, "q_threshold": 100.0,
+                       "tol": RUN["tol"], "qsl_cell": "Q >= 100"},
+            "results": res}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_learned(args, qsl, torch, dev, rank, world, local):
     """Config 5: the learned refinement proposal. Training: 2000 tracer-generated
     maps (random 4-12-charge fields on 128^3, coarse 128^2 z=0 cuts refined two
@@ -544,8 +596,8 @@ def main():
     dev = torch.device("cuda", local)
     from paper_1609_00724_gb300 import qsl
     qsl.lib()
-    if args.config in ("volume", "batch64", "learned"):
-        {"volume": run_volume, "batch64": run_batch, "learned": run_learned}[args.config](
+    if args.config in ("volume", "batch64", "learned", "qcrit"):
+        {"volume": run_volume, "batch64": run_batch, "learned": run_learned, "qcrit": run_qcrit}[args.config](
             args, qsl, torch, dev, rank, world, local)
         if world > 1:
             torch.distributed.destroy_process_group()

@@ -216,7 +216,15 @@ typedef struct qsl_refine_spec {
   const uint8_t* proposal;      /* optional (device or host per `mem`): one byte per coarse
                                    cell, x fastest; nonzero cells are sampled at every
                                    effective cell before the first iteration          */
+  int32_t criterion;            /* QSL_REFINE_FLL_JUMP (0): |L_i - L_i+1| > tau (the paper's);
+                                   QSL_REFINE_Q_THRESHOLD (1): a pair is refined when either
+                                   sample's Q (opts.q_form) is finite and > q_threshold, the
+                                   alternative Sec. "Adaptive refinements" compares against */
+  int32_t reserved;             /* must be 0                                              */
+  double q_threshold;
 } qsl_refine_spec;
+#define QSL_REFINE_FLL_JUMP 0
+#define QSL_REFINE_Q_THRESHOLD 1
 
 typedef struct qsl_samples {
   int64_t capacity;  /* entries the arrays below can hold                           */

@@ -159,12 +159,25 @@ __global__ void mask_cells_kernel(const uint8_t* __restrict__ mask, int64_t n, i
 }
 
 // Pass A flags: candidate key per pair, NONE when not refined.
-__global__ void flag_pairs_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ L, int64_t n,
-                                  double tau, int nd, int bits, Region reg, uint64_t* cand) {
+// Refinement criterion of a pair of samples adjacent along a curve, on the
+// criterion value v of each (L for the FLL jump, Q for the Q threshold).
+struct Criterion {
+  int kind;  // QSL_REFINE_FLL_JUMP or QSL_REFINE_Q_THRESHOLD
+  double tau, q_threshold;
+};
+
+__device__ __forceinline__ bool pair_flagged(const Criterion& cr, float va, float vb) {
+  if (cr.kind == QSL_REFINE_Q_THRESHOLD)
+    return (isfinite(va) && (double)va > cr.q_threshold) || (isfinite(vb) && (double)vb > cr.q_threshold);
+  return fabs((double)vb - (double)va) > cr.tau;
+}
+
+__global__ void flag_pairs_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ V, int64_t n,
+                                  Criterion cr, int nd, int bits, Region reg, uint64_t* cand) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + 1 < n; i += (int64_t)gridDim.x * blockDim.x) {
     uint64_t a = keys[i], b = keys[i + 1];
     uint64_t out = NONE;
-    if (b - a > 1 && fabs((double)L[i + 1] - (double)L[i]) > tau) {
+    if (b - a > 1 && pair_flagged(cr, V[i], V[i + 1])) {
       uint64_t got;
       if (nearest_in_region(a + (b - a) / 2, a, b, nd, bits, reg, &got)) out = got;
     }
@@ -185,12 +198,12 @@ __global__ void shift_keys_kernel(const uint64_t* __restrict__ keys, int64_t n, 
 }
 
 // Pass B flags along the shifted curve; candidates are keys on the original curve.
-__global__ void flag_shifted_kernel(const uint64_t* __restrict__ skeys, const float* __restrict__ sL, int64_t n,
-                                    double tau, int nd, int bits, uint32_t S, Region sreg, uint64_t* cand) {
+__global__ void flag_shifted_kernel(const uint64_t* __restrict__ skeys, const float* __restrict__ sV, int64_t n,
+                                    Criterion cr, int nd, int bits, uint32_t S, Region sreg, uint64_t* cand) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + 1 < n; i += (int64_t)gridDim.x * blockDim.x) {
     uint64_t a = skeys[i], b = skeys[i + 1];
     uint64_t out = NONE;
-    if (b - a > 1 && fabs((double)sL[i + 1] - (double)sL[i]) > tau) {
+    if (b - a > 1 && pair_flagged(cr, sV[i], sV[i + 1])) {
       uint64_t got;
       if (nearest_in_region(a + (b - a) / 2, a, b, nd, bits + 1, sreg, &got)) {
         uint32_t c[3] = {0, 0, 0};
@@ -620,7 +633,11 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
       (rc = sc.alloc(&L2, cap)) || (rc = sc.alloc(&fa2, 2 * cap)) || (rc = sc.alloc(&st2, cap)))
     return rc;
 
-  // Shifted-curve orders (shifted key, length) for the two alternating
+  // the criterion and the per-sample value it reads (L or Q)
+  Criterion crit{sp->criterion, sp->tau, sp->q_threshold};
+  auto crit_values = [&]() -> float* { return sp->criterion == QSL_REFINE_Q_THRESHOLD ? smp->q : smp->length; };
+
+  // Shifted-curve orders (shifted key, criterion value) for the two alternating
   // shifts of pass B, built on first use and then kept sorted by merging each
   // batch of new samples (as the main order is), so no pass re-sorts the set.
   const uint32_t half = 1u << (p - 1 >= 0 ? p - 1 : 0);
@@ -683,7 +700,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((r = sort_pairs(sk, sk2, perm, perm2, m, nd * (p + 1), s))) return r;
-      merge_order_kernel<<<grid_for(off + m), 256, 0, s>>>(ord_key[b], ord_L[b], off, sk2, perm2, smp->length + off,
+      merge_order_kernel<<<grid_for(off + m), 256, 0, s>>>(ord_key[b], ord_L[b], off, sk2, perm2, crit_values() + off,
                                                             m, ord_ktmp, ord_Ltmp);
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
@@ -806,7 +823,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
     int64_t added_total = 0, added = 0;
     // (A) along the curve (candidates come out in key order)
     if (n > 1) {
-      flag_pairs_kernel<<<grid_for(n - 1), 256, 0, s>>>(smp->key, smp->length, n, sp->tau, nd, p, reg, cand);
+      flag_pairs_kernel<<<grid_for(n - 1), 256, 0, s>>>(smp->key, crit_values(), n, crit, nd, p, reg, cand);
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((rc = compact(n - 1, &added))) return rc;
@@ -823,7 +840,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
         qsl::count_launch();
         QSL_CHECK_CUDA(cudaGetLastError());
         if ((rc = sort_pairs(sk, ord_key[b], perm, perm2, n, nd * (p + 1), s))) return rc;
-        gather_f_kernel<<<grid_for(n), 256, 0, s>>>(perm2, n, smp->length, ord_L[b]);
+        gather_f_kernel<<<grid_for(n), 256, 0, s>>>(perm2, n, crit_values(), ord_L[b]);
         qsl::count_launch();
         QSL_CHECK_CUDA(cudaGetLastError());
         ord_built[b] = true;
@@ -833,7 +850,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
         sreg.lo[a] = reg.lo[a] + (a < nd ? S : 0);
         sreg.hi[a] = reg.hi[a] + (a < nd ? S : 0);
       }
-      flag_shifted_kernel<<<grid_for(n - 1), 256, 0, s>>>(ord_key[b], ord_L[b], n, sp->tau, nd, p, S, sreg, cand);
+      flag_shifted_kernel<<<grid_for(n - 1), 256, 0, s>>>(ord_key[b], ord_L[b], n, crit, nd, p, S, sreg, cand);
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((rc = compact(n - 1, &added))) return rc;
@@ -1012,6 +1029,14 @@ int qsl_refine(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o,
   int nd = sp->ndim, p = sp->max_order, p0 = sp->coarse_order;
   if (p0 < 0 || p < p0 || nd * (p + 1) > 63 || p > 30) {
     set_error("need 0 <= coarse_order <= max_order and ndim * (max_order + 1) <= 63");
+    return QSL_EINVAL;
+  }
+  if (sp->criterion != QSL_REFINE_FLL_JUMP && sp->criterion != QSL_REFINE_Q_THRESHOLD) {
+    set_error("criterion must be QSL_REFINE_FLL_JUMP or QSL_REFINE_Q_THRESHOLD");
+    return QSL_EINVAL;
+  }
+  if (sp->reserved != 0) {
+    set_error("reserved must be 0");
     return QSL_EINVAL;
   }
   int R = 1 << (p - p0);

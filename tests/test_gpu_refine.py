@@ -236,3 +236,44 @@ def test_refine_time_accounting(qsl, oracle_mod):
     assert st["total_ms"] > 0 and st["coarse_ms"] > 0
     assert st["coarse_ms"] + st["passes_ms"] <= st["total_ms"] * 1.001
     assert st["coarse_stage_evals"] > 0 and (st["pass_stage_evals"] > 0) == (st["pass_lines"] > 0)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_refine_q_threshold_criterion_matches_oracle(qsl, oracle_mod, ndim):
+    """The Q-threshold criterion (QSL_REFINE_Q_THRESHOLD) gives the oracle's
+    sample set (up to pairs whose Q sits within the parity error of the
+    threshold) and the oracle's values on the common samples."""
+    F, Fo = _fields(qsl, oracle_mod, n=40, seed=3)
+    if ndim == 2:
+        kw = dict(ndim=2, coarse_order=4, max_order=7, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), tau=0.05)
+        cap = 128 * 128
+    else:
+        kw = dict(ndim=3, coarse_order=2, max_order=4, extent=(16, 16, 8), lo=(-1, -1, 0), hi=(1, 1, 1), tau=0.05)
+        cap = 16 * 16 * 8
+    thr = 30.0 if ndim == 2 else 10.0  # the 3D coarse samples stay below 30
+    kw.update(criterion=qsl.QSL_REFINE_Q_THRESHOLD, q_threshold=thr)
+    sp = qsl.refine_spec(**kw)
+    b = _alloc(cap)
+    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL)
+    n, iters, traced, rc = qsl.qsl_refine(F, sp, o, b["key"], b["q"], b["L"], b["faces"], b["st"])
+    assert rc == qsl.QSL_OK and iters > 0
+    keys = b["key"].cpu().numpy()[:n].view(np.uint64)
+    ref = oracle_mod.refine(Fo, oracle_mod.refine_spec(**kw), oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
+    rk = set(int(k) for k in ref["key"])
+    gk = set(int(k) for k in keys)
+    assert len(rk) > (1 << (kw["coarse_order"] * ndim)) * 1.05  # it refined
+    sym = len(rk ^ gk)
+    assert sym <= max(3, 0.02 * len(rk)), (sym, len(rk), len(gk))
+    common = np.array(sorted(rk & gk), dtype=np.uint64)
+    gi = np.searchsorted(keys, common)
+    ri = np.searchsorted(ref["key"], common)
+    q = b["q"].cpu().numpy()[:n][gi]
+    qr = ref["q"][ri]
+    ok = np.isfinite(qr) & (qr < 1e6)
+    assert np.all(np.abs(q[ok] / qr[ok] - 1) <= Q_RTOL)
+    # termination: no pair adjacent along the curve with a gap has a sample above the threshold
+    qa = b["q"].cpu().numpy()[:n]
+    hot = (np.nan_to_num(qa[:-1]) > thr) | (np.nan_to_num(qa[1:]) > thr)
+    gaps = np.diff(keys.astype(np.int64))
+    if ndim == 2:  # full square lattice: every gap has cells to insert
+        assert not np.any(hot & (gaps > 1) & (iters < sp.max_iters))
