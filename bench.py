@@ -61,7 +61,8 @@ def parse():
                     help="cell: cell-wise Dormand-Prince (default); ck: the paper's plain Cash-Karp")
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (fixed tolerance and shape)")
-    ap.add_argument("--config", default="refine2d", choices=["refine2d", "volume", "batch64", "learned", "qcrit"],
+    ap.add_argument("--config", default="refine2d",
+                    choices=["refine2d", "volume", "batch64", "learned", "qcrit", "euler"],
                     help="refine2d: 1024^2 map refined to 4096^2 (default); volume: 512x512x256 Q/FLL/FLEDGE volume "
                          "of an 8-charge field on 384^3")
     ap.add_argument("--shape", default=None,
@@ -442,6 +443,56 @@ def run_batch(args, qsl, torch, dev, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_euler(args, qsl, torch, dev, rank, world, local):
+    """Fixed-step Euler (Sec. "Integration methods": step 1/5 of the smallest
+    spacing) against the adaptive cell-wise Dormand-Prince path on the bench
+    field's 1024^2 z = 0 map: map time (CUDA events) and each path's error
+    against the FP64 oracle at tol 1e-11 on 200 seeded pixels."""
+    import oracle
+    from paper_1609_00724_gb300 import inputs
+    c = args.coarse
+    gf = make_field(replica_seed(FIELD_SEED, rank), dev, args.grid)
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
+    N = c * c
+    q = torch.empty(N, device=dev)
+    L = torch.empty(N, device=dev)
+    fc = torch.empty(2 * N, dtype=torch.uint8, device=dev)
+    runs = {"euler": qsl.qsl_opts_default(integrator=qsl.QSL_EULER, euler_h=0.2),
+            "adaptive_cell": opts(qsl)}
+    idx = inputs.subsample(N, 200, 7)
+    seeds = oracle.plane_seeds([0, 0, 0], [2, 0, 0], [0, 2, 0], c, c)[idx]
+    g = inputs.to_numpy64(make_field(replica_seed(FIELD_SEED, rank), "cpu", args.grid))
+    Fo = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
+    ref = oracle.trace_seeds(Fo, seeds, oracle.default_opts(tol_abs=1e-11, tol_rel=1e-11, nthreads=os.cpu_count()))
+    cell = float(min(np.min(np.diff(a)) for a in (g.xc, g.yc, g.zc)))
+    res = {}
+    for name, o in runs.items():
+        best = None
+        for _ in range(3):
+            qsl.qsl_q_map_2d(F, (0, 0, 0), (2, 0, 0), (0, 2, 0), c, c, o, q=q, length=L, faces=fc)
+            st = qsl.qsl_last_stats()
+            best = st["kernel_ms"] if best is None else min(best, st["kernel_ms"])
+        qg, lg = q.cpu().numpy()[idx], L.cpu().numpy()[idx]
+        fg = fc.cpu().numpy().reshape(-1, 2)[idx]
+        same = (fg[:, 0] == ref["face_f"]) & (fg[:, 1] == ref["face_b"])
+        ok = same & np.isfinite(ref["q_perp"]) & (ref["q_perp"] < 1e6)
+        qe = np.abs(qg[ok] / ref["q_perp"][ok] - 1)
+        le = np.abs(lg[same] - ref["L"][same]) / np.maximum(ref["L"][same], cell)
+        res[name] = {"map_ms": best, "q_points_per_s": N / (best / 1000.0), "stage_evals": st["stage_evals"],
+                     "faces_equal": float(same.mean()), "q_rel_median": float(np.median(qe)),
+                     "q_rel_p99": float(np.quantile(qe, 0.99)), "q_rel_max": float(qe.max()),
+                     "l_rel_max": float(le.max())}
+    line = {"metric": "Euler fixed-step map throughput / adaptive cell-wise throughput (errors vs FP64 oracle)",
+            "value": res["euler"]["q_points_per_s"] / res["adaptive_cell"]["q_points_per_s"], "unit": "x",
+            "n_gpus": world, "steps": 3, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "4-charge potential field %d^3 FP32, %d^2 z=0 Q map" % (args.grid, c),
+                       "euler_h_cells": 0.2, "adaptive_tol": RUN["tol"], "parity_seeds": 200},
+            "results": res}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_qcrit(args, qsl, torch, dev, rank, world, local):
     """Refinement criteria compared (Sec. "Adaptive refinements"): the FLL jump
     (tau 0.05) against a Q threshold (Q > 100), both refining the 1024^2 z = 0
@@ -596,18 +647,19 @@ def main():
     dev = torch.device("cuda", local)
     from paper_1609_00724_gb300 import qsl
     qsl.lib()
-    if args.config in ("volume", "batch64", "learned", "qcrit"):
-        {"volume": run_volume, "batch64": run_batch, "learned": run_learned, "qcrit": run_qcrit}[args.config](
+    if args.shape:
+        RUN["shape"] = tuple(int(v) for v in args.shape.split(","))
+    if args.hmax:
+        RUN["h_max"] = args.hmax
+    if args.config in ("volume", "batch64", "learned", "qcrit", "euler"):
+        {"volume": run_volume, "batch64": run_batch, "learned": run_learned, "qcrit": run_qcrit,
+         "euler": run_euler}[args.config](
             args, qsl, torch, dev, rank, world, local)
         if world > 1:
             torch.distributed.destroy_process_group()
         return
     field_seed = replica_seed(FIELD_SEED, rank)
     gf = make_field(field_seed, dev, args.grid)
-    if args.shape:
-        RUN["shape"] = tuple(int(v) for v in args.shape.split(","))
-    if args.hmax:
-        RUN["h_max"] = args.hmax
     if args.profile_refine:
         bufs = alloc(torch, args.coarse, dev)
         for _ in range(args.steps):
