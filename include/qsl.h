@@ -398,6 +398,15 @@ int qsl_convert(const uint64_t* keys, const float* vals, int64_t n, int ndim, in
 /* Kernels of this library launched by this process since the library was
  * loaded (all threads). Radix sorts and scans inside qsl_refine run CUB
  * kernels, which are not counted. */
+/* Device memory: the library's temporary buffers (tracer scratch, refinement
+ * work arrays, sort storage) come from its own stream-ordered pool on each
+ * device, which keeps freed blocks cached for the next call (no return to the
+ * driver at each synchronisation; peak about 100 bytes per refinement sample
+ * of capacity). qsl_trim_pool hands the cached blocks back to the driver on
+ * every device the library has used (no paper counterpart). Synchronous with
+ * respect to nothing: blocks still in use by queued work stay allocated. */
+int qsl_trim_pool(void);
+
 int64_t qsl_kernel_launches(void);
 
 /* Human-readable message of the last failing call on this thread. */

@@ -6,6 +6,9 @@
 #include <cstring>
 #include <string>
 
+#include <map>
+#include <mutex>
+
 #include "qsl_internal.cuh"
 
 namespace qsl {
@@ -106,6 +109,38 @@ int validate_opts(const qsl_field* f, const qsl_opts* o) {
     QSL_FAIL(QSL_EINVAL, "line_lanes must be 0, 1 or 3");
   if (o->reserved != 0) QSL_FAIL(QSL_EINVAL, "reserved must be 0");
   return QSL_OK;
+}
+
+namespace {
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+}  // namespace
+
+cudaError_t alloc_async(void** p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it == g_pools.end()) {
+      cudaMemPoolProps props;
+      memset(&props, 0, sizeof props);
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pool, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = UINT64_MAX;
+      e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) return e;
+      g_pools[dev] = pool;
+    } else {
+      pool = it->second;
+    }
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
 int default_shape(const qsl_opts* o, int tangent, int precision, LaunchShape* s) {
@@ -328,8 +363,8 @@ int run_lines(const qsl_field* f, const SeedSource& src, int64_t S, const qsl_op
   if (o->precision == QSL_FP32_MIXED && o->retrace_q > 0 && !o->length_only && S > 0) {
     int64_t* index = nullptr;
     int64_t* count = nullptr;
-    QSL_CHECK_CUDA(cudaMallocAsync((void**)&index, sizeof(int64_t) * S, stream));
-    QSL_CHECK_CUDA(cudaMallocAsync((void**)&count, sizeof(int64_t), stream));
+    QSL_CHECK_CUDA(qsl::alloc_async((void**)&index, sizeof(int64_t) * S, stream));
+    QSL_CHECK_CUDA(qsl::alloc_async((void**)&count, sizeof(int64_t), stream));
     rc = select_retrace(src, S, out, o->retrace_q, index, count, stream);
     if (rc) return rc;
     LineOutputs o2 = out;
@@ -362,7 +397,7 @@ static int stage_out(void* user, size_t bytes, int mem, cudaStream_t s, Staged* 
     st->dev = user;
     return QSL_OK;
   }
-  QSL_CHECK_CUDA(cudaMallocAsync(&st->dev, bytes ? bytes : 1, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&st->dev, bytes ? bytes : 1, s));
   st->owned = true;
   return QSL_OK;
 }
@@ -374,7 +409,7 @@ static int stage_in(const void* user, size_t bytes, int mem, cudaStream_t s, Sta
     st->dev = (void*)user;
     return QSL_OK;
   }
-  QSL_CHECK_CUDA(cudaMallocAsync(&st->dev, bytes ? bytes : 1, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&st->dev, bytes ? bytes : 1, s));
   st->owned = true;
   if (bytes) QSL_CHECK_CUDA(cudaMemcpyAsync(st->dev, user, bytes, cudaMemcpyHostToDevice, s));
   return QSL_OK;
@@ -409,7 +444,7 @@ static int map_common(const qsl_field* f, const SeedSource& src, int64_t S, cons
   // the FP64 retrace selects from the q output; give it a scratch one if absent
   Staged sq2;
   if (!out.q && o->precision == QSL_FP32_MIXED && o->retrace_q > 0 && !o->length_only) {
-    QSL_CHECK_CUDA(cudaMallocAsync(&sq2.dev, S * sizeof(float) + 4, stream));
+    QSL_CHECK_CUDA(qsl::alloc_async((void**)&sq2.dev, S * sizeof(float) + 4, stream));
     sq2.owned = true;
     sq2.bytes = 0;
     out.q = (float*)sq2.dev;
@@ -485,6 +520,12 @@ int qsl_q_volume_3d(const qsl_field* f, const double lo[3], const double hi[3], 
     src.u[k] = hi[k];
   }
   return map_common(f, src, (int64_t)nx * ny * nz, o, q, length, faces, status, mem, (cudaStream_t)stream);
+}
+
+int qsl_trim_pool(void) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  for (auto& kv : g_pools) QSL_CHECK_CUDA(cudaMemPoolTrimTo(kv.second, 0));
+  return QSL_OK;
 }
 
 int qsl_last_stats(qsl_stats* s) {

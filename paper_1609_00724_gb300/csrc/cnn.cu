@@ -212,7 +212,7 @@ int ensure_act(qsl_cnn* c, size_t pixels, cudaStream_t s) {
   if (need <= c->act_cap) return QSL_OK;
   if (c->act) QSL_CHECK_CUDA(cudaFreeAsync(c->act, s));
   c->act = nullptr;
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&c->act, need * sizeof(float), s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&c->act, need * sizeof(float), s));
   c->act_cap = need;
   return QSL_OK;
 }

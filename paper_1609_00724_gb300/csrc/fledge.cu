@@ -121,7 +121,7 @@ int fledge_device(const float* L, int ndim, const int64_t* shape, float* S, cuda
   int64_t n = 1;
   for (int i = 0; i < ndim; ++i) n *= shape[i];
   unsigned* fill = nullptr;
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&fill, sizeof(unsigned), stream));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&fill, sizeof(unsigned), stream));
   QSL_CHECK_CUDA(cudaMemsetAsync(fill, 0, sizeof(unsigned), stream));
   int dev = 0, sms = 0;
   QSL_CHECK_CUDA(cudaGetDevice(&dev));
@@ -179,8 +179,8 @@ extern "C" int qsl_fledge(const float* length, int ndim, const int64_t* shape, f
     return QSL_EINVAL;
   }
   float *dL = nullptr, *dS = nullptr;
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&dL, n * sizeof(float), stream));
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&dS, n * sizeof(float), stream));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&dL, n * sizeof(float), stream));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&dS, n * sizeof(float), stream));
   QSL_CHECK_CUDA(cudaMemcpyAsync(dL, length, n * sizeof(float), cudaMemcpyHostToDevice, stream));
   int rc = qsl::fledge_device(dL, ndim, shape, dS, stream);
   if (rc) return rc;

@@ -112,6 +112,12 @@ struct TraceConfig {
   unsigned long long timeout_ns;  // device watchdog per warp (%globaltimer), 0 = none
 };
 
+// Stream-ordered allocation from the library's own memory pool on the current
+// device (created on first use, release threshold unlimited: freed blocks stay
+// cached for the next call instead of going back to the driver at every
+// synchronisation). Free with cudaFreeAsync.
+cudaError_t alloc_async(void** p, size_t bytes, cudaStream_t s);
+
 struct LaunchShape {
   int warps_per_block;
   int blocks_per_sm;

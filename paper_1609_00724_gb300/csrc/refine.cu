@@ -451,9 +451,9 @@ struct Scratch {
   template <class T>
   int alloc(T** p, size_t count) {
     void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, count * sizeof(T) + 16, s);
+    cudaError_t e = qsl::alloc_async((void**)&q, count * sizeof(T) + 16, s);
     if (e != cudaSuccess) {
-      set_error("cudaMallocAsync of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      set_error("stream-ordered allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
       return QSL_ENOMEM;
     }
     bufs.push_back(q);
@@ -472,7 +472,7 @@ int sort_pairs(const uint64_t* kin, uint64_t* kout, const int64_t* vin, int64_t*
   size_t tmp = 0;
   QSL_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, kin, kout, vin, vout, n, 0, bits, s));
   void* t = nullptr;
-  QSL_CHECK_CUDA(cudaMallocAsync(&t, tmp + 16, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&t, tmp + 16, s));
   QSL_CHECK_CUDA(cub::DeviceRadixSort::SortPairs(t, tmp, kin, kout, vin, vout, n, 0, bits, s));
   QSL_CHECK_CUDA(cudaFreeAsync(t, s));
   return QSL_OK;
@@ -483,7 +483,7 @@ int exclusive_sum(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
   size_t tmp = 0;
   QSL_CHECK_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, in, out, n, s));
   void* t = nullptr;
-  QSL_CHECK_CUDA(cudaMallocAsync(&t, tmp + 16, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&t, tmp + 16, s));
   QSL_CHECK_CUDA(cub::DeviceScan::ExclusiveSum(t, tmp, in, out, n, s));
   QSL_CHECK_CUDA(cudaFreeAsync(t, s));
   return QSL_OK;
@@ -931,8 +931,8 @@ int qsl_hilbert_encode(const uint32_t* coords, int64_t n, int ndim, int bits, ui
   const uint32_t* c = coords;
   uint64_t* k = keys;
   if (mem == QSL_MEM_HOST) {
-    QSL_CHECK_CUDA(cudaMallocAsync((void**)&c, n * ndim * 4, s));
-    QSL_CHECK_CUDA(cudaMallocAsync((void**)&k, n * 8, s));
+    QSL_CHECK_CUDA(qsl::alloc_async((void**)&c, n * ndim * 4, s));
+    QSL_CHECK_CUDA(qsl::alloc_async((void**)&k, n * 8, s));
     QSL_CHECK_CUDA(cudaMemcpyAsync((void*)c, coords, n * ndim * 4, cudaMemcpyHostToDevice, s));
   }
   encode_kernel<<<grid_for(n), 256, 0, s>>>(c, n, ndim, bits, k);
@@ -962,8 +962,8 @@ int qsl_hilbert_decode(const uint64_t* keys, int64_t n, int ndim, int bits, uint
   const uint64_t* k = keys;
   uint32_t* c = coords;
   if (mem == QSL_MEM_HOST) {
-    QSL_CHECK_CUDA(cudaMallocAsync((void**)&k, n * 8, s));
-    QSL_CHECK_CUDA(cudaMallocAsync((void**)&c, n * ndim * 4, s));
+    QSL_CHECK_CUDA(qsl::alloc_async((void**)&k, n * 8, s));
+    QSL_CHECK_CUDA(qsl::alloc_async((void**)&c, n * ndim * 4, s));
     QSL_CHECK_CUDA(cudaMemcpyAsync((void*)k, keys, n * 8, cudaMemcpyHostToDevice, s));
   }
   decode_kernel<<<grid_for(n), 256, 0, s>>>(k, n, ndim, bits, c);
@@ -998,9 +998,9 @@ int qsl_convert(const uint64_t* keys, const float* vals, int64_t n, int ndim, in
   if (mem == QSL_MEM_DEVICE) return convert_device(keys, vals, n, ndim, max_order, extent, out_order, log_interp, out, s);
   uint64_t* k = nullptr;
   float *v = nullptr, *o = nullptr;
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&k, n * 8 + 8, s));
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&v, n * 4 + 4, s));
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&o, N * 4, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&k, n * 8 + 8, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&v, n * 4 + 4, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&o, N * 4, s));
   if (n) {
     QSL_CHECK_CUDA(cudaMemcpyAsync(k, keys, n * 8, cudaMemcpyHostToDevice, s));
     QSL_CHECK_CUDA(cudaMemcpyAsync(v, vals, n * 4, cudaMemcpyHostToDevice, s));
@@ -1066,11 +1066,11 @@ int qsl_refine(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o,
     void* sf = nullptr;
     void* ss = nullptr;
     if (!d.faces) {
-      QSL_CHECK_CUDA(cudaMallocAsync(&sf, 2 * d.capacity, s));
+      QSL_CHECK_CUDA(qsl::alloc_async((void**)&sf, 2 * d.capacity, s));
       d.faces = (uint8_t*)sf;
     }
     if (!d.status) {
-      QSL_CHECK_CUDA(cudaMallocAsync(&ss, d.capacity, s));
+      QSL_CHECK_CUDA(qsl::alloc_async((void**)&ss, d.capacity, s));
       d.status = (uint8_t*)ss;
     }
     int rc = refine_device(f, sp, o, &d, q_grid, l_grid, QSL_MEM_DEVICE, s);
@@ -1087,11 +1087,11 @@ int qsl_refine(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o,
   }
   int64_t cap = smp->capacity;
   qsl_samples d = *smp;
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&d.key, cap * 8, s));
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&d.q, cap * 4, s));
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&d.length, cap * 4, s));
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&d.faces, cap * 2, s));
-  QSL_CHECK_CUDA(cudaMallocAsync((void**)&d.status, cap, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&d.key, cap * 8, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&d.q, cap * 4, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&d.length, cap * 4, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&d.faces, cap * 2, s));
+  QSL_CHECK_CUDA(qsl::alloc_async((void**)&d.status, cap, s));
   int64_t c0 = smp->count;
   if (c0) {
     QSL_CHECK_CUDA(cudaMemcpyAsync(d.key, smp->key, c0 * 8, cudaMemcpyHostToDevice, s));
@@ -1108,8 +1108,8 @@ int qsl_refine(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o,
   int64_t N = 1;
   for (int a = 0; a < nd; ++a) N *= ext[a] >> dd;
   float *qg = nullptr, *lg = nullptr;
-  if (q_grid) QSL_CHECK_CUDA(cudaMallocAsync((void**)&qg, N * 4, s));
-  if (l_grid) QSL_CHECK_CUDA(cudaMallocAsync((void**)&lg, N * 4, s));
+  if (q_grid) QSL_CHECK_CUDA(qsl::alloc_async((void**)&qg, N * 4, s));
+  if (l_grid) QSL_CHECK_CUDA(qsl::alloc_async((void**)&lg, N * 4, s));
   int rc = refine_device(f, sp, o, &d, qg, lg, QSL_MEM_HOST, s);
   if (rc == QSL_OK || rc == QSL_ECAPACITY) {
     int64_t n = d.count;

@@ -1981,7 +1981,7 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
   size_t n_units = (size_t)(2 * n_seeds);
   const bool own = scratch == nullptr;
   if (own)
-    QSL_CHECK_CUDA(cudaMallocAsync(&scratch, 256 + sizeof(EndRec<R>) * (n_units ? n_units : 1), stream));
+    QSL_CHECK_CUDA(qsl::alloc_async((void**)&scratch, 256 + sizeof(EndRec<R>) * (n_units ? n_units : 1), stream));
   unsigned long long* head = reinterpret_cast<unsigned long long*>(scratch);
   EndRec<R>* ends = reinterpret_cast<EndRec<R>*>(reinterpret_cast<unsigned char*>(scratch) + 256);
   QSL_CHECK_CUDA(cudaMemsetAsync(head, 0, 16, stream));

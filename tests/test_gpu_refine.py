@@ -236,6 +236,10 @@ def test_refine_time_accounting(qsl, oracle_mod):
     assert st["total_ms"] > 0 and st["coarse_ms"] > 0
     assert st["coarse_ms"] + st["passes_ms"] <= st["total_ms"] * 1.001
     assert st["coarse_stage_evals"] > 0 and (st["pass_stage_evals"] > 0) == (st["pass_lines"] > 0)
+    # the pool's cached blocks go back to the driver; a later refine allocates again
+    qsl.qsl_trim_pool()
+    n2, _, _, rc2 = qsl.qsl_refine(F, sp, o, b["key"], b["q"], b["L"], b["faces"], b["st"])
+    assert rc2 == qsl.QSL_OK and n2 == n
 
 
 @pytest.mark.parametrize("ndim", [2, 3])
