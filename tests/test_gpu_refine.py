@@ -281,3 +281,55 @@ def test_refine_q_threshold_criterion_matches_oracle(qsl, oracle_mod, ndim):
     gaps = np.diff(keys.astype(np.int64))
     if ndim == 2:  # full square lattice: every gap has cells to insert
         assert not np.any(hot & (gaps > 1) & (iters < sp.max_iters))
+
+
+def test_bench_refined_map_full_size_sampled(qsl, oracle_mod):
+    """The refined-map workload at full size in the settings the bench times
+    after tuning (4 charges, seed 2, on 256^3 FP32; 1024^2 z = 0 map refined to
+    4096^2; tol 1e-5, step cap 4 smallest spacings, 4 warps per block, 32
+    blocks per SM, refill 8): coarse and refined samples against the FP64
+    oracle, and FLEDGE of the converted length grid against the oracle's
+    Sobel on a block."""
+    from gpu_helpers import compare_lines
+    gf = inputs.charge_field(inputs.random_charges(4, 2), 256, dtype=torch.float32, device="cuda", slab=32)
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
+    sp = qsl.refine_spec(ndim=2, coarse_order=10, max_order=12, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0),
+                         tau=0.05, shift=1, max_iters=64)
+    o = qsl.qsl_opts_default(tol_abs=1e-5, tol_rel=1e-5, integrator=qsl.QSL_DOPRI5_CELL, h_max=4.0)
+    o.warps_per_block, o.blocks_per_sm, o.refill_min = 4, 32, 8
+    eff = 4096
+    b = _alloc(eff * eff)
+    qg = torch.empty(eff * eff, device="cuda")
+    lg = torch.empty(eff * eff, device="cuda")
+    n, iters, traced, rc = qsl.qsl_refine(F, sp, o, b["key"], b["q"], b["L"], b["faces"], b["st"], q_grid=qg,
+                                          l_grid=lg)
+    assert rc == qsl.QSL_OK and iters > 0 and n > 1024 * 1024
+    S = torch.empty((eff, eff), device="cuda")
+    qsl.qsl_fledge(lg.view(eff, eff), S)
+    torch.cuda.synchronize()
+    keys = b["key"].cpu().numpy()[:n].view(np.uint64)
+    assert np.all(np.diff(keys.astype(np.int64)) > 0)
+    # 150 coarse (index 2 modulo 4 on both axes) and 150 refined samples
+    c = np.zeros((n, 2), dtype=np.uint32)
+    qsl.qsl_hilbert_decode(keys, 2, 12, c)
+    coarse = (c[:, 0] % 4 == 2) & (c[:, 1] % 4 == 2)
+    assert coarse.sum() == 1024 * 1024
+    ci = np.where(coarse)[0][inputs.subsample(int(coarse.sum()), 150, 31)]
+    ri = np.where(~coarse)[0][inputs.subsample(int((~coarse).sum()), 150, 32)]
+    idx = np.concatenate([ci, ri])
+    pos = np.column_stack([(c[idx, 0] + 0.5) / eff * 2 - 1, (c[idx, 1] + 0.5) / eff * 2 - 1, np.zeros(len(idx))])
+    g = inputs.GridField(*(a.cpu().numpy().astype(np.float64) for a in (gf.bx, gf.by, gf.bz)), gf.xc, gf.yc, gf.zc)
+    del gf
+    Fo = oracle_mod.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
+    cell = min_spacing(g)
+    del g
+    ref = oracle_mod.trace_seeds(Fo, pos, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
+    fa = b["faces"].cpu().numpy()[:2 * n].reshape(-1, 2)
+    gd = {"q_perp": b["q"].cpu().numpy()[:n][idx], "L": b["L"].cpu().numpy()[:n][idx], "face_f": fa[idx, 0],
+          "face_b": fa[idx, 1]}
+    compare_lines(gd, ref, cell, (-1, -1, 0), (1, 1, 1))
+    # FLEDGE of the converted length grid on a block (Sobel input is that same grid)
+    Lb = lg.view(eff, eff)[2000:2100, 1500:1620].contiguous().cpu().numpy()
+    Sb = S[2001:2099, 1501:1619].cpu().numpy()
+    want = oracle_mod.fledge(Lb)[1:-1, 1:-1]
+    assert np.allclose(Sb, want, rtol=1e-5, atol=1e-6 * float(np.abs(Lb).max()))
