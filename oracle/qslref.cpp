@@ -55,6 +55,7 @@ struct Field {
   int mode;                  // 0 = paper (normalise first), 1 = raw B
   double glo[3], ghi[3];
   double cell;               // smallest grid spacing over all axes
+  int order = 1;             // interpolation: 1 trilinear, 2 triquadratic, 3 tricubic (uniform grids)
 };
 
 struct Stats {
@@ -123,7 +124,58 @@ struct Interp {
   double bmag;     // unnormalised |B| at the point
 };
 
-// Trilinear interpolation (Eq. interp with the trilinear kernels f_v) and its
+// Higher-order interpolation kernels of Sec. "Interpolation schemes" (the
+// paper cites them; written here from their published definitions), as 1D
+// weights w_k and dw_k/du for the stencil vertices idx_k along one axis. The
+// point lies in cell c at fraction u; s is its offset from a vertex in units of
+// the spacing. Stencil vertices beyond the grid are clamped to its edge.
+//  order 3, Keys (1981) cubic convolution with a = -1/2, vertices c-1..c+2:
+//    W(s) = 1.5|s|^3 - 2.5|s|^2 + 1 (|s| <= 1), -0.5|s|^3 + 2.5|s|^2 - 4|s| + 2
+//    (1 < |s| < 2), 0 beyond;
+//  order 2, Dodgson (1997) interpolating quadratic, the vertex m nearest the
+//  point and its two neighbours:
+//    W(s) = 1 - 2 s^2 (|s| <= 1/2), s^2 - 2.5|s| + 1.5 (1/2 < |s| <= 3/2), 0 beyond.
+// Returns the number of taps.
+int ho_weights(int order, int c, double u, int n, int* idx, double* w, double* dw) {
+  if (order == 3) {
+    for (int k = 0; k < 4; ++k) {
+      double s = u - (k - 1);  // offset from vertex c - 1 + k
+      double a = std::fabs(s), sg = s < 0 ? -1.0 : 1.0;
+      if (a <= 1) {
+        w[k] = 1.5 * a * a * a - 2.5 * a * a + 1;
+        dw[k] = sg * (4.5 * a * a - 5 * a);
+      } else if (a < 2) {
+        w[k] = -0.5 * a * a * a + 2.5 * a * a - 4 * a + 2;
+        dw[k] = sg * (-1.5 * a * a + 5 * a - 4);
+      } else {
+        w[k] = 0;
+        dw[k] = 0;
+      }
+      idx[k] = std::min(std::max(c - 1 + k, 0), n - 1);
+    }
+    return 4;
+  }
+  int m = c + (u >= 0.5 ? 1 : 0);
+  double t = u - (m - c);
+  for (int k = 0; k < 3; ++k) {
+    double s = t - (k - 1);  // offset from vertex m - 1 + k
+    double a = std::fabs(s), sg = s < 0 ? -1.0 : 1.0;
+    if (a <= 0.5) {
+      w[k] = 1 - 2 * s * s;
+      dw[k] = -4 * s;
+    } else if (a <= 1.5) {
+      w[k] = a * a - 2.5 * a + 1.5;
+      dw[k] = sg * (2 * a - 2.5);
+    } else {
+      w[k] = 0;
+      dw[k] = 0;
+    }
+    idx[k] = std::min(std::max(m - 1 + k, 0), n - 1);
+  }
+  return 3;
+}
+
+// Interpolation (Eq. interp with the kernels f_v of the field's order) and its
 // analytic gradient (the gradient acts on the kernels only, Sec. "Field-line
 // deviation using linearization").
 void interp(const Field& F, const double* x, Interp* out, Stats* st) {
@@ -133,6 +185,25 @@ void interp(const Field& F, const double* x, Interp* out, Stats* st) {
   for (int a = 0; a < 3; ++a) locate(F, a, x[a], &ci[a], &u[a], &h[a]);
   double val[4] = {0, 0, 0, 0};
   double grad[4][3] = {{0}};
+  if (F.order > 1) {
+    int idx[3][4];
+    double w[3][4], dw[3][4];
+    int K = 0;
+    for (int a = 0; a < 3; ++a) K = ho_weights(F.order, ci[a], u[a], F.n[a], idx[a], w[a], dw[a]);
+    for (int kz = 0; kz < K; ++kz)
+      for (int ky = 0; ky < K; ++ky)
+        for (int kx = 0; kx < K; ++kx) {
+          double f = w[0][kx] * w[1][ky] * w[2][kz];
+          double df[3] = {dw[0][kx] * w[1][ky] * w[2][kz] / h[0], w[0][kx] * dw[1][ky] * w[2][kz] / h[1],
+                          w[0][kx] * w[1][ky] * dw[2][kz] / h[2]};
+          size_t vi = ((size_t)idx[2][kz] * F.n[1] + idx[1][ky]) * F.n[0] + idx[0][kx];
+          const double* p = &F.v[4 * vi];
+          for (int k = 0; k < 4; ++k) {
+            val[k] += p[k] * f;
+            for (int j = 0; j < 3; ++j) grad[k][j] += p[k] * df[j];
+          }
+        }
+  } else
   for (int vz = 0; vz < 2; ++vz)
     for (int vy = 0; vy < 2; ++vy)
       for (int vx = 0; vx < 2; ++vx) {
@@ -811,6 +882,23 @@ void qslref_opts_default(Opts* o) {
 }
 
 int qslref_sizeof_opts(void) { return (int)sizeof(Opts); }
+
+// Interpolation order of a loaded field: 1 (trilinear), 2 (triquadratic) or
+// 3 (tricubic; orders 2 and 3 need uniform spacing on every axis). Returns 0,
+// or -1 for a bad order or a non-uniform grid.
+int qslref_set_interp_order(void* field, int order) {
+  Field* F = (Field*)field;
+  if (order < 1 || order > 3) return -1;
+  if (order > 1) {
+    for (int a = 0; a < 3; ++a) {
+      double h0 = F->c[a][1] - F->c[a][0];
+      for (int i = 1; i + 1 < F->n[a]; ++i)
+        if (std::fabs((F->c[a][i + 1] - F->c[a][i]) - h0) > 1e-9 * h0) return -1;
+    }
+  }
+  F->order = order;
+  return 0;
+}
 
 void* qslref_load_field(const double* bx, const double* by, const double* bz, int nx, int ny, int nz,
                         const double* xc, const double* yc, const double* zc, int mode) {
