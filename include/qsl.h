@@ -116,12 +116,17 @@ typedef struct qsl_opts {
                               up to 512 line directions per SM, where a launch is bound
                               by the latency of its longest lines; results agree to
                               rounding)                                                  */
-  int32_t reserved;        /* must be 0                                                 */
+  int32_t interp_order;    /* Sec. "Interpolation schemes": 1 (or 0) trilinear, 2 triquadratic
+                              (Dodgson's interpolating quadratic, 27 vertices), 3 tricubic
+                              (Keys cubic convolution, 64 vertices); 2 and 3 need a uniform
+                              grid and QSL_RKCK54 or QSL_EULER; stencil vertices beyond the
+                              grid are clamped to its edge                                */
 } qsl_opts; /* 176 bytes */
 
 /* Fills the defaults: RKCK54, Q_PERP, FP32_MIXED, tol 1e-2/1e-2, h_init 0.1,
  * h_max 2, h_min 1e-15 cells, max_length 20 x diagonal, max_steps 1e6,
- * euler_h 0.2, retrace_q 1e6, land_tol 1e-12, no watchdog, line_lanes 0 (auto). */
+ * euler_h 0.2, retrace_q 1e6, land_tol 1e-12, no watchdog, line_lanes 0 (auto),
+ * interp_order 1. */
 void qsl_opts_default(qsl_opts* opts);
 
 /* ---- per-line record (qsl_trace_seeds) --------------------------------------- */

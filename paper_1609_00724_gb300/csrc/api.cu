@@ -89,6 +89,7 @@ void resolve_config(const qsl_field* f, const qsl_opts* o, TraceConfig* c) {
   c->integrator = o->integrator;
   c->length_only = o->length_only;
   c->timeout_ns = o->timeout_s > 0 ? (unsigned long long)(o->timeout_s * 1e9) : 0ull;
+  c->interp_order = o->interp_order > 1 ? o->interp_order : 1;
 }
 
 int validate_opts(const qsl_field* f, const qsl_opts* o) {
@@ -107,7 +108,11 @@ int validate_opts(const qsl_field* f, const qsl_opts* o) {
   if (o->refill_min < 0 || o->refill_min > 32) QSL_FAIL(QSL_EINVAL, "refill_min must be 0..32");
   if (o->line_lanes != 0 && o->line_lanes != 1 && o->line_lanes != 3)
     QSL_FAIL(QSL_EINVAL, "line_lanes must be 0, 1 or 3");
-  if (o->reserved != 0) QSL_FAIL(QSL_EINVAL, "reserved must be 0");
+  if (o->interp_order < 0 || o->interp_order > 3) QSL_FAIL(QSL_EINVAL, "interp_order must be 0..3");
+  if (o->interp_order > 1 && !f->uniform)
+    QSL_FAIL(QSL_EINVAL, "triquadratic and tricubic interpolation need a uniform grid");
+  if (o->interp_order > 1 && o->integrator == QSL_DOPRI5_CELL)
+    QSL_FAIL(QSL_EINVAL, "the cell-wise integrator is trilinear only; use QSL_RKCK54 or QSL_EULER");
   return QSL_OK;
 }
 
@@ -205,7 +210,7 @@ void qsl_opts_default(qsl_opts* o) {
   o->land_tol = 1e-12;
   o->timeout_s = 0;
   o->line_lanes = 0;
-  o->reserved = 0;
+  o->interp_order = 1;
 }
 
 int qsl_load_field(const void* bx, const void* by, const void* bz, int dtype, int mem, int nx, int ny, int nz,

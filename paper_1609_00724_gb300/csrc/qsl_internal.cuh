@@ -49,6 +49,7 @@ struct FieldView {
   int n[3];
   int uniform;        // 1: all axes uniform (fast cell location)
   int raw;            // 1: QSL_RAW_B packing, 0: paper packing
+  int order;          // interpolation: 1 trilinear, 2 triquadratic, 3 tricubic (uniform grids)
 };
 
 }  // namespace qsl
@@ -110,6 +111,7 @@ struct TraceConfig {
   int integrator;
   int length_only;
   unsigned long long timeout_ns;  // device watchdog per warp (%globaltimer), 0 = none
+  int interp_order;  // 1, 2 or 3
 };
 
 // Stream-ordered allocation from the library's own memory pool on the current

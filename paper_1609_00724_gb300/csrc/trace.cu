@@ -119,12 +119,103 @@ __device__ __forceinline__ R tri0(R v000, R v100, R v010, R v110, R v001, R v101
   return fma(w, b1 - b0, b0);
 }
 
+// Taps of the higher-order kernels along one axis for a point in cell c at
+// fraction u (Sec. "Interpolation schemes"; the cited methods, restated):
+// order 3, Keys cubic convolution (a = -1/2) on vertices c-1..c+2; order 2,
+// Dodgson's interpolating quadratic on the vertex m nearest the point and its
+// two neighbours. w: weights, g: d w / d u; vertices clamped to [0, n-1].
+// Returns the number of taps (4 or 3; a fourth tap of weight 0 pads order 2).
+template <class R>
+__device__ __forceinline__ int ho_taps(int order, int c, R u, int n, int* idx, R* w, R* g) {
+  if (order == 3) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const R s = u - R(k - 1), a = fabs(s), sg = s < R(0) ? R(-1) : R(1);
+      if (a <= R(1)) {
+        w[k] = (R(1.5) * a - R(2.5)) * a * a + R(1);
+        g[k] = sg * (R(4.5) * a - R(5)) * a;
+      } else if (a < R(2)) {
+        w[k] = ((R(-0.5) * a + R(2.5)) * a - R(4)) * a + R(2);
+        g[k] = sg * ((R(-1.5) * a + R(5)) * a - R(4));
+      } else {
+        w[k] = R(0);
+        g[k] = R(0);
+      }
+      idx[k] = min(max(c - 1 + k, 0), n - 1);
+    }
+    return 4;
+  }
+  const int m = c + (u >= R(0.5) ? 1 : 0);
+  const R t = u - R(m - c);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const R s = t - R(k - 1), a = fabs(s), sg = s < R(0) ? R(-1) : R(1);
+    if (a <= R(0.5)) {
+      w[k] = R(1) - R(2) * s * s;
+      g[k] = R(-4) * s;
+    } else if (a <= R(1.5)) {
+      w[k] = (a - R(2.5)) * a + R(1.5);
+      g[k] = sg * (R(2) * a - R(2.5));
+    } else {
+      w[k] = R(0);
+      g[k] = R(0);
+    }
+    idx[k] = min(max(m - 1 + k, 0), n - 1);
+  }
+  w[3] = R(0);
+  g[3] = R(0);
+  idx[3] = idx[2];
+  return 3;
+}
+
+// Value (4 stored components) and local-coordinate gradient of the
+// higher-order interpolant: separable sums over the K^3 stencil vertices.
+template <class R, class S, bool GRAD>
+__device__ void ho_sum(const FieldView<S>& F, const int* ci, const R* uu, R* val4, R (*d)[3]) {
+  int ix[4], iy[4], iz[4];
+  R wx[4], wy[4], wz[4], gx[4], gy[4], gz[4];
+  const int K = ho_taps<R>(F.order, ci[0], uu[0], F.n[0], ix, wx, gx);
+  ho_taps<R>(F.order, ci[1], uu[1], F.n[1], iy, wy, gy);
+  ho_taps<R>(F.order, ci[2], uu[2], F.n[2], iz, wz, gz);
+  typedef typename V4<S>::type V;
+  const size_t sy = (size_t)F.n[0], sz = (size_t)F.n[0] * (size_t)F.n[1];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    val4[c] = R(0);
+    if (GRAD && c < 3) d[c][0] = d[c][1] = d[c][2] = R(0);
+  }
+  for (int kz = 0; kz < K; ++kz) {
+    for (int ky = 0; ky < K; ++ky) {
+      const size_t row = (size_t)iz[kz] * sz + (size_t)iy[ky] * sy;
+      const R wyz = wy[ky] * wz[kz], gyz = gy[ky] * wz[kz], wgz = wy[ky] * gz[kz];
+      for (int kx = 0; kx < K; ++kx) {
+        const V q = ldg4(F.v + row + ix[kx]);
+        const R f = wx[kx] * wyz;
+        const R comp[4] = {R(q.x), R(q.y), R(q.z), R(q.w)};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) val4[c] = fma(comp[c], f, val4[c]);
+        if (GRAD) {
+          const R fx = gx[kx] * wyz, fy = wx[kx] * gyz, fz = wx[kx] * wgz;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            d[c][0] = fma(comp[c], fx, d[c][0]);
+            d[c][1] = fma(comp[c], fy, d[c][1]);
+            d[c][2] = fma(comp[c], fz, d[c][2]);
+          }
+        }
+      }
+    }
+  }
+}
+
 // Interpolated b, grad b and |B| at a point. Storage type S (float/double),
 // arithmetic R. Global frame (LOC = false): (x0, x1, x2) in domain units.
 // Local frame (LOC = true, uniform grids): the point is vertex `ic` plus
 // (x0, x1, x2) in cell units, so the cell and its local coordinates come from
 // small exact numbers instead of a subtraction of nearly equal coordinates.
-template <class R, class S, bool GRAD, bool MAG, bool LOC = false>
+// HO = false compiles the trilinear path only (the cell-wise kernels, which
+// are trilinear by construction).
+template <class R, class S, bool GRAD, bool MAG, bool LOC = false, bool HO = true>
 __device__ __forceinline__ void interp(const FieldView<S>& F, R x0, R x1, R x2, Interp<R>& I,
                                        const int* ic = nullptr) {
   int ci[3];
@@ -147,13 +238,21 @@ __device__ __forceinline__ void interp(const FieldView<S>& F, R x0, R x1, R x2, 
       locate_axis<R, S>(F.axis[a], xs[a], F.n[a], ci[a], uu[a], sc[a]);
     }
   }
+  R val[3], d[3][3];
+  if (HO && F.order > 1) {
+    R v4[4];
+    ho_sum<R, S, GRAD>(F, ci, uu, v4, d);
+    val[0] = v4[0];
+    val[1] = v4[1];
+    val[2] = v4[2];
+    if (MAG || F.raw) I.m = v4[3];
+  } else {
   typedef typename V4<S>::type V;
   const size_t sy = (size_t)F.n[0], sz = (size_t)F.n[0] * (size_t)F.n[1];
   const V* p = F.v + (size_t)ci[2] * sz + (size_t)ci[1] * sy + (size_t)ci[0];
   V q000 = ldg4(p), q100 = ldg4(p + 1), q010 = ldg4(p + sy), q110 = ldg4(p + sy + 1);
   V q001 = ldg4(p + sz), q101 = ldg4(p + sz + 1), q011 = ldg4(p + sz + sy), q111 = ldg4(p + sz + sy + 1);
   R u = uu[0], v = uu[1], w = uu[2];
-  R val[3], d[3][3];
 #define QSL_TRI(C, K)                                                                                    \
   if (GRAD) {                                                                                            \
     tri1<R>(R(q000.C), R(q100.C), R(q010.C), R(q110.C), R(q001.C), R(q101.C), R(q011.C), R(q111.C), u, v, \
@@ -169,6 +268,7 @@ __device__ __forceinline__ void interp(const FieldView<S>& F, R x0, R x1, R x2, 
   if (MAG || F.raw) {
     I.m = tri0<R>(R(q000.w), R(q100.w), R(q010.w), R(q110.w), R(q001.w), R(q101.w), R(q011.w), R(q111.w), u,
                   v, w);
+  }
   }
   if (GRAD) {
 #pragma unroll
@@ -205,10 +305,10 @@ __device__ __forceinline__ void interp(const FieldView<S>& F, R x0, R x1, R x2, 
   }
 }
 
-template <class R, class S, int NC, bool LOC>
+template <class R, class S, int NC, bool LOC, bool HO = false>
 __device__ __forceinline__ void rhs(const FieldView<S>& F, const R* y, R* k, const int* ic) {
   Interp<R> I;
-  interp<R, S, NC == 9, false, LOC>(F, y[0], y[1], y[2], I, ic);
+  interp<R, S, NC == 9, false, LOC, HO>(F, y[0], y[1], y[2], I, ic);
   if (LOC) {
     k[0] = I.b[0] * R(F.inv_h[0]);
     k[1] = I.b[1] * R(F.inv_h[1]);
@@ -229,27 +329,27 @@ __device__ __forceinline__ void rhs(const FieldView<S>& F, const R* y, R* k, con
 
 // One Cash-Karp step of signed size hh from y: the 5th-order increment dy
 // (y_new = y + dy) and the embedded error estimate yerr.
-template <class R, class S, int NC, bool LOC>
+template <class R, class S, int NC, bool LOC, bool HO = false>
 __device__ __forceinline__ void ck_step(const FieldView<S>& F, const R* y, R hh, R* dy, R* yerr, const int* ic) {
   R k1[NC], k2[NC], k3[NC], k4[NC], k5[NC], k6[NC], t[NC];
-  rhs<R, S, NC, LOC>(F, y, k1, ic);
+  rhs<R, S, NC, LOC, HO>(F, y, k1, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(A21) * k1[i], y[i]);
-  rhs<R, S, NC, LOC>(F, t, k2, ic);
+  rhs<R, S, NC, LOC, HO>(F, t, k2, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(A31) * k1[i] + R(A32) * k2[i], y[i]);
-  rhs<R, S, NC, LOC>(F, t, k3, ic);
+  rhs<R, S, NC, LOC, HO>(F, t, k3, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(A41) * k1[i] + R(A42) * k2[i] + R(A43) * k3[i], y[i]);
-  rhs<R, S, NC, LOC>(F, t, k4, ic);
+  rhs<R, S, NC, LOC, HO>(F, t, k4, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i)
     t[i] = fma(hh, R(A51) * k1[i] + R(A52) * k2[i] + R(A53) * k3[i] + R(A54) * k4[i], y[i]);
-  rhs<R, S, NC, LOC>(F, t, k5, ic);
+  rhs<R, S, NC, LOC, HO>(F, t, k5, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i)
     t[i] = fma(hh, R(A61) * k1[i] + R(A62) * k2[i] + R(A63) * k3[i] + R(A64) * k4[i] + R(A65) * k5[i], y[i]);
-  rhs<R, S, NC, LOC>(F, t, k6, ic);
+  rhs<R, S, NC, LOC, HO>(F, t, k6, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i) {
     dy[i] = hh * (R(B1) * k1[i] + R(B3) * k3[i] + R(B4) * k4[i] + R(B6) * k6[i]);
@@ -257,11 +357,11 @@ __device__ __forceinline__ void ck_step(const FieldView<S>& F, const R* y, R hh,
   }
 }
 
-template <class R, class S, int NC, bool LOC>
+template <class R, class S, int NC, bool LOC, bool HO = false>
 __device__ __forceinline__ void euler_step(const FieldView<S>& F, const R* y, R hh, R* dy, R* yerr,
                                            const int* ic) {
   R k[NC];
-  rhs<R, S, NC, LOC>(F, y, k, ic);
+  rhs<R, S, NC, LOC, HO>(F, y, k, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i) {
     dy[i] = hh * k[i];
@@ -448,7 +548,10 @@ __device__ __forceinline__ void write_end(const TraceParams<R>& P, const Item<R>
   e.steps = steps;
 }
 
-template <class R, int NC, bool LOC>
+// HO: higher-order interpolation (Sec. "Interpolation schemes"; uniform grids,
+// local frame); a separate instantiation so the trilinear one keeps its
+// registers.
+template <class R, int NC, bool LOC, bool HO = false>
 __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ TraceParams<R> P) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -535,7 +638,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
               status = QSL_LINE_OUTSIDE;
             } else {
               Interp<R> I0;
-              interp<R, R, false, false, LOC>(E->F, y[0], y[1], y[2], I0, ic);
+              interp<R, R, false, false, LOC, HO>(E->F, y[0], y[1], y[2], I0, ic);
               R m0 = sqrt(I0.b[0] * I0.b[0] + I0.b[1] * I0.b[1] + I0.b[2] * I0.b[2]);
               if (!(m0 > R(0))) {
                 status = QSL_LINE_NULL;
@@ -615,10 +718,10 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
     if (status == ST_RUNNING) {
       R dy[NC], yerr[NC];
       if (P.euler) {
-        euler_step<R, R, NC, LOC>(E->F, y, sgn * hs, dy, yerr, ic);
+        euler_step<R, R, NC, LOC, HO>(E->F, y, sgn * hs, dy, yerr, ic);
         c_stage += 1;
       } else {
-        ck_step<R, R, NC, LOC>(E->F, y, sgn * hs, dy, yerr, ic);
+        ck_step<R, R, NC, LOC, HO>(E->F, y, sgn * hs, dy, yerr, ic);
         c_stage += 6;
       }
       steps += 1;
@@ -958,7 +1061,7 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
               status = QSL_LINE_OUTSIDE;
             } else {
               Interp<R> I0;
-              interp<R, R, false, false, true>(E->F, y[0], y[1], y[2], I0, ic);
+              interp<R, R, false, false, true, false>(E->F, y[0], y[1], y[2], I0, ic);
               R m0 = sqrt(I0.b[0] * I0.b[0] + I0.b[1] * I0.b[1] + I0.b[2] * I0.b[2]);
               if (!(m0 > R(0))) {
                 status = QSL_LINE_NULL;
@@ -1448,7 +1551,7 @@ __global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ 
               status = QSL_LINE_OUTSIDE;
             } else {
               Interp<R> I0;
-              interp<R, R, false, false, true>(E->F, yf[0], yf[1], yf[2], I0, ic);
+              interp<R, R, false, false, true, false>(E->F, yf[0], yf[1], yf[2], I0, ic);
               R m0 = sqrt(I0.b[0] * I0.b[0] + I0.b[1] * I0.b[1] + I0.b[2] * I0.b[2]);
               if (!(m0 > R(0))) {
                 status = QSL_LINE_NULL;
@@ -1917,6 +2020,7 @@ FieldView<float> make_view<float>(const qsl_field* f) {
   }
   v.uniform = f->uniform;
   v.raw = f->mode == QSL_RAW_B;
+  v.order = 1;
   return v;
 }
 template <>
@@ -1931,6 +2035,7 @@ FieldView<double> make_view<double>(const qsl_field* f) {
   }
   v.uniform = f->uniform;
   v.raw = f->mode == QSL_RAW_B;
+  v.order = 1;
   return v;
 }
 
@@ -1940,6 +2045,7 @@ template <class R>
 Item<R> make_item(const qsl_field* f, const SeedSource& src, const TraceConfig& cfg, int64_t seed_start, bool loc) {
   Item<R> it;
   it.F = make_view<R>(f);
+  it.F.order = cfg.interp_order;
   it.src = src;
   it.seed_start = seed_start;
   for (int a = 0; a < 3; ++a) {
@@ -2023,6 +2129,9 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_coop_kernel<R, NC>, threads, 0));
   else if (use_cell)
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_kernel<R, NC>, threads, smem));
+  else if (loc && cfg.interp_order > 1)
+    QSL_CHECK_CUDA(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, trace_kernel<R, NC, true, true>, threads, 0));
   else if (loc)
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, trace_kernel<R, NC, true>, threads, 0));
   else
@@ -2043,6 +2152,9 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
       qsl::count_launch();
     } else if (use_cell) {
       cell_kernel<R, NC><<<blocks, threads, smem, stream>>>(P);
+      qsl::count_launch();
+    } else if (loc && cfg.interp_order > 1) {
+      trace_kernel<R, NC, true, true><<<blocks, threads, 0, stream>>>(P);
       qsl::count_launch();
     } else if (loc) {
       trace_kernel<R, NC, true><<<blocks, threads, 0, stream>>>(P);

@@ -39,7 +39,7 @@ class qsl_opts(C.Structure):
                 ("max_length", C.c_double), ("max_steps", C.c_int64), ("euler_h", C.c_double),
                 ("retrace_q", C.c_double), ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
                 ("land_tol", C.c_double), ("timeout_s", C.c_double), ("line_lanes", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("interp_order", C.c_int32)]
 
 
 QSL_LINE_DTYPE = np.dtype([("q_perp", "<f8"), ("q_foot", "<f8"), ("q_det", "<f8"), ("b0", "<f8"), ("bf", "<f8"),
