@@ -311,7 +311,7 @@ def run_reference(args, rank, world):
     seeds = oracle.plane_seeds([0, 0, 0], [2, 0, 0], [0, 2, 0], args.coarse, args.coarse)
     cores = os.cpu_count() or 1
     o = oracle.default_opts(tol_abs=TOL, tol_rel=TOL, nthreads=cores)
-    per_step = 24 * cores
+    per_step = 256 * cores  # 4 of the oracle's 64-seed work chunks per thread
     for w in range(args.warmup):
         oracle.trace_seeds(F, seeds[inputs.subsample(len(seeds), per_step, 1000 + w)], o)
     t = 0.0
