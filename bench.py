@@ -43,6 +43,12 @@ FIELD_SEED = 2
 # value + gradient (99), scaling (12), deviation right-hand sides (30), the
 # stage's share of the combinations (414 per step) and error norm (144 per
 # step) over 6.5 evaluations per step (85).
+# DRAM bytes per launch of the two tracer phases of the default workload
+# (4-charge field on 256^3, 1024^2 map refined to 4096^2): dram__bytes_read.sum
+# + dram__bytes_write.sum from one ncu capture of the current kernels (the
+# coarse pass; the mean over the 27 refinement passes)
+TRAFFIC_COARSE_BYTES = 561.2e6
+TRAFFIC_PASS_BYTES = 29.28e6
 FLOP_PER_STAGE = {"ck": 246.0, "cell": 227.0}
 # FP32 peak of the FMA pipe: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -736,8 +742,10 @@ def main():
     flop_per_stage = FLOP_PER_STAGE[RUN["integrator"]]
     achieved_tflops = st["stage_evals"] * flop_per_stage / (kms / 1000.0) / 1e12
     kname = "cell_kernel<float,9>" if RUN["integrator"] == "cell" else "trace_kernel<float,9>"
+    default_workload = args.grid == 256 and args.coarse == 1024 and RUN["integrator"] == "cell"
     roof_coarse = {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                   "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                   "frac": achieved_tflops / FP32_PEAK_TFLOPS,
+                   "traffic": TRAFFIC_COARSE_BYTES if default_workload else None,
                    "kernel": kname + " (%d^2 coarse map, one launch)" % args.coarse, "kernel_ms": kms,
                    "stage_evals": st["stage_evals"], "accepted": st["accepted"], "rejected": st["rejected"],
                    "landings": st["landing"], "flop_per_stage": flop_per_stage,
@@ -748,7 +756,8 @@ def main():
     pass_tflops = (rs["pass_stage_evals"] * flop_per_stage / (rs["passes_ms"] / 1000.0) / 1e12
                    if rs["passes_ms"] > 0 else 0.0)
     roof_passes = {"bound": "alu", "achieved": pass_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                   "frac": pass_tflops / FP32_PEAK_TFLOPS, "traffic": None,
+                   "frac": pass_tflops / FP32_PEAK_TFLOPS,
+                   "traffic": TRAFFIC_PASS_BYTES if default_workload else None,
                    "kernel": ("cell_coop_kernel<float,9>" if RUN["integrator"] == "cell" else kname)
                    + " (refinement passes, %d per step)" % rs["passes"], "kernel_ms": pass_ms,
                    "stage_evals": rs["pass_stage_evals"] // max(rs["passes"], 1), "flop_per_stage": flop_per_stage,
