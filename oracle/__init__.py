@@ -91,7 +91,7 @@ def default_opts(**kw):
 class Field:
     """Packed FP64 field on a rectilinear grid; b arrays are [nz, ny, nx] (x fastest)."""
 
-    def __init__(self, bx, by, bz, xc, yc, zc, mode=0, order=1):
+    def __init__(self, bx, by, bz, xc, yc, zc, mode=0, order=1, geometry=0):
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (bx, by, bz, xc, yc, zc)]
         bx, by, bz, xc, yc, zc = self._keep
         nz, ny, nx = bx.shape
@@ -105,6 +105,9 @@ class Field:
         if order != 1 and lib().qslref_set_interp_order(self.handle, int(order)) != 0:
             raise ValueError("interpolation order %r needs 1..3 and, above 1, a uniform grid" % (order,))
         self.order = order
+        if geometry != 0 and lib().qslref_set_geometry(self.handle, int(geometry)) != 0:
+            raise ValueError("spherical geometry needs latitudes inside (-pi/2, pi/2) and radii > 0")
+        self.geometry = geometry
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:

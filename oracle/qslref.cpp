@@ -56,7 +56,23 @@ struct Field {
   double glo[3], ghi[3];
   double cell;               // smallest grid spacing over all axes
   int order = 1;             // interpolation: 1 trilinear, 2 triquadratic, 3 tricubic (uniform grids)
+  int geom = 0;              // 0 Cartesian; 1 spherical: axes (phi, theta, r) = longitude, latitude
+                             // (radians) and radius, field components in (phi^, theta^, r^)
+  double cell_q = 0;         // smallest coordinate spacing (landing tolerance)
 };
+
+// Scale factors of the coordinates at point q: a coordinate displacement dq_i
+// is a physical length m_i dq_i. Cartesian: 1; spherical (Sec. "Integrating
+// field lines", Eq. fl_sph): (r cos(theta), r, 1).
+inline void metric(const Field& F, const double* q, double* m) {
+  if (F.geom == 1) {
+    m[0] = q[2] * std::cos(q[1]);
+    m[1] = q[2];
+    m[2] = 1.0;
+  } else {
+    m[0] = m[1] = m[2] = 1.0;
+  }
+}
 
 struct Stats {
   double stage_evals = 0, accepted = 0, rejected = 0, landing = 0;
@@ -254,15 +270,20 @@ void interp(const Field& F, const double* x, Interp* out, Stats* st) {
 // Right-hand side: y = (x, dx1, dx2); dy/dl = s * (b(x), G dx1, G dx2)
 // (Eq. fl and Eq. dev; s = +1 forward to lambda_F, -1 backward to lambda_B).
 // ---------------------------------------------------------------------------
+// Spherical geometry: Eq. fl_sph for the position, and Eq. dev_sph (the
+// paper's form, which leaves out the terms of the metric factors' variation)
+// for the coordinate deviations: m_i d(dq_i)/dl = sum_j (d b_i / d q_j) dq_j.
 void rhs(const Field& F, int s, int ncomp, const double* y, double* dy, Stats* st) {
   Interp I;
   interp(F, y, &I, st);
-  for (int i = 0; i < 3; ++i) dy[i] = s * I.b[i];
+  double m[3];
+  metric(F, y, m);
+  for (int i = 0; i < 3; ++i) dy[i] = s * I.b[i] / m[i];
   if (ncomp == 9) {
     for (int v = 0; v < 2; ++v) {
       const double* d = y + 3 + 3 * v;
       for (int i = 0; i < 3; ++i)
-        dy[3 + 3 * v + i] = s * (I.g[i][0] * d[0] + I.g[i][1] * d[1] + I.g[i][2] * d[2]);
+        dy[3 + 3 * v + i] = s * (I.g[i][0] * d[0] + I.g[i][1] * d[1] + I.g[i][2] * d[2]) / m[i];
     }
   }
 }
@@ -345,7 +366,7 @@ struct End {
 // instead and the search repeats on the shorter step.
 void land(const Field& F, const Opts& o, const double* lo, const double* hi, int s, int ncomp,
           const double* y, double h_full, const double* y_full, End* e, Stats* st) {
-  double tol = o.land_tol * F.cell;
+  double tol = o.land_tol * (F.geom == 1 ? F.cell_q : F.cell);
   double hi_h = h_full;
   double yhi[9], ym[9], yerr[9];
   std::memcpy(yhi, y_full, sizeof(double) * ncomp);
@@ -491,10 +512,24 @@ End trace_dir(const Field& F, const Opts& o, const double* lo, const double* hi,
     e.steps += 1;
     double err = 0;
     bool finite = true;
-    for (int i = 0; i < ncomp; ++i) {
-      if (!std::isfinite(ynew[i])) finite = false;
-      double sc = o.tol_abs + o.tol_rel * std::max(std::fabs(e.y[i]), std::fabs(ynew[i]));
-      err = std::max(err, std::fabs(yerr[i]) / sc);
+    if (F.geom == 1) {
+      // spherical: errors and magnitudes as physical lengths (positions scaled
+      // by the radius, the distance from the centre)
+      double m[3];
+      metric(F, e.y, m);
+      double rr = std::max(std::fabs(e.y[2]), std::fabs(ynew[2]));
+      for (int i = 0; i < ncomp; ++i) {
+        if (!std::isfinite(ynew[i])) finite = false;
+        double mi = m[i % 3];
+        double mag = i < 3 ? rr : std::max(std::fabs(e.y[i]), std::fabs(ynew[i])) * mi;
+        err = std::max(err, std::fabs(yerr[i]) * mi / (o.tol_abs + o.tol_rel * mag));
+      }
+    } else {
+      for (int i = 0; i < ncomp; ++i) {
+        if (!std::isfinite(ynew[i])) finite = false;
+        double sc = o.tol_abs + o.tol_rel * std::max(std::fabs(e.y[i]), std::fabs(ynew[i]));
+        err = std::max(err, std::fabs(yerr[i]) / sc);
+      }
     }
     if (!finite) {
       e.status = ST_NONFINITE;
@@ -548,8 +583,12 @@ void resolve_domain(const Field& F, const Opts& o, double* lo, double* hi, doubl
     lo[a] = use ? o.lo[a] : F.glo[a];
     hi[a] = use ? o.hi[a] : F.ghi[a];
   }
-  double d = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
-                       (hi[2] - lo[2]) * (hi[2] - lo[2]));
+  double e[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+  if (F.geom == 1) {  // physical extents at the outer radius
+    e[0] *= hi[2];
+    e[1] *= hi[2];
+  }
+  double d = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
   *max_len = (o.max_length > 0) ? o.max_length : 20.0 * d;
 }
 
@@ -575,8 +614,13 @@ EndQ end_terms(const Field& F, const End& e, bool have_face) {
   double m = std::sqrt(dot3(I.b, I.b));
   double u[3] = {I.b[0] / m, I.b[1] / m, I.b[2] / m};
   double ap[3], bp[3];
-  const double* d1 = e.y + 3;
-  const double* d2 = e.y + 6;
+  // deviations as physical vectors in the end's orthonormal frame
+  double sf[3], d1[3], d2[3];
+  metric(F, e.y, sf);
+  for (int i = 0; i < 3; ++i) {
+    d1[i] = e.y[3 + i] * sf[i];
+    d2[i] = e.y[6 + i] * sf[i];
+  }
   double ud1 = dot3(u, d1), ud2 = dot3(u, d2);
   for (int i = 0; i < 3; ++i) {
     ap[i] = d1[i] - u[i] * ud1;
@@ -652,9 +696,11 @@ LineOut trace_line(const Field& F, const Opts& o, const double* x0, Stats* st) {
     double an = std::sqrt(dot3(av, av));
     for (int i = 0; i < 3; ++i) av[i] /= an;
     cross3(u0, av, bv);
+    double m[3];
+    metric(F, x0, m);  // physical vectors to coordinate deviations
     for (int i = 0; i < 3; ++i) {
-      y0[3 + i] = av[i];
-      y0[6 + i] = bv[i];
+      y0[3 + i] = av[i] / m[i];
+      y0[6 + i] = bv[i] / m[i];
     }
   }
   End ef = trace_dir(F, o, lo, hi, max_len, +1, ncomp, y0, st);
@@ -897,6 +943,35 @@ int qslref_set_interp_order(void* field, int order) {
     }
   }
   F->order = order;
+  return 0;
+}
+
+// Geometry of a loaded field: 0 Cartesian, 1 spherical (axes: longitude and
+// latitude in radians, radius > 0; latitudes inside (-pi/2, pi/2)). Step sizes
+// are physical lengths: the smallest cell edge becomes the smallest of
+// r_min cos(theta) h_phi (over the grid's latitudes), r_min h_theta and h_r.
+// Returns 0, or -1 for a bad geometry or a grid outside those ranges.
+int qslref_set_geometry(void* field, int geom) {
+  Field* F = (Field*)field;
+  if (geom != 0 && geom != 1) return -1;
+  double cq = std::numeric_limits<double>::infinity();
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i + 1 < F->n[a]; ++i) cq = std::min(cq, F->c[a][i + 1] - F->c[a][i]);
+  F->cell_q = cq;
+  if (geom == 1) {
+    double th_lo = F->c[1][0], th_hi = F->c[1][F->n[1] - 1], r_lo = F->c[2][0];
+    const double half_pi = 1.5707963267948966;
+    if (!(th_lo > -half_pi && th_hi < half_pi && r_lo > 0)) return -1;
+    double cmin = std::min(std::cos(th_lo), std::cos(th_hi));
+    double c = std::numeric_limits<double>::infinity();
+    for (int i = 0; i + 1 < F->n[0]; ++i) c = std::min(c, r_lo * cmin * (F->c[0][i + 1] - F->c[0][i]));
+    for (int i = 0; i + 1 < F->n[1]; ++i) c = std::min(c, r_lo * (F->c[1][i + 1] - F->c[1][i]));
+    for (int i = 0; i + 1 < F->n[2]; ++i) c = std::min(c, F->c[2][i + 1] - F->c[2][i]);
+    F->cell = c;
+  } else {
+    F->cell = cq;
+  }
+  F->geom = geom;
   return 0;
 }
 
