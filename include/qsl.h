@@ -403,6 +403,24 @@ int qsl_convert(const uint64_t* keys, const float* vals, int64_t n, int ndim, in
 /* Kernels of this library launched by this process since the library was
  * loaded (all threads). Radix sorts and scans inside qsl_refine run CUB
  * kernels, which are not counted. */
+/* Geometry of a loaded field (Sec. "Integrating field lines"):
+ * QSL_GEOM_CARTESIAN (default) or QSL_GEOM_SPHERICAL. Spherical: the grid's
+ * axes are longitude phi and latitude theta (radians, latitudes inside
+ * (-pi/2, pi/2)) and radius r > 0, uniform on each axis; the three field
+ * arrays are B_phi, B_theta, B_r in the local orthonormal basis. Field lines
+ * follow Eq. fl_sph and the deviations Eq. dev_sph (the paper's form, without
+ * the terms of the metric factors' variation); seeds and end points are
+ * (phi, theta, r); planar seeds (qsl_q_map_2d) are planes in these
+ * coordinates, so (0, 0, r0) + u = (dphi, 0, 0), v = (0, dtheta, 0) is the
+ * spherical slice at radius r0. Eq. ic's vectors are orthonormal in the
+ * seed's physical frame; Q uses the deviations as physical vectors in each
+ * end's frame; step bounds are in units of the smallest physical cell edge
+ * at the lowest radius; the step error is measured on physical lengths.
+ * Runs with QSL_RKCK54 or QSL_EULER (any interpolation order). */
+#define QSL_GEOM_CARTESIAN 0
+#define QSL_GEOM_SPHERICAL 1
+int qsl_set_geometry(qsl_field* field, int geometry);
+
 /* Device memory: the library's temporary buffers (tracer scratch, refinement
  * work arrays, sort storage) come from its own stream-ordered pool on each
  * device, which keeps freed blocks cached for the next call (no return to the

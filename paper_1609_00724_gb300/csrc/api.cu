@@ -74,17 +74,23 @@ void resolve_config(const qsl_field* f, const qsl_opts* o, TraceConfig* c) {
     c->lo[a] = use ? o->domain_lo[a] : f->glo[a];
     c->hi[a] = use ? o->domain_hi[a] : f->ghi[a];
   }
-  double d2 = 0;
-  for (int a = 0; a < 3; ++a) d2 += (c->hi[a] - c->lo[a]) * (c->hi[a] - c->lo[a]);
+  double ext[3];
+  for (int a = 0; a < 3; ++a) ext[a] = c->hi[a] - c->lo[a];
+  if (f->geom == QSL_GEOM_SPHERICAL) {  // physical extents at the outer radius
+    ext[0] *= c->hi[2];
+    ext[1] *= c->hi[2];
+  }
+  double d2 = ext[0] * ext[0] + ext[1] * ext[1] + ext[2] * ext[2];
   c->max_len = o->max_length > 0 ? o->max_length : 20.0 * std::sqrt(d2);
   c->cell = f->cell;
+  c->geom = f->geom;
   c->tol_abs = o->tol_abs;
   c->tol_rel = o->tol_rel;
   c->h_init = o->h_init;
   c->h_max = o->h_max;
   c->h_min = o->h_min;
   c->euler_h = o->euler_h;
-  c->land_tol = o->land_tol * f->cell;
+  c->land_tol = o->land_tol * (f->geom == QSL_GEOM_SPHERICAL ? f->cell_q : f->cell);
   c->max_steps = o->max_steps;
   c->integrator = o->integrator;
   c->length_only = o->length_only;
@@ -113,6 +119,8 @@ int validate_opts(const qsl_field* f, const qsl_opts* o) {
     QSL_FAIL(QSL_EINVAL, "triquadratic and tricubic interpolation need a uniform grid");
   if (o->interp_order > 1 && o->integrator == QSL_DOPRI5_CELL)
     QSL_FAIL(QSL_EINVAL, "the cell-wise integrator is trilinear only; use QSL_RKCK54 or QSL_EULER");
+  if (f->geom == QSL_GEOM_SPHERICAL && o->integrator == QSL_DOPRI5_CELL)
+    QSL_FAIL(QSL_EINVAL, "spherical geometry runs with QSL_RKCK54 or QSL_EULER");
   return QSL_OK;
 }
 
@@ -525,6 +533,28 @@ int qsl_q_volume_3d(const qsl_field* f, const double lo[3], const double hi[3], 
     src.u[k] = hi[k];
   }
   return map_common(f, src, (int64_t)nx * ny * nz, o, q, length, faces, status, mem, (cudaStream_t)stream);
+}
+
+int qsl_set_geometry(qsl_field* f, int geometry) {
+  if (!f) QSL_FAIL(QSL_EINVAL, "field is NULL");
+  double hmin = fmin(fmin(f->h[0], f->h[1]), f->h[2]);
+  if (geometry == QSL_GEOM_CARTESIAN) {
+    f->geom = QSL_GEOM_CARTESIAN;
+    if (f->uniform) f->cell = hmin;  // (a spherical field had a physical cell edge here)
+    f->cell_q = f->cell;
+    return QSL_OK;
+  }
+  if (geometry != QSL_GEOM_SPHERICAL) QSL_FAIL(QSL_EINVAL, "bad geometry %d", geometry);
+  if (!f->uniform) QSL_FAIL(QSL_EINVAL, "spherical geometry needs a uniform (phi, theta, r) grid");
+  const double half_pi = 1.5707963267948966;
+  if (!(f->glo[1] > -half_pi && f->ghi[1] < half_pi && f->glo[2] > 0))
+    QSL_FAIL(QSL_EINVAL, "spherical grid needs latitudes inside (-pi/2, pi/2) and radii > 0");
+  // step sizes are physical lengths: the smallest cell edge at the lowest radius
+  double cmin = fmin(cos(f->glo[1]), cos(f->ghi[1]));
+  f->cell = fmin(fmin(f->glo[2] * cmin * f->h[0], f->glo[2] * f->h[1]), f->h[2]);
+  f->cell_q = hmin;
+  f->geom = QSL_GEOM_SPHERICAL;
+  return QSL_OK;
 }
 
 int qsl_trim_pool(void) {

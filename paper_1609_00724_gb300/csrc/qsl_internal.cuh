@@ -50,7 +50,17 @@ struct FieldView {
   int uniform;        // 1: all axes uniform (fast cell location)
   int raw;            // 1: QSL_RAW_B packing, 0: paper packing
   int order;          // interpolation: 1 trilinear, 2 triquadratic, 3 tricubic (uniform grids)
+  int geom;           // 0 Cartesian; 1 spherical: axes (phi, theta, r), components (phi^, theta^, r^)
 };
+
+// Scale factors of the coordinates (a displacement dq_i is the physical
+// length m_i dq_i): Cartesian 1; spherical (r cos(theta), r, 1), Eq. fl_sph.
+template <class R>
+__host__ __device__ __forceinline__ void sph_scale(R theta, R r, R* m) {
+  m[0] = r * cos(theta);
+  m[1] = r;
+  m[2] = R(1);
+}
 
 }  // namespace qsl
 
@@ -66,6 +76,8 @@ struct qsl_field {
   double* axis64[3];           // device axis coordinates
   float* axis32[3];
   int device;
+  int geom;                    // QSL_GEOM_CARTESIAN or QSL_GEOM_SPHERICAL
+  double cell_q;               // smallest coordinate spacing (landing tolerance)
 };
 
 namespace qsl {
@@ -112,6 +124,7 @@ struct TraceConfig {
   int length_only;
   unsigned long long timeout_ns;  // device watchdog per warp (%globaltimer), 0 = none
   int interp_order;  // 1, 2 or 3
+  int geom;          // QSL_GEOM_CARTESIAN or QSL_GEOM_SPHERICAL
 };
 
 // Stream-ordered allocation from the library's own memory pool on the current

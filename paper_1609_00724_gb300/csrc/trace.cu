@@ -305,13 +305,31 @@ __device__ __forceinline__ void interp(const FieldView<S>& F, R x0, R x1, R x2, 
   }
 }
 
-template <class R, class S, int NC, bool LOC, bool HO = false>
+// Spherical coordinates of the local-frame point vertex ic + y (cell units).
+template <class R, class S>
+__device__ __forceinline__ void sph_point(const FieldView<S>& F, const R* y, const int* ic, R* theta, R* r) {
+  *theta = R(F.org[1]) + (R(ic[1]) + y[1]) / R(F.inv_h[1]);
+  *r = R(F.org[2]) + (R(ic[2]) + y[2]) / R(F.inv_h[2]);
+}
+
+// SPH: spherical geometry (local frame): Eq. fl_sph for the position and
+// Eq. dev_sph for the coordinate deviations, m_i d(dq_i)/dl = sum_j
+// (d b_i / d q_j) dq_j with m = (r cos(theta), r, 1).
+template <class R, class S, int NC, bool LOC, bool HO = false, bool SPH = false>
 __device__ __forceinline__ void rhs(const FieldView<S>& F, const R* y, R* k, const int* ic) {
   Interp<R> I;
   interp<R, S, NC == 9, false, LOC, HO>(F, y[0], y[1], y[2], I, ic);
+  R im[3] = {R(1), R(1), R(1)};
+  if (SPH) {
+    R th, rr, m[3];
+    sph_point<R, S>(F, y, ic, &th, &rr);
+    sph_scale<R>(th, rr, m);
+    im[0] = R(1) / m[0];
+    im[1] = R(1) / m[1];
+  }
   if (LOC) {
-    k[0] = I.b[0] * R(F.inv_h[0]);
-    k[1] = I.b[1] * R(F.inv_h[1]);
+    k[0] = I.b[0] * im[0] * R(F.inv_h[0]);
+    k[1] = I.b[1] * im[1] * R(F.inv_h[1]);
     k[2] = I.b[2] * R(F.inv_h[2]);
   } else {
     k[0] = I.b[0];
@@ -323,33 +341,34 @@ __device__ __forceinline__ void rhs(const FieldView<S>& F, const R* y, R* k, con
     for (int v = 0; v < 2; ++v)
 #pragma unroll
       for (int i = 0; i < 3; ++i)
-        k[3 + 3 * v + i] = I.g[i][0] * y[3 + 3 * v] + I.g[i][1] * y[4 + 3 * v] + I.g[i][2] * y[5 + 3 * v];
+        k[3 + 3 * v + i] =
+            (I.g[i][0] * y[3 + 3 * v] + I.g[i][1] * y[4 + 3 * v] + I.g[i][2] * y[5 + 3 * v]) * im[i];
   }
 }
 
 // One Cash-Karp step of signed size hh from y: the 5th-order increment dy
 // (y_new = y + dy) and the embedded error estimate yerr.
-template <class R, class S, int NC, bool LOC, bool HO = false>
+template <class R, class S, int NC, bool LOC, bool HO = false, bool SPH = false>
 __device__ __forceinline__ void ck_step(const FieldView<S>& F, const R* y, R hh, R* dy, R* yerr, const int* ic) {
   R k1[NC], k2[NC], k3[NC], k4[NC], k5[NC], k6[NC], t[NC];
-  rhs<R, S, NC, LOC, HO>(F, y, k1, ic);
+  rhs<R, S, NC, LOC, HO, SPH>(F, y, k1, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(A21) * k1[i], y[i]);
-  rhs<R, S, NC, LOC, HO>(F, t, k2, ic);
+  rhs<R, S, NC, LOC, HO, SPH>(F, t, k2, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(A31) * k1[i] + R(A32) * k2[i], y[i]);
-  rhs<R, S, NC, LOC, HO>(F, t, k3, ic);
+  rhs<R, S, NC, LOC, HO, SPH>(F, t, k3, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(A41) * k1[i] + R(A42) * k2[i] + R(A43) * k3[i], y[i]);
-  rhs<R, S, NC, LOC, HO>(F, t, k4, ic);
+  rhs<R, S, NC, LOC, HO, SPH>(F, t, k4, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i)
     t[i] = fma(hh, R(A51) * k1[i] + R(A52) * k2[i] + R(A53) * k3[i] + R(A54) * k4[i], y[i]);
-  rhs<R, S, NC, LOC, HO>(F, t, k5, ic);
+  rhs<R, S, NC, LOC, HO, SPH>(F, t, k5, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i)
     t[i] = fma(hh, R(A61) * k1[i] + R(A62) * k2[i] + R(A63) * k3[i] + R(A64) * k4[i] + R(A65) * k5[i], y[i]);
-  rhs<R, S, NC, LOC, HO>(F, t, k6, ic);
+  rhs<R, S, NC, LOC, HO, SPH>(F, t, k6, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i) {
     dy[i] = hh * (R(B1) * k1[i] + R(B3) * k3[i] + R(B4) * k4[i] + R(B6) * k6[i]);
@@ -357,11 +376,11 @@ __device__ __forceinline__ void ck_step(const FieldView<S>& F, const R* y, R hh,
   }
 }
 
-template <class R, class S, int NC, bool LOC, bool HO = false>
+template <class R, class S, int NC, bool LOC, bool HO = false, bool SPH = false>
 __device__ __forceinline__ void euler_step(const FieldView<S>& F, const R* y, R hh, R* dy, R* yerr,
                                            const int* ic) {
   R k[NC];
-  rhs<R, S, NC, LOC, HO>(F, y, k, ic);
+  rhs<R, S, NC, LOC, HO, SPH>(F, y, k, ic);
 #pragma unroll
   for (int i = 0; i < NC; ++i) {
     dy[i] = hh * k[i];
@@ -551,7 +570,7 @@ __device__ __forceinline__ void write_end(const TraceParams<R>& P, const Item<R>
 // HO: higher-order interpolation (Sec. "Interpolation schemes"; uniform grids,
 // local frame); a separate instantiation so the trilinear one keeps its
 // registers.
-template <class R, int NC, bool LOC, bool HO = false>
+template <class R, int NC, bool LOC, bool HO = false, bool SPH = false>
 __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ TraceParams<R> P) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -665,6 +684,17 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
                   y[6] = u0[1] * av[2] - u0[2] * av[1];
                   y[7] = u0[2] * av[0] - u0[0] * av[2];
                   y[8] = u0[0] * av[1] - u0[1] * av[0];
+                  if (SPH) {
+                    // physical vectors of the seed's frame to coordinate deviations
+                    R th, rr, m[3];
+                    sph_point<R, R>(E->F, y, ic, &th, &rr);
+                    sph_scale<R>(th, rr, m);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                      y[3 + i] /= m[i];
+                      y[6 + i] /= m[i];
+                    }
+                  }
                 }
                 // a seed on a face whose field points out of the domain ends
                 // this side at once with zero length
@@ -718,22 +748,41 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
     if (status == ST_RUNNING) {
       R dy[NC], yerr[NC];
       if (P.euler) {
-        euler_step<R, R, NC, LOC, HO>(E->F, y, sgn * hs, dy, yerr, ic);
+        euler_step<R, R, NC, LOC, HO, SPH>(E->F, y, sgn * hs, dy, yerr, ic);
         c_stage += 1;
       } else {
-        ck_step<R, R, NC, LOC, HO>(E->F, y, sgn * hs, dy, yerr, ic);
+        ck_step<R, R, NC, LOC, HO, SPH>(E->F, y, sgn * hs, dy, yerr, ic);
         c_stage += 6;
       }
       steps += 1;
       if (phase == 0) {
         R err = 0;
         bool finite = true;
+        R sm[3] = {R(1), R(1), R(1)}, srr = R(0);
+        if (SPH) {
+          // spherical: errors and magnitudes as physical lengths, positions
+          // against the radius (the distance from the centre)
+          R th, rr;
+          sph_point<R, R>(E->F, y, ic, &th, &rr);
+          sph_scale<R>(th, rr, sm);
+          srr = fmax(fabs(rr), fabs(rr + dy[2] / R(E->F.inv_h[2])));
+        }
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
           R yn = y[i] + dy[i];
           if (!isfinite(yn)) finite = false;
           R e = fabs(yerr[i]), ya = fabs(y[i]), yb = fabs(yn);
-          if (LOC && i < 3) {
+          if (SPH) {
+            const R mi = sm[i % 3];
+            if (i < 3) {
+              e *= mi / R(E->F.inv_h[i]);
+              ya = yb = srr;
+            } else {
+              e *= mi;
+              ya *= mi;
+              yb *= mi;
+            }
+          } else if (LOC && i < 3) {
             // position error in domain units, scaled by |x| in domain units
             R hh = R(1) / R(E->F.inv_h[i]);
             R base = R(E->F.org[i]) + R(ic[i]) * hh;
@@ -1856,8 +1905,14 @@ struct EndTerms {
 };
 
 template <class S>
-__device__ void end_terms(const FieldView<S>& F, const double* x, const double* d1, const double* d2, int face,
-                          bool have_face, EndTerms& r) {
+__device__ void end_terms(const FieldView<S>& F, const double* x, const double* d1_in, const double* d2_in,
+                          int face, bool have_face, EndTerms& r) {
+  // deviations as physical vectors in the end's orthonormal frame (spherical
+  // coordinates: (r cos(theta) dphi, r dtheta, dr))
+  double sf[3] = {1.0, 1.0, 1.0};
+  if (F.geom == QSL_GEOM_SPHERICAL) sph_scale<double>(x[1], x[2], sf);
+  const double d1[3] = {d1_in[0] * sf[0], d1_in[1] * sf[1], d1_in[2] * sf[2]};
+  const double d2[3] = {d2_in[0] * sf[0], d2_in[1] * sf[1], d2_in[2] * sf[2]};
   Interp<double> I;
   interp<double, S, false, true>(F, x[0], x[1], x[2], I);
   r.bmag = I.m;
@@ -2021,6 +2076,7 @@ FieldView<float> make_view<float>(const qsl_field* f) {
   v.uniform = f->uniform;
   v.raw = f->mode == QSL_RAW_B;
   v.order = 1;
+  v.geom = f->geom;
   return v;
 }
 template <>
@@ -2036,6 +2092,7 @@ FieldView<double> make_view<double>(const qsl_field* f) {
   v.uniform = f->uniform;
   v.raw = f->mode == QSL_RAW_B;
   v.order = 1;
+  v.geom = f->geom;
   return v;
 }
 
@@ -2129,6 +2186,12 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_coop_kernel<R, NC>, threads, 0));
   else if (use_cell)
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_kernel<R, NC>, threads, smem));
+  else if (loc && cfg.geom == QSL_GEOM_SPHERICAL && cfg.interp_order > 1)
+    QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, trace_kernel<R, NC, true, true, true>,
+                                                                 threads, 0));
+  else if (loc && cfg.geom == QSL_GEOM_SPHERICAL)
+    QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, trace_kernel<R, NC, true, false, true>,
+                                                                 threads, 0));
   else if (loc && cfg.interp_order > 1)
     QSL_CHECK_CUDA(
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, trace_kernel<R, NC, true, true>, threads, 0));
@@ -2152,6 +2215,12 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
       qsl::count_launch();
     } else if (use_cell) {
       cell_kernel<R, NC><<<blocks, threads, smem, stream>>>(P);
+      qsl::count_launch();
+    } else if (loc && cfg.geom == QSL_GEOM_SPHERICAL && cfg.interp_order > 1) {
+      trace_kernel<R, NC, true, true, true><<<blocks, threads, 0, stream>>>(P);
+      qsl::count_launch();
+    } else if (loc && cfg.geom == QSL_GEOM_SPHERICAL) {
+      trace_kernel<R, NC, true, false, true><<<blocks, threads, 0, stream>>>(P);
       qsl::count_launch();
     } else if (loc && cfg.interp_order > 1) {
       trace_kernel<R, NC, true, true><<<blocks, threads, 0, stream>>>(P);

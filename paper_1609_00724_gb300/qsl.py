@@ -431,6 +431,16 @@ def qsl_last_stats():
     return {k: getattr(s, k) for k, _ in s._fields_ if k != "pad"}
 
 
+QSL_GEOM_CARTESIAN = 0
+QSL_GEOM_SPHERICAL = 1
+
+
+def qsl_set_geometry(field, geometry):
+    """Sets the field's geometry (QSL_GEOM_CARTESIAN or QSL_GEOM_SPHERICAL)."""
+    _check(lib().qsl_set_geometry(field.handle, int(geometry)))
+    return field
+
+
 def qsl_trim_pool():
     """Returns the library pool's cached device memory to the driver."""
     _check(lib().qsl_trim_pool())
@@ -448,4 +458,4 @@ EXPORTS = ["qsl_opts_default", "qsl_load_field", "qsl_free_field", "qsl_trace_se
            "qsl_last_error", "qsl_last_stats", "qsl_trace_seeds_noalloc", "qsl_kernel_launches", "qsl_q_map_batch",
            "qsl_plan_q_map_batch", "qsl_plan_launch", "qsl_plan_stats", "qsl_plan_free", "qsl_autotune",
            "qsl_cnn_create", "qsl_cnn_params", "qsl_cnn_forward", "qsl_cnn_loss_grad", "qsl_cnn_adam_step",
-           "qsl_cnn_free", "qsl_cnn_nparams", "qsl_last_refine_stats", "qsl_trim_pool"]
+           "qsl_cnn_free", "qsl_cnn_nparams", "qsl_last_refine_stats", "qsl_trim_pool", "qsl_set_geometry"]
