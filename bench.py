@@ -741,7 +741,7 @@ def main():
     kms = st["kernel_ms"]
     flop_per_stage = FLOP_PER_STAGE[RUN["integrator"]]
     achieved_tflops = st["stage_evals"] * flop_per_stage / (kms / 1000.0) / 1e12
-    kname = "cell_kernel<float,9>" if RUN["integrator"] == "cell" else "trace_kernel<float,9>"
+    kname = "cell_kernel_f32<9>" if RUN["integrator"] == "cell" else "trace_kernel<float,9>"
     default_workload = args.grid == 256 and args.coarse == 1024 and RUN["integrator"] == "cell"
     roof_coarse = {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                    "frac": achieved_tflops / FP32_PEAK_TFLOPS,

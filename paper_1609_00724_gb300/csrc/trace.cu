@@ -1024,7 +1024,7 @@ __device__ __forceinline__ void cell_rhs(const R* __restrict__ cs, int st, bool 
 }
 
 template <class R, int NC>
-__global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ TraceParams<R> P) {
+__device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int st = blockDim.x;
   R* cs = reinterpret_cast<R*>(smem_raw) + threadIdx.x;
@@ -1431,6 +1431,26 @@ __global__ void __launch_bounds__(256) cell_kernel(const __grid_constant__ Trace
     if (any_to) atomicAdd(&P.stats->timeouts, 1ull);
   }
   if (lane == 0 && any_to && P.timeout_flag) atomicExch(P.timeout_flag, 1);
+}
+
+// The cell-wise kernel. FP32: at most 168 registers, so three blocks of 128
+// threads stay resident per SM (the allocation granularity would make 170 a
+// two-block kernel); FP64 keeps the compiler's choice (a cap would spill).
+template <int NC>
+__global__ void __maxnreg__(168) cell_kernel_f32(const __grid_constant__ TraceParams<float> P) {
+  cell_trace<float, NC>(P);
+}
+template <int NC>
+__global__ void __launch_bounds__(256) cell_kernel_f64(const __grid_constant__ TraceParams<double> P) {
+  cell_trace<double, NC>(P);
+}
+template <int NC>
+inline void (*cell_kernel_fn(float*))(const TraceParams<float>) {
+  return cell_kernel_f32<NC>;
+}
+template <int NC>
+inline void (*cell_kernel_fn(double*))(const TraceParams<double>) {
+  return cell_kernel_f64<NC>;
 }
 
 // ------------------------------------------------------------ cooperative cell-wise tracer
@@ -2185,7 +2205,8 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
   if (coop)
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_coop_kernel<R, NC>, threads, 0));
   else if (use_cell)
-    QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_kernel<R, NC>, threads, smem));
+    QSL_CHECK_CUDA(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_kernel_fn<NC>((R*)nullptr), threads, smem));
   else if (loc && cfg.geom == QSL_GEOM_SPHERICAL && cfg.interp_order > 1)
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, trace_kernel<R, NC, true, true, true>,
                                                                  threads, 0));
@@ -2214,7 +2235,7 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
       cell_coop_kernel<R, NC><<<blocks, threads, 0, stream>>>(P);
       qsl::count_launch();
     } else if (use_cell) {
-      cell_kernel<R, NC><<<blocks, threads, smem, stream>>>(P);
+      cell_kernel_fn<NC>((R*)nullptr)<<<blocks, threads, smem, stream>>>(P);
       qsl::count_launch();
     } else if (loc && cfg.geom == QSL_GEOM_SPHERICAL && cfg.interp_order > 1) {
       trace_kernel<R, NC, true, true, true><<<blocks, threads, 0, stream>>>(P);
