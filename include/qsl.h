@@ -251,15 +251,20 @@ typedef struct qsl_samples {
  * Samples sit at effective-cell centres; positions as in qsl_q_map_2d /
  * qsl_q_volume_3d over the effective lattice. With samples->count > 0 the
  * call resumes from those (sorted) samples instead of the coarse pass.
- * QSL_ECAPACITY when the capacity is reached (samples so far are valid). */
+ * QSL_ECAPACITY when the capacity is reached (samples so far are valid).
+ * With the FLL-jump criterion the refinement passes trace lengths only (the
+ * criterion reads L) and the pass samples' Q, L, end faces and status come
+ * from one tangent-space trace after the last iteration. */
 int qsl_refine(const qsl_field* field, const qsl_refine_spec* spec, const qsl_opts* opts, qsl_samples* samples,
                float* q_grid, float* l_grid, int mem, void* stream);
 
 /* Time accounting of the last qsl_refine on this thread (no paper counterpart;
  * CUDA events on the call's stream). total_ms spans the whole call on the
  * device; coarse_ms the tracing of the coarse pass (and of a proposal);
- * passes_ms the tracing of the refinement passes (FP32 trace, FP64 assembly
- * and FP64 retrace of each pass); the rest is sorting, merging, flagging,
+ * passes_ms the tracing of the refinement passes (with the FLL-jump criterion:
+ * length-only traces of each pass, and one trace of all pass samples with the
+ * deviation equations, FP64 assembly and FP64 retrace, after the last
+ * iteration; passes counts both); the rest is sorting, merging, flagging,
  * conversion and host round trips. Synchronises that stream. QSL_EINVAL
  * before the first qsl_refine. */
 typedef struct qsl_refine_stats {

@@ -297,6 +297,23 @@ __global__ void merge_order_kernel(const uint64_t* __restrict__ skey, const floa
   }
 }
 
+// Outputs of samples traced in a separate batch (keys bkey[j], all present
+// in the sorted set `key`) written to their places in the set.
+__global__ void scatter_by_key_kernel(const uint64_t* __restrict__ bkey, int64_t m, const uint64_t* __restrict__ key,
+                                      int64_t n, const float* __restrict__ q, const float* __restrict__ L,
+                                      const uint8_t* __restrict__ fa, const uint8_t* __restrict__ st, float* oq,
+                                      float* oL, uint8_t* ofa, uint8_t* ost) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = count_below(key, n, bkey[j]);
+    if (p >= n || key[p] != bkey[j]) continue;  // not in the set (cannot happen)
+    oq[p] = q[j];
+    oL[p] = L[j];
+    ofa[2 * p] = fa[2 * j];
+    ofa[2 * p + 1] = fa[2 * j + 1];
+    ost[p] = st[j];
+  }
+}
+
 __global__ void gather_f_kernel(const int64_t* __restrict__ perm, int64_t n, const float* __restrict__ in,
                                 float* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -657,6 +674,18 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
   }
   if ((rc = sc.alloc(&nperm, cap)) || (rc = sc.alloc(&nkey, cap))) return rc;
 
+  // With the FLL-jump criterion the passes need lengths only: they trace in
+  // length-only mode, and one launch after the last iteration traces every
+  // pass sample with the deviation equations; its Q, L, end faces and status
+  // (FP64 retrace above retrace_q included) replace the pass values, whose
+  // lengths only decided the refinement.
+  const bool decouple = sp->criterion == QSL_REFINE_FLL_JUMP && !o->length_only;
+  qsl_opts o_len = *o;
+  o_len.length_only = 1;
+  uint64_t* pkeys = nullptr;
+  int64_t n_pass = 0;
+  if (decouple && (rc = sc.alloc(&pkeys, cap))) return rc;
+
   // trace samples [off, off + m) (keys already written; `sorted`: in key
   // order) and merge them into the sorted set and into the built orders
   auto trace_and_merge = [&](int64_t off, int64_t m, bool sorted) -> int {
@@ -674,9 +703,15 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
     int r = rk.take(&e0, &e1);
     if (r) return r;
     QSL_CHECK_CUDA(cudaEventRecord(e0, s));
-    r = run_lines(f, s2, m, o, lo, s);
+    const bool len_only = decouple && trace_kind == 1;
+    r = run_lines(f, s2, m, len_only ? &o_len : o, lo, s);
     if (r) return r;
     QSL_CHECK_CUDA(cudaEventRecord(e1, s));
+    if (len_only) {
+      QSL_CHECK_CUDA(
+          cudaMemcpyAsync(pkeys + n_pass, smp->key + off, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+      n_pass += m;
+    }
     if (rk.kind.size() < (size_t)RefineClock::kSnaps)
       QSL_CHECK_CUDA(cudaMemcpyAsync(rk.snap + rk.kind.size(), last_run_stats_dev(), sizeof(DeviceStats),
                                      cudaMemcpyDeviceToDevice, s));
@@ -859,6 +894,41 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
       added_total += added;
     }
     if (added_total == 0) break;
+  }
+  if (decouple && n_pass > 0) {
+    // Q of every pass sample (keys sorted first: neighbouring seeds on
+    // neighbouring lanes), then scattered to its place in the sorted set
+    float *q_s = nullptr, *L_s = nullptr;
+    uint8_t *fa_s = nullptr, *st_s = nullptr;
+    if ((rc = sc.alloc(&q_s, n_pass)) || (rc = sc.alloc(&L_s, n_pass)) || (rc = sc.alloc(&fa_s, 2 * n_pass)) ||
+        (rc = sc.alloc(&st_s, n_pass)))
+      return rc;
+    iota_kernel<<<grid_for(n_pass), 256, 0, s>>>(perm, n_pass);
+    qsl::count_launch();
+    if ((rc = sort_pairs(pkeys, nkey, perm, nperm, n_pass, nd * p, s))) return rc;
+    SeedSource s3 = src;
+    s3.keys = nkey;
+    LineOutputs lo{};
+    lo.q = q_s;
+    lo.length = L_s;
+    lo.faces = fa_s;
+    lo.status = st_s;
+    lo.q_form = o->q_form;
+    lo.skip_open = o->skip_open;
+    cudaEvent_t e0, e1;
+    if ((rc = rk.take(&e0, &e1))) return rc;
+    QSL_CHECK_CUDA(cudaEventRecord(e0, s));
+    if ((rc = run_lines(f, s3, n_pass, o, lo, s))) return rc;
+    QSL_CHECK_CUDA(cudaEventRecord(e1, s));
+    if (rk.kind.size() < (size_t)RefineClock::kSnaps)
+      QSL_CHECK_CUDA(cudaMemcpyAsync(rk.snap + rk.kind.size(), last_run_stats_dev(), sizeof(DeviceStats),
+                                     cudaMemcpyDeviceToDevice, s));
+    rk.kind.push_back(1);
+    rk.lines.push_back(0);  // time and work count with the passes; the seeds were counted there
+    scatter_by_key_kernel<<<grid_for(n_pass), 256, 0, s>>>(nkey, n_pass, smp->key, n, q_s, L_s, fa_s, st_s,
+                                                            smp->q, smp->length, smp->faces, smp->status);
+    qsl::count_launch();
+    QSL_CHECK_CUDA(cudaGetLastError());
   }
   smp->count = n;
   smp->iters = it;
