@@ -47,9 +47,13 @@ FIELD_SEED = 2
 # (4-charge field on 256^3, 1024^2 map refined to 4096^2): dram__bytes_read.sum
 # + dram__bytes_write.sum from one ncu capture of the current kernels (the
 # coarse pass; the mean over the 27 refinement passes)
-TRAFFIC_COARSE_BYTES = 561.2e6
-TRAFFIC_PASS_BYTES = 29.28e6
+TRAFFIC_COARSE_BYTES = 564.2e6
+TRAFFIC_PASS_BYTES = 29.17e6
 FLOP_PER_STAGE = {"ck": 246.0, "cell": 227.0}
+# length-only stage evaluation of the cell-wise kernels (trilinear values of 3
+# components 63, position scaling 3, the 3-component share of the stage
+# combinations and error norm 29)
+FLOP_PER_STAGE_LEN = 95.0
 # FP32 peak of the FMA pipe: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -751,23 +755,27 @@ def main():
                    "landings": st["landing"], "flop_per_stage": flop_per_stage,
                    "peak_note": "FP32 FMA pipe at 2.07 GHz (derived from unit counts)"}
     # refinement passes: few lines per launch, each launch as long as its
-    # longest line (latency-bound); average over the step's passes
+    # longest line (latency-bound); average over the step's passes, which
+    # trace lengths only with the FLL-jump criterion
     pass_ms = rs["passes_ms"] / max(rs["passes"], 1)
-    pass_tflops = (rs["pass_stage_evals"] * flop_per_stage / (rs["passes_ms"] / 1000.0) / 1e12
+    len_only = rs["deferred_ms"] > 0
+    pass_flop = FLOP_PER_STAGE_LEN if (len_only and RUN["integrator"] == "cell") else flop_per_stage
+    pass_tflops = (rs["pass_stage_evals"] * pass_flop / (rs["passes_ms"] / 1000.0) / 1e12
                    if rs["passes_ms"] > 0 else 0.0)
     roof_passes = {"bound": "alu", "achieved": pass_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                    "frac": pass_tflops / FP32_PEAK_TFLOPS,
                    "traffic": TRAFFIC_PASS_BYTES if default_workload else None,
-                   "kernel": ("cell_coop_kernel<float,9>" if RUN["integrator"] == "cell" else kname)
-                   + " (refinement passes, %d per step)" % rs["passes"], "kernel_ms": pass_ms,
-                   "stage_evals": rs["pass_stage_evals"] // max(rs["passes"], 1), "flop_per_stage": flop_per_stage,
+                   "kernel": (("cell_coop_kernel<float,%d>" % (3 if len_only else 9)) if RUN["integrator"] == "cell"
+                              else kname) + " (%srefinement passes, %d per step)"
+                   % ("length-only " if len_only else "", rs["passes"]), "kernel_ms": pass_ms,
+                   "stage_evals": rs["pass_stage_evals"] // max(rs["passes"], 1), "flop_per_stage": pass_flop,
                    "peak_note": "FP32 FMA pipe at 2.07 GHz (derived from unit counts); launches are bound by "
                                 "the latency of their longest line, not by the pipe"}
     passes_dominate = rs["passes_ms"] > rs["coarse_ms"]
     step_breakdown = {"device_ms": rs["total_ms"], "coarse_trace_ms": rs["coarse_ms"],
-                      "pass_trace_ms": rs["passes_ms"], "passes": rs["passes"], "iters": rs["iters"],
-                      "pass_lines": rs["pass_lines"],
-                      "other_ms": rs["total_ms"] - rs["coarse_ms"] - rs["passes_ms"]}
+                      "pass_trace_ms": rs["passes_ms"], "deferred_trace_ms": rs["deferred_ms"],
+                      "passes": rs["passes"], "iters": rs["iters"], "pass_lines": rs["pass_lines"],
+                      "other_ms": rs["total_ms"] - rs["coarse_ms"] - rs["passes_ms"] - rs["deferred_ms"]}
 
     # --- end to end through the C ABI with host buffers (pinned), copies inside
     eff = args.coarse << (P - P0)

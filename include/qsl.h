@@ -261,19 +261,19 @@ int qsl_refine(const qsl_field* field, const qsl_refine_spec* spec, const qsl_op
 /* Time accounting of the last qsl_refine on this thread (no paper counterpart;
  * CUDA events on the call's stream). total_ms spans the whole call on the
  * device; coarse_ms the tracing of the coarse pass (and of a proposal);
- * passes_ms the tracing of the refinement passes (with the FLL-jump criterion:
- * length-only traces of each pass, and one trace of all pass samples with the
- * deviation equations, FP64 assembly and FP64 retrace, after the last
- * iteration; passes counts both); the rest is sorting, merging, flagging,
+ * passes_ms the tracing of the refinement passes (length-only with the
+ * FLL-jump criterion); deferred_ms the one trace of all pass samples with the
+ * deviation equations (FP64 assembly and retrace included) that follows the
+ * last iteration with that criterion; the rest is sorting, merging, flagging,
  * conversion and host round trips. Synchronises that stream. QSL_EINVAL
  * before the first qsl_refine. */
 typedef struct qsl_refine_stats {
-  double total_ms, coarse_ms, passes_ms;
+  double total_ms, coarse_ms, passes_ms, deferred_ms;
   int64_t coarse_lines, pass_lines; /* seeds traced                                      */
-  int64_t coarse_stage_evals, pass_stage_evals; /* FP32 tracer stage evaluations (the
-                                       first 512 trace calls of the refine)              */
-  int32_t passes, iters;            /* refinement trace calls, iterations                */
-} qsl_refine_stats; /* 64 bytes */
+  int64_t coarse_stage_evals, pass_stage_evals, deferred_stage_evals; /* FP32 tracer
+                                       stage evaluations (the first 512 trace calls)     */
+  int32_t passes, iters;            /* refinement pass trace calls, iterations           */
+} qsl_refine_stats; /* 80 bytes */
 int qsl_last_refine_stats(qsl_refine_stats* out);
 
 /* ---- batches of fields and cuts: one persistent launch, captured plans ---------

@@ -923,8 +923,8 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
     if (rk.kind.size() < (size_t)RefineClock::kSnaps)
       QSL_CHECK_CUDA(cudaMemcpyAsync(rk.snap + rk.kind.size(), last_run_stats_dev(), sizeof(DeviceStats),
                                      cudaMemcpyDeviceToDevice, s));
-    rk.kind.push_back(1);
-    rk.lines.push_back(0);  // time and work count with the passes; the seeds were counted there
+    rk.kind.push_back(2);
+    rk.lines.push_back(n_pass);
     scatter_by_key_kernel<<<grid_for(n_pass), 256, 0, s>>>(nkey, n_pass, smp->key, n, q_s, L_s, fa_s, st_s,
                                                             smp->q, smp->length, smp->faces, smp->status);
     qsl::count_launch();
@@ -969,10 +969,12 @@ int qsl_last_refine_stats(qsl_refine_stats* out) {
     if (rk.kind[i] == 0) {
       out->coarse_ms += t;
       out->coarse_lines += rk.lines[i];
-    } else {
+    } else if (rk.kind[i] == 1) {
       out->passes_ms += t;
       out->pass_lines += rk.lines[i];
       out->passes += 1;
+    } else {
+      out->deferred_ms += t;
     }
   }
   size_t ns = rk.kind.size() < (size_t)RefineClock::kSnaps ? rk.kind.size() : (size_t)RefineClock::kSnaps;
@@ -980,7 +982,8 @@ int qsl_last_refine_stats(qsl_refine_stats* out) {
   if (ns) QSL_CHECK_CUDA(cudaMemcpy(h.data(), rk.snap, sizeof(DeviceStats) * ns, cudaMemcpyDeviceToHost));
   for (size_t i = 0; i < ns; ++i) {
     if (rk.kind[i] == 0) out->coarse_stage_evals += (int64_t)h[i].stage_evals;
-    else out->pass_stage_evals += (int64_t)h[i].stage_evals;
+    else if (rk.kind[i] == 1) out->pass_stage_evals += (int64_t)h[i].stage_evals;
+    else out->deferred_stage_evals += (int64_t)h[i].stage_evals;
   }
   out->iters = rk.iters;
   return QSL_OK;

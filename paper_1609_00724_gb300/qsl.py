@@ -59,8 +59,9 @@ class qsl_stats(C.Structure):
 
 class qsl_refine_stats(C.Structure):
     _fields_ = [("total_ms", C.c_double), ("coarse_ms", C.c_double), ("passes_ms", C.c_double),
-                ("coarse_lines", C.c_int64), ("pass_lines", C.c_int64), ("coarse_stage_evals", C.c_int64),
-                ("pass_stage_evals", C.c_int64), ("passes", C.c_int32), ("iters", C.c_int32)]
+                ("deferred_ms", C.c_double), ("coarse_lines", C.c_int64), ("pass_lines", C.c_int64),
+                ("coarse_stage_evals", C.c_int64), ("pass_stage_evals", C.c_int64),
+                ("deferred_stage_evals", C.c_int64), ("passes", C.c_int32), ("iters", C.c_int32)]
 
 
 class qsl_refine_spec(C.Structure):

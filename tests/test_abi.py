@@ -34,6 +34,6 @@ def test_opts_default_and_struct_sizes():
     o = qsl.qsl_opts_default()
     assert o.integrator == qsl.QSL_RKCK54 and o.tol_abs == 1e-2 and o.retrace_q == 1e6
     assert C.sizeof(qsl.qsl_opts) == 176
-    assert C.sizeof(qsl.qsl_refine_stats) == 64
+    assert C.sizeof(qsl.qsl_refine_stats) == 80
     assert qsl.QSL_LINE_DTYPE.itemsize == 112
     assert qsl.lib().qsl_last_error() == b""
