@@ -1778,7 +1778,7 @@ __global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ 
         c_acc += (c == 0);
         R hnext = hs * ((err == R(0)) ? R(5) : fmin(R(5), R(0.9) * cpow(err, R(-0.2))));
         // first crossing of this axis's planes within the step, on the dense
-        // output (same bracket and safeguarded Newton as cell_kernel, with the
+        // output (same bracket and safeguarded Newton as cell_trace, with the
         // root t = 0 divided out when the step starts on the plane)
         R thc = R(2);
         int upc = 0;

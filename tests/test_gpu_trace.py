@@ -38,7 +38,7 @@ def _rec_to_dict(rec):
 
 @pytest.mark.parametrize("mode,integ,lanes", [(0, 0, 0), (1, 0, 0), (0, 2, 1), (1, 2, 1), (0, 2, 3), (1, 2, 3)])
 def test_trace_seeds_charge_field(qsl, oracle_mod, mode, integ, lanes):
-    """lanes: 1 = one lane per line (cell_kernel), 3 = a group of three lanes
+    """lanes: 1 = one lane per line (cell_kernel_f32/_f64), 3 = a group of three lanes
     per line (cell_coop_kernel)."""
     tol = GPU_TOL
     ch = inputs.random_charges(4, 2)
