@@ -349,7 +349,11 @@ int qsl_cnn_nparams(void);
  *    meets the bounds;
  *  - the fastest launch shape (warps per block 2/4/8, blocks per SM at most
  *    2 or as many as fit, refill threshold 1/8) and step cap at that
- *    tolerance, timed with CUDA events on `stream`.
+ *    tolerance, timed with CUDA events on `stream` on the sample repeated
+ *    until one launch holds at least 16 x 384 line directions per SM (a
+ *    throughput measurement; the sample's own launch is often as long as its
+ *    longest line). The repeated sample and its records are allocated for
+ *    the call (S x 3 doubles and S records per copy).
  * Writes the choice into *opts (tol_abs = tol_rel, h_max, warps_per_block,
  * blocks_per_sm, refill_min) and into *report (optional). The result is cached
  * per (grid size, interpolation mode, integrator, q_form, length_only, input
@@ -359,12 +363,13 @@ typedef struct qsl_tune_report {
   double tol;            /* chosen tolerance                                  */
   double q_err, l_err;   /* worst relative errors at that tolerance           */
   double face_mismatch;  /* fraction of sample lines with different end faces */
-  double sample_ms;      /* time of the chosen shape on the sample            */
+  double sample_ms;      /* time of the chosen shape on the sample repeated
+                            shape_reps times (one launch)                      */
   int64_t sample_seeds;
   double h_max;          /* chosen step cap (units of the smallest spacing)   */
   int32_t passed;        /* 1: the chosen tolerance met the bounds; 0: none of
                             the candidates did and the tightest was taken      */
-  int32_t reserved;
+  int32_t shape_reps;    /* copies of the sample in each shape timing         */
 } qsl_tune_report;
 int qsl_autotune(const qsl_field* field, const double* seeds, int64_t S, qsl_opts* opts, qsl_tune_report* report,
                  void* stream);

@@ -4,7 +4,10 @@
 // blocks per SM, refill threshold of the work queue) and the step cap (the
 // requested one, or 4 smallest spacings when that also meets the bounds; the
 // cell-wise stepper otherwise often stops just short of a face on anisotropic
-// grids). Each candidate is timed with CUDA events on the caller's stream.
+// grids). Each candidate is timed with CUDA events on the caller's stream;
+// shapes on the sample repeated until one launch holds many waves of resident
+// lines, so that the timing measures throughput, not the latency of the
+// sample's longest line.
 // Results are cached per (grid size, interpolation mode, integrator, q_form,
 // length_only, requested tolerance decade).
 #include <cmath>
@@ -150,7 +153,32 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
     if (eq4 <= 2e-4 && el4 <= 2e-6 && fm4 <= 1e-3) hmaxes[n_hmax++] = 4.0;
   }
   // launch shape and step cap: fastest of the candidates at the chosen
-  // tolerance (best of 2)
+  // tolerance (best of 2), on the sample repeated to at least 16 waves of
+  // 12 resident warps per SM (copies far apart in the queue, so that a line
+  // and its copies do not run side by side)
+  int dev = 0, sms = 1;
+  QSL_CHECK_CUDA(cudaGetDevice(&dev));
+  QSL_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t want_dirs = (int64_t)16 * sms * 12 * 32;
+  const int64_t reps = (want_dirs + 2 * S - 1) / (2 * S);
+  const int64_t ST = reps * S;
+  DevLines dt;
+  double* tiled = nullptr;
+  struct DevFree {
+    double* p;
+    ~DevFree() {
+      if (p) cudaFree(p);
+    }
+  } tiled_free{nullptr};
+  if (reps > 1) {
+    QSL_CHECK_CUDA(cudaMalloc((void**)&tiled, sizeof(double) * 3 * ST));
+    tiled_free.p = tiled;
+    QSL_CHECK_CUDA(cudaMalloc((void**)&dt.p, sizeof(qsl_line) * ST));
+    for (int64_t k = 0; k < reps; ++k)
+      QSL_CHECK_CUDA(cudaMemcpyAsync(tiled + 3 * S * k, seeds, sizeof(double) * 3 * S, cudaMemcpyDeviceToDevice, s));
+  }
+  const double* shape_seeds = reps > 1 ? tiled : seeds;
+  qsl_line* shape_out = reps > 1 ? dt.p : d.p;
   const int wpb[] = {2, 4, 8};
   const int bps[] = {32, 2};
   const int refill[] = {1, 8};
@@ -168,8 +196,8 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
           c.blocks_per_sm = b;
           c.refill_min = rf;
           double t1 = 0, t2 = 0;
-          if ((rc = time_trace(f, seeds, S, &c, d.p, s, &t1))) return rc;
-          if ((rc = time_trace(f, seeds, S, &c, d.p, s, &t2))) return rc;
+          if ((rc = time_trace(f, shape_seeds, ST, &c, shape_out, s, &t1))) return rc;
+          if ((rc = time_trace(f, shape_seeds, ST, &c, shape_out, s, &t2))) return rc;
           double t = fmin(t1, t2);
           if (t < best) {
             best = t;
@@ -192,6 +220,7 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
   rep.sample_seeds = S;
   rep.h_max = bh;
   rep.passed = passed;
+  rep.shape_reps = (int32_t)reps;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = rep;

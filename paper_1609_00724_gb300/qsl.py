@@ -92,7 +92,7 @@ class qsl_tune_report(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_min", C.c_int32),
                 ("cached", C.c_int32), ("tol", C.c_double), ("q_err", C.c_double), ("l_err", C.c_double),
                 ("face_mismatch", C.c_double), ("sample_ms", C.c_double), ("sample_seeds", C.c_int64),
-                ("h_max", C.c_double), ("passed", C.c_int32), ("reserved", C.c_int32)]
+                ("h_max", C.c_double), ("passed", C.c_int32), ("shape_reps", C.c_int32)]
 
 
 _lib = None

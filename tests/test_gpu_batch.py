@@ -98,6 +98,10 @@ def test_autotune_picks_valid_shape_and_tolerance(qsl):
     assert rep["q_err"] <= 2e-4 and rep["l_err"] <= 2e-6 and rep["cached"] == 0
     assert o.tol_rel == rep["tol"] and o.warps_per_block == rep["warps_per_block"]
     assert rep["h_max"] in (2.0, 4.0) and o.h_max == rep["h_max"]
+    # shapes are timed on the sample repeated to at least 16 x 384 line
+    # directions per SM (throughput, not the latency of the longest line)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert rep["shape_reps"] >= 1 and 2 * 2000 * rep["shape_reps"] >= 16 * 384 * sms
     o2 = qsl.qsl_opts_default(integrator=qsl.QSL_DOPRI5_CELL)
     rep2 = qsl.qsl_autotune(items[1][0], seeds, o2)
     assert rep2["cached"] == 1 and o2.refill_min == rep["refill_min"] and o2.h_max == rep["h_max"]
