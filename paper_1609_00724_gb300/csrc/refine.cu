@@ -320,20 +320,6 @@ __global__ void gather_f_kernel(const int64_t* __restrict__ perm, int64_t n, con
     out[i] = in[perm[i]];
 }
 
-__global__ void gather_u64_kernel(const int64_t* __restrict__ perm, int64_t n, const uint64_t* __restrict__ in,
-                                  uint64_t* out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = in[perm[i]];
-}
-
-// 32-bit radix keys that sort lengths in decreasing order (the bit pattern of
-// a non-negative float grows with its value; a length that is not a number
-// sorts last, as 0).
-__global__ void length_desc_keys_kernel(const float* __restrict__ L, int64_t n, uint64_t* keys) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    keys[i] = (uint64_t)(~__float_as_uint(fmaxf(L[i], 0.0f)));
-}
-
 
 // Converter: one thread per output cell.
 __global__ void convert_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ vals, int64_t n, int nd,
@@ -697,9 +683,8 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
   qsl_opts o_len = *o;
   o_len.length_only = 1;
   uint64_t* pkeys = nullptr;
-  float* plen = nullptr;
   int64_t n_pass = 0;
-  if (decouple && ((rc = sc.alloc(&pkeys, cap)) || (rc = sc.alloc(&plen, cap)))) return rc;
+  if (decouple && (rc = sc.alloc(&pkeys, cap))) return rc;
 
   // trace samples [off, off + m) (keys already written; `sorted`: in key
   // order) and merge them into the sorted set and into the built orders
@@ -725,8 +710,6 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
     if (len_only) {
       QSL_CHECK_CUDA(
           cudaMemcpyAsync(pkeys + n_pass, smp->key + off, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-      QSL_CHECK_CUDA(
-          cudaMemcpyAsync(plen + n_pass, smp->length + off, m * sizeof(float), cudaMemcpyDeviceToDevice, s));
       n_pass += m;
     }
     if (rk.kind.size() < (size_t)RefineClock::kSnaps)
@@ -913,10 +896,8 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
     if (added_total == 0) break;
   }
   if (decouple && n_pass > 0) {
-    // Q of every pass sample, then scattered to its place in the sorted set.
-    // The launch takes the samples in order of decreasing pass length: it
-    // holds few lines per resident lane, so it lasts about as long as the
-    // latest-started long line, and the longest lines start first.
+    // Q of every pass sample (keys sorted first: neighbouring seeds on
+    // neighbouring lanes), then scattered to its place in the sorted set
     float *q_s = nullptr, *L_s = nullptr;
     uint8_t *fa_s = nullptr, *st_s = nullptr;
     if ((rc = sc.alloc(&q_s, n_pass)) || (rc = sc.alloc(&L_s, n_pass)) || (rc = sc.alloc(&fa_s, 2 * n_pass)) ||
@@ -924,13 +905,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
       return rc;
     iota_kernel<<<grid_for(n_pass), 256, 0, s>>>(perm, n_pass);
     qsl::count_launch();
-    length_desc_keys_kernel<<<grid_for(n_pass), 256, 0, s>>>(plen, n_pass, sk);
-    qsl::count_launch();
-    QSL_CHECK_CUDA(cudaGetLastError());
-    if ((rc = sort_pairs(sk, sk2, perm, nperm, n_pass, 32, s))) return rc;
-    gather_u64_kernel<<<grid_for(n_pass), 256, 0, s>>>(nperm, n_pass, pkeys, nkey);
-    qsl::count_launch();
-    QSL_CHECK_CUDA(cudaGetLastError());
+    if ((rc = sort_pairs(pkeys, nkey, perm, nperm, n_pass, nd * p, s))) return rc;
     SeedSource s3 = src;
     s3.keys = nkey;
     LineOutputs lo{};
