@@ -307,7 +307,7 @@ int qsl_plan_launch(qsl_plan* plan, void* stream);
 int qsl_plan_stats(qsl_plan* plan, void* stream, qsl_stats* out);
 void qsl_plan_free(qsl_plan* plan);
 
-/* ---- learned refinement proposal (spec addition; the paper has none) -------
+/* ---- learned refinement proposal (an addition to the method; the paper has none) 
  * A 3-layer CNN over coarse tiles with 2 channels (normalised FLEDGE, log10 Q)
  * giving, per coarse cell, the probability that FLL-jump refinement
  * (Sec. "Adaptive refinements") will sample inside it:

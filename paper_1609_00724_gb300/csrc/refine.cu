@@ -1134,7 +1134,7 @@ int qsl_refine(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o,
     return QSL_EINVAL;
   }
   if (mem == QSL_MEM_DEVICE) {
-    // faces/status are optional: give the driver scratch ones
+    // faces/status are optional: give the refinement loop scratch ones
     qsl_samples d = *smp;
     void* sf = nullptr;
     void* ss = nullptr;
