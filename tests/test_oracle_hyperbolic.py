@@ -165,3 +165,31 @@ def test_golden_fixture(oracle_mod, raw_field):
     assert np.allclose(r["q_foot"], g[:, 4], rtol=1e-8, atol=0)
     assert np.allclose(r["q_perp"], g[:, 5], rtol=1e-8, atol=0)
     assert np.allclose(r["L"], g[:, 6], rtol=1e-10, atol=0)
+
+
+def test_euler_is_first_order(oracle_mod, raw_field):
+    """Fixed-step Euler (Sec. "Integration methods"): against the closed forms,
+    the length, footpoint Q and perpendicular Q errors halve with the step
+    (first order), the exit faces are exact at every step, and Richardson
+    extrapolation of two steps, 2 X(h/2) - X(h), removes the first-order term
+    (error at least 20x smaller). A dropped or mis-signed term would leave an
+    O(1) error or another order."""
+    seeds = np.array([[0.02, 0.3, 0.0], [-0.03, -0.5, 0.0], [0.3, 0.2, 0.0], [-0.6, 0.7, 0.0],
+                      [0.1, -0.1, 0.0]])
+    cf = [closed_forms(x, y) for x, y, _ in seeds]
+    exact = {"q_foot": np.array([c[0] for c in cf]), "q_perp": np.array([c[1] for c in cf]),
+             "L": np.array([c[2] for c in cf])}
+    res = {}
+    for eh in (0.2, 0.1, 0.05):
+        r = oracle_mod.trace_seeds(raw_field, seeds, oracle_mod.default_opts(integrator=1, euler_h=eh))
+        assert np.all(r["st_f"] == oracle_mod.ST_OK) and np.all(r["st_b"] == oracle_mod.ST_OK)
+        assert list(r["face_f"]) == [c[3] for c in cf] and np.all(r["face_b"] == 4)
+        res[eh] = r
+    for key, ex in exact.items():
+        err = {eh: np.abs(res[eh][key] / ex - 1) for eh in res}
+        assert np.all(err[0.05] > 1e-7), key  # not exact: a genuine fixed-step method
+        for a, b in ((0.2, 0.1), (0.1, 0.05)):
+            ratio = err[a] / err[b]
+            assert np.all((ratio > 1.8) & (ratio < 2.2)), (key, ratio)
+        rich = np.abs((2 * res[0.05][key] - res[0.1][key]) / ex - 1)
+        assert np.all(rich <= err[0.05] / 20), (key, rich / err[0.05])
