@@ -187,6 +187,47 @@ def test_refine_sample_set_matches_oracle(qsl, oracle_mod, ndim):
     assert np.array_equal(lg.cpu().numpy()[flat], b["L"].cpu().numpy()[:n])
 
 
+def test_refine_proposal_traces_every_cell_of_flagged_coarse_cells(qsl, oracle_mod):
+    """Proposal step (one byte per coarse cell, x fastest) with no refinement
+    iteration after it: the sample set is the coarse samples plus every
+    effective cell of the flagged coarse cells, key for key (keys from the
+    oracle's Hilbert curve), and the lines traced there match the oracle."""
+    from gpu_helpers import compare_lines
+    F, Fo = _fields(qsl, oracle_mod, n=40, seed=3)
+    p0, p = 4, 6
+    R, nc = 1 << (p - p0), 1 << p0
+    mask = (np.random.default_rng(11).random(nc * nc) < 0.15).astype(np.uint8)
+    mask[0] = mask[nc * nc - 1] = 1  # both ends of the coarse lattice
+    kw = dict(ndim=2, coarse_order=p0, max_order=p, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), tau=0.05,
+              max_iters=0)
+    mask_dev = torch.as_tensor(mask).cuda()
+    sp = qsl.refine_spec(proposal=mask_dev, **kw)
+    cap = (nc * R) ** 2
+    b = _alloc(cap)
+    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL)
+    n, iters, traced, rc = qsl.qsl_refine(F, sp, o, b["key"], b["q"], b["L"], b["faces"], b["st"])
+    assert rc == qsl.QSL_OK and iters == 0 and traced == n
+    keys = b["key"].cpu().numpy()[:n].view(np.uint64)
+    want = set()
+    for j in range(nc):
+        for i in range(nc):
+            if mask[i + nc * j]:
+                for bb in range(R):
+                    for aa in range(R):
+                        want.add(oracle_mod.hilbert_key((i * R + aa, j * R + bb), 2, p))
+            else:
+                want.add(oracle_mod.hilbert_key((i * R + R // 2, j * R + R // 2), 2, p))
+    assert n == len(want) and list(keys) == sorted(want)
+    # the lines: a seeded sample of the samples against the oracle
+    idx = np.sort(np.random.default_rng(12).choice(n, 80, replace=False))
+    pos = _positions(qsl, keys[idx], sp)
+    ref = oracle_mod.trace_seeds(Fo, pos, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
+    fc = b["faces"].cpu().numpy()[:2 * n].reshape(-1, 2)[idx]
+    gd = {"q_perp": b["q"].cpu().numpy()[:n][idx], "L": b["L"].cpu().numpy()[:n][idx], "face_f": fc[:, 0],
+          "face_b": fc[:, 1]}
+    compare_lines(gd, ref, Fo.cell, (-1, -1, 0), (1, 1, 1))
+
+
 def test_refine_resume_capacity_and_host_path(qsl, oracle_mod):
     F, _ = _fields(qsl, oracle_mod, n=40, seed=5)
     kw = dict(ndim=2, coarse_order=4, max_order=7, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), tau=0.05)
