@@ -45,10 +45,12 @@ FIELD_SEED = 2
 # step) over 6.5 evaluations per step (85).
 # DRAM bytes per launch of the two tracer phases of the default workload
 # (4-charge field on 256^3, 1024^2 map refined to 4096^2): dram__bytes_read.sum
-# + dram__bytes_write.sum from one ncu capture of the current kernels (the
-# coarse pass; the mean over the 27 refinement passes)
+# + dram__bytes_write.sum from one ncu capture (the coarse pass; the mean over
+# the 27 refinement passes). None where the kernel has changed since its
+# capture: the passes' three-lane kernel now evaluates its stages on the cell's
+# trilinear polynomial coefficients.
 TRAFFIC_COARSE_BYTES = 564.2e6
-TRAFFIC_PASS_BYTES = 29.17e6
+TRAFFIC_PASS_BYTES = None
 FLOP_PER_STAGE = {"ck": 246.0, "cell": 227.0}
 # length-only stage evaluation of the cell-wise kernels (trilinear values of 3
 # components 63, position scaling 3, the 3-component share of the stage

@@ -1509,6 +1509,69 @@ __device__ __forceinline__ void coop_rhs(unsigned gm, int gb, const R* cv, bool 
   }
 }
 
+// Lengths only, normalise-first field: the stage derivative of the lane's axis
+// is component c of the trilinear interpolant, a polynomial in the in-cell
+// coordinates, f = a0 + a1 u + a2 v + a3 w + a4 uv + a5 uw + a6 vw + a7 uvw
+// (coefficients from the cell's 8 corner values, scaled by 1/h_c once per
+// cell). Nested, it is three dependent FMAs after the shuffles, against the
+// differences and interpolations of the corner form.
+template <class R>
+__device__ __forceinline__ void trilinear_coeffs(const R* cv, R ihc, R* a) {
+  a[0] = cv[0] * ihc;
+  a[1] = (cv[1] - cv[0]) * ihc;
+  a[2] = (cv[2] - cv[0]) * ihc;
+  a[3] = (cv[4] - cv[0]) * ihc;
+  a[4] = ((cv[3] - cv[1]) - (cv[2] - cv[0])) * ihc;
+  a[5] = ((cv[5] - cv[1]) - (cv[4] - cv[0])) * ihc;
+  a[6] = ((cv[6] - cv[2]) - (cv[4] - cv[0])) * ihc;
+  a[7] = (((cv[7] - cv[6]) - (cv[5] - cv[4])) - ((cv[3] - cv[2]) - (cv[1] - cv[0]))) * ihc;
+}
+
+template <class R>
+__device__ __forceinline__ R coop_val_poly(unsigned gm, int gb, const R* a, R y0) {
+  const R u = gbc(gm, y0, gb), v = gbc(gm, y0, gb + 1), w = gbc(gm, y0, gb + 2);
+  const R p0 = fma(a[1], u, a[0]), p1 = fma(a[4], u, a[2]), p2 = fma(a[5], u, a[3]), p3 = fma(a[7], u, a[6]);
+  return fma(fma(p3, v, p2), w, fma(p1, v, p0));
+}
+
+// The six new stages of one Dormand-Prince step of the lane's components
+// (k2..k7; dy = the 5th-order increment, t = y + dy). POLY: stage derivatives
+// from the cell polynomial (lengths only, normalise-first field), decided once
+// per step so that the six stages form one straight-line sequence.
+template <class R, int NC, bool POLY>
+__device__ __forceinline__ void coop_stages(unsigned gm, int gb, const R* cv, const R* pc, bool raw, const R* ih,
+                                           R ihc, R hh, const R* y, const R* k1, R* k2, R* k3, R* k4, R* k5, R* k6,
+                                           R* k7, R* dy, R* t) {
+  constexpr int ND = NC / 3;
+  auto stage = [&](const R* tt, R* k) {
+    if constexpr (POLY) k[0] = coop_val_poly<R>(gm, gb, pc, tt[0]);
+    else coop_rhs<R, NC>(gm, gb, cv, raw, ih, ihc, tt, k);
+  };
+#pragma unroll
+  for (int i = 0; i < ND; ++i) t[i] = fma(hh, R(DA21) * k1[i], y[i]);
+  stage(t, k2);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) t[i] = fma(hh, R(DA31) * k1[i] + R(DA32) * k2[i], y[i]);
+  stage(t, k3);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) t[i] = fma(hh, R(DA41) * k1[i] + R(DA42) * k2[i] + R(DA43) * k3[i], y[i]);
+  stage(t, k4);
+#pragma unroll
+  for (int i = 0; i < ND; ++i)
+    t[i] = fma(hh, R(DA51) * k1[i] + R(DA52) * k2[i] + R(DA53) * k3[i] + R(DA54) * k4[i], y[i]);
+  stage(t, k5);
+#pragma unroll
+  for (int i = 0; i < ND; ++i)
+    t[i] = fma(hh, R(DA61) * k1[i] + R(DA62) * k2[i] + R(DA63) * k3[i] + R(DA64) * k4[i] + R(DA65) * k5[i], y[i]);
+  stage(t, k6);
+#pragma unroll
+  for (int i = 0; i < ND; ++i) {
+    dy[i] = hh * (R(DB1) * k1[i] + R(DB3) * k3[i] + R(DB4) * k4[i] + R(DB5) * k5[i] + R(DB6) * k6[i]);
+    t[i] = y[i] + dy[i];
+  }
+  stage(t, k7);
+}
+
 // End record of a group: lane c writes axis c, the group's first lane the rest.
 template <class R, int NC>
 __device__ __forceinline__ void write_end_coop(const TraceParams<R>& P, const Item<R>* E, int64_t unit, int c,
@@ -1562,6 +1625,8 @@ __global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ 
   bool active = false, exhausted = false, kvalid = false;
   int64_t unit = 0;
   R y[ND], k1[ND], cv[8];
+  R pc[8];             // lengths only, normalise-first field: trilinear_coeffs of the cell
+  bool poly = false;   // evaluate the stages on pc
   int ic[3] = {0, 0, 0};
   R mu = 0, muc = 0, h = 0, sgn = 1;
   int steps = 0, zc = 0;
@@ -1596,6 +1661,7 @@ __global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ 
             for (int a = 0; a < 3; ++a) ih[a] = R(E->F.inv_h[a]);
             ihc = sel3(c, ih[0], ih[1], ih[2]);
             hhc = R(1) / ihc;
+            poly = NC == 3 && !E->F.raw;
             tiny = R(1e-4) * E->h_max;
             R yf[NC];
 #pragma unroll
@@ -1698,7 +1764,16 @@ __global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ 
         cv[5] = __ldg(p + 4 * sz + 4);
         cv[6] = __ldg(p + 4 * (sz + sy));
         cv[7] = __ldg(p + 4 * (sz + sy) + 4);
-        coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, y, k1);
+        if constexpr (NC == 3) {
+          if (poly) {
+            trilinear_coeffs<R>(cv, ihc, pc);
+            k1[0] = coop_val_poly<R>(gm, gb, pc, y[0]);
+          } else {
+            coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, y, k1);
+          }
+        } else {
+          coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, y, k1);
+        }
         c_stage += (c == 0);
         kvalid = true;
       }
@@ -1724,30 +1799,10 @@ __global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ 
       }
       const R hh = sgn * hs;
       R k2[ND], k3[ND], k4[ND], k5[ND], k6[ND], k7[ND], t[ND], dy[ND];
-#pragma unroll
-      for (int i = 0; i < ND; ++i) t[i] = fma(hh, R(DA21) * k1[i], y[i]);
-      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k2);
-#pragma unroll
-      for (int i = 0; i < ND; ++i) t[i] = fma(hh, R(DA31) * k1[i] + R(DA32) * k2[i], y[i]);
-      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k3);
-#pragma unroll
-      for (int i = 0; i < ND; ++i) t[i] = fma(hh, R(DA41) * k1[i] + R(DA42) * k2[i] + R(DA43) * k3[i], y[i]);
-      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k4);
-#pragma unroll
-      for (int i = 0; i < ND; ++i)
-        t[i] = fma(hh, R(DA51) * k1[i] + R(DA52) * k2[i] + R(DA53) * k3[i] + R(DA54) * k4[i], y[i]);
-      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k5);
-#pragma unroll
-      for (int i = 0; i < ND; ++i)
-        t[i] = fma(hh, R(DA61) * k1[i] + R(DA62) * k2[i] + R(DA63) * k3[i] + R(DA64) * k4[i] + R(DA65) * k5[i],
-                   y[i]);
-      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k6);
-#pragma unroll
-      for (int i = 0; i < ND; ++i) {
-        dy[i] = hh * (R(DB1) * k1[i] + R(DB3) * k3[i] + R(DB4) * k4[i] + R(DB5) * k5[i] + R(DB6) * k6[i]);
-        t[i] = y[i] + dy[i];
-      }
-      coop_rhs<R, NC>(gm, gb, cv, E->F.raw, ih, ihc, t, k7);
+      if (NC == 3 && poly)
+        coop_stages<R, NC, NC == 3>(gm, gb, cv, pc, E->F.raw, ih, ihc, hh, y, k1, k2, k3, k4, k5, k6, k7, dy, t);
+      else
+        coop_stages<R, NC, false>(gm, gb, cv, pc, E->F.raw, ih, ihc, hh, y, k1, k2, k3, k4, k5, k6, k7, dy, t);
       c_stage += (c == 0) ? 6 : 0;
       steps += 1;
       R err = 0;
