@@ -241,6 +241,10 @@ typedef struct qsl_samples {
   uint8_t* status;   /* 1 per sample (optional)                                        */
   int32_t iters;     /* out: iterations run                                            */
   int32_t traced;    /* out: samples traced by this call (low 31 bits)                 */
+  int32_t* origin;   /* optional (NULL): the pass of this call that added each sample:
+                        0 the coarse pass or the proposal, 2i + 1 the pass along the
+                        curve of iteration i, 2i + 2 its shifted-curve pass; entries
+                        of resumed samples are kept                                    */
 } qsl_samples;
 
 /* Refines seeds along a Hilbert curve wherever the field-line length jumps by
@@ -410,9 +414,6 @@ int qsl_hilbert_decode(const uint64_t* keys, int64_t n, int ndim, int bits, uint
 int qsl_convert(const uint64_t* keys, const float* vals, int64_t n, int ndim, int max_order, const int32_t* extent,
                 int out_order, int log_interp, float* out, int mem, void* stream);
 
-/* Kernels of this library launched by this process since the library was
- * loaded (all threads). Radix sorts and scans inside qsl_refine run CUB
- * kernels, which are not counted. */
 /* Geometry of a loaded field (Sec. "Integrating field lines"):
  * QSL_GEOM_CARTESIAN (default) or QSL_GEOM_SPHERICAL. Spherical: the grid's
  * axes are longitude phi and latitude theta (radians, latitudes inside
@@ -440,6 +441,9 @@ int qsl_set_geometry(qsl_field* field, int geometry);
  * respect to nothing: blocks still in use by queued work stay allocated. */
 int qsl_trim_pool(void);
 
+/* Kernels of this library launched by this process since the library was
+ * loaded (all threads). Radix sorts and scans inside qsl_refine run CUB
+ * kernels, which are not counted. */
 int64_t qsl_kernel_launches(void);
 
 /* Human-readable message of the last failing call on this thread. */

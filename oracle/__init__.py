@@ -63,9 +63,12 @@ def lib():
         L.qslref_hilbert_key.argtypes = [vp, i32, i32]
         L.qslref_hilbert_coords.argtypes = [u64, i32, i32, vp]
         L.qslref_refine.restype = i64
-        L.qslref_refine.argtypes = [vp, C.POINTER(Opts), C.POINTER(RefineSpec), i64] + [vp] * 9
+        L.qslref_refine.argtypes = [vp, C.POINTER(Opts), C.POINTER(RefineSpec), i64] + [vp] * 10
         L.qslref_refine_fn.restype = i64
         L.qslref_refine_fn.argtypes = [vp, C.POINTER(RefineSpec), i64, vp, vp, vp, vp, vp]
+        L.qslref_refine_replay.restype = i64
+        L.qslref_refine_replay.argtypes = [vp, C.POINTER(RefineSpec), C.c_double, C.c_double, vp, vp, i64, i64, vp,
+                                           vp, vp, vp, vp, vp]
         L.qslref_convert.argtypes = [vp, vp, i64, i32, i32, vp, i32, i32, vp]
         assert L.qslref_sizeof_opts() == C.sizeof(Opts)
         assert L.qslref_sizeof_refine_spec() == C.sizeof(RefineSpec)
@@ -242,12 +245,12 @@ def refine(field, spec, opts=None, capacity=None):
         for a in range(spec.ndim):
             capacity *= spec.extent[a]
     arrs = {"key": np.zeros(capacity, dtype=np.uint64), "q": np.zeros(capacity), "L": np.zeros(capacity)}
-    for n in ("face_f", "face_b", "st_f", "st_b"):
+    for n in ("face_f", "face_b", "st_f", "st_b", "origin"):
         arrs[n] = np.zeros(capacity, dtype=np.int32)
     iters = np.zeros(1, dtype=np.int32)
     per = np.zeros(spec.max_iters + 1, dtype=np.int64)
     n = lib().qslref_refine(field.handle, C.byref(opts), C.byref(spec), capacity, *(_p(arrs[k]) for k in (
-        "key", "q", "L", "face_f", "face_b", "st_f", "st_b")), _p(iters), _p(per))
+        "key", "q", "L", "face_f", "face_b", "st_f", "st_b")), _p(iters), _p(per), _p(arrs["origin"]))
     if n < 0:
         raise RuntimeError("capacity too small: need %d" % -n)
     out = {k: a[:n].copy() for k, a in arrs.items()}
@@ -284,6 +287,54 @@ def refine_fn(fn, spec, capacity=None):
         raise RuntimeError("capacity too small: need %d" % -n)
     return {"key": key[:n].copy(), "q": q[:n].copy(), "L": L[:n].copy(), "iters": int(iters[0]),
             "traced_per_iter": per[:int(iters[0]) + 2].copy()}
+
+
+_EVAL_KFN = C.CFUNCTYPE(None, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double),
+                        C.POINTER(C.c_double))
+
+
+def refine_replay(fn, spec, tie_keys=(), tie_origin=(), band_abs=0.0, band_rel=0.0, capacity=None):
+    """Refinement driver (test hook) with values from fn(xyz[n,3], keys[n]) ->
+    (q[n], L[n]); a pair whose criterion value lies within the band of the
+    threshold (| |dL| - tau | <= band_abs + band_rel max(|L|), or Q within
+    band_rel of q_threshold) is refined exactly when another run added its new
+    cell in the same pass (tie_keys sorted, tie_origin the pass that added each:
+    0 coarse pass, 2i+1 / 2i+2 pass A / B of iteration i). With values that
+    carry no error, the band set to the error bound of the other run's values
+    and that run's samples as the ties, the replay reproduces the other run's
+    set when all their disagreements lie within the bound. Returns key, q, L,
+    origin, iters."""
+    if capacity is None:
+        capacity = 1
+        for a in range(spec.ndim):
+            capacity *= spec.extent[a]
+    tk = np.asarray(tie_keys, dtype=np.uint64)
+    to = np.asarray(tie_origin, dtype=np.int32)
+    assert tk.shape == to.shape
+    order = np.argsort(tk, kind="stable")
+    tk, to = np.ascontiguousarray(tk[order]), np.ascontiguousarray(to[order])
+
+    def cb(n, xyz, keys, q, L):
+        x = np.ctypeslib.as_array(xyz, shape=(n, 3)).copy()
+        k = np.ctypeslib.as_array(keys, shape=(n,)).copy()
+        qq, ll = fn(x, k)
+        np.ctypeslib.as_array(q, shape=(n,))[:] = qq
+        np.ctypeslib.as_array(L, shape=(n,))[:] = ll
+
+    cfn = _EVAL_KFN(cb)
+    key = np.zeros(capacity, dtype=np.uint64)
+    q = np.zeros(capacity)
+    L = np.zeros(capacity)
+    origin = np.zeros(capacity, dtype=np.int32)
+    iters = np.zeros(1, dtype=np.int32)
+    per = np.zeros(spec.max_iters + 1, dtype=np.int64)
+    n = lib().qslref_refine_replay(C.cast(cfn, C.c_void_p), C.byref(spec), float(band_abs), float(band_rel),
+                                   _p(tk), _p(to), tk.size, capacity, _p(key), _p(q), _p(L), _p(origin), _p(iters),
+                                   _p(per))
+    if n < 0:
+        raise RuntimeError("capacity too small: need %d" % -n)
+    return {"key": key[:n].copy(), "q": q[:n].copy(), "L": L[:n].copy(), "origin": origin[:n].copy(),
+            "iters": int(iters[0]), "traced_per_iter": per[:int(iters[0]) + 2].copy()}
 
 
 def convert(keys, vals, ndim, max_order, extent, out_order, log_interp):

@@ -6,7 +6,7 @@
 // helper with the CUDA library; the two only see the same synthetic inputs.
 //
 // Every function names the passage of the paper it follows. Where the paper is
-// silent, the reading taken is stated next to the code and listed in the design doc.
+// silent, the reading taken is stated next to the code.
 //
 // Parity pins (tests/test_oracle_*.py): closed forms of the linear hyperbolic
 // field, Q >= 2, flux conservation, equal Q from either footpoint and from a
@@ -1151,6 +1151,7 @@ struct Sample {
   uint64_t key;
   double q, L;
   int face_f, face_b, st_f, st_b;
+  int origin;  // pass that added it: 0 coarse pass, 2i + 1 / 2i + 2 pass A / B of iteration i
 };
 
 // Position of the centre of effective-lattice cell c.
@@ -1174,6 +1175,26 @@ struct Evaluator {
   const Field* F = nullptr;
   const Opts* o = nullptr;
   void (*fn)(int64_t, const double*, double*, double*) = nullptr;  // test hook: (n, xyz, q, L)
+  // test hook with the samples' keys: (n, xyz, keys, q, L)
+  void (*fnk)(int64_t, const double*, const uint64_t*, double*, double*) = nullptr;
+};
+
+// Test hook of the refinement driver (no counterpart in the paper): pairs
+// whose criterion value lies within a band of the threshold are decided by
+// whether another run added their new cell in the same pass, read from that
+// run's sorted keys and the pass that added each. A traced sample set whose
+// values carry a known error can then be replayed from values without that
+// error: with the band set to the error bound, the replay reproduces the set
+// exactly when every decision the two runs disagree on lies within the bound.
+//  - FLL jump: ambiguous when | |L_i - L_j| - tau | <= band_abs + band_rel * max(|L_i|, |L_j|).
+//  - Q threshold: a sample is ambiguous when its Q is finite and
+//    |Q / q_threshold - 1| <= band_rel; a pair is ambiguous when neither sample
+//    is clearly above the threshold and one of them is ambiguous.
+struct Arbiter {
+  double band_abs, band_rel;
+  const uint64_t* keys;   // sorted ascending
+  const int32_t* origin;  // pass that added each of them (as Sample::origin)
+  int64_t n;
 };
 
 // Region test for curve cells: lo[a] <= c[a] < hi[a] on every axis.
@@ -1243,9 +1264,15 @@ void trace_samples(const Evaluator& ev, const RefineSpec& s, std::vector<Sample>
     hilbert_coords(v[i].key, s.ndim, s.max_order, c);
     cell_position(s, c, &seeds[3 * i]);
   }
-  if (ev.fn) {
+  if (ev.fn || ev.fnk) {
     std::vector<double> q(v.size()), L(v.size());
-    ev.fn((int64_t)v.size(), seeds.data(), q.data(), L.data());
+    if (ev.fnk) {
+      std::vector<uint64_t> keys(v.size());
+      for (size_t i = 0; i < v.size(); ++i) keys[i] = v[i].key;
+      ev.fnk((int64_t)v.size(), seeds.data(), keys.data(), q.data(), L.data());
+    } else {
+      ev.fn((int64_t)v.size(), seeds.data(), q.data(), L.data());
+    }
     for (size_t i = 0; i < v.size(); ++i) {
       v[i].q = q[i];
       v[i].L = L[i];
@@ -1303,9 +1330,29 @@ static bool pair_flagged(const RefineSpec& s, const Sample& A, const Sample& B) 
   return std::fabs(B.L - A.L) > s.tau;
 }
 
+// The decision with the test hook: the comparison, or, for a pair within the
+// band, whether its new cell `cand` is in the arbiter's key set.
+static bool pair_ambiguous(const RefineSpec& s, const Sample& A, const Sample& B, const Arbiter& arb) {
+  if (s.criterion == 1) {
+    auto clear_above = [&](double q) { return std::isfinite(q) && q / s.q_threshold - 1.0 > arb.band_rel; };
+    auto near = [&](double q) { return std::isfinite(q) && std::fabs(q / s.q_threshold - 1.0) <= arb.band_rel; };
+    return !clear_above(A.q) && !clear_above(B.q) && (near(A.q) || near(B.q));
+  }
+  double d = std::fabs(B.L - A.L);
+  double band = arb.band_abs + arb.band_rel * std::max(std::fabs(A.L), std::fabs(B.L));
+  return std::fabs(d - s.tau) <= band;
+}
+
+// Whether the arbiter's run added cell k in pass `pass`.
+static bool added_in(const Arbiter& arb, uint64_t k, int pass) {
+  const uint64_t* it = std::lower_bound(arb.keys, arb.keys + arb.n, k);
+  return it != arb.keys + arb.n && *it == k && arb.origin[it - arb.keys] == pass;
+}
+
 static int64_t refine_impl(const Evaluator& ev, const RefineSpec* sp, int64_t capacity, uint64_t* key,
                            double* q, double* L, int32_t* face_f, int32_t* face_b, int32_t* st_f,
-                           int32_t* st_b, int32_t* iters_out, int64_t* traced_per_iter) {
+                           int32_t* st_b, int32_t* iters_out, int64_t* traced_per_iter,
+                           const Arbiter* arb = nullptr, int32_t* origin = nullptr) {
   const RefineSpec& s = *sp;
   int p = s.max_order, p0 = s.coarse_order, nd = s.ndim;
   uint32_t R = 1u << (p - p0);
@@ -1336,12 +1383,16 @@ static int64_t refine_impl(const Evaluator& ev, const RefineSpec* sp, int64_t ca
     std::vector<Sample> add;
     for (size_t i = 0; i + 1 < all.size(); ++i) {
       uint64_t gap = all[i + 1].key - all[i].key;
-      if (gap > 1 && pair_flagged(s, all[i], all[i + 1])) {
+      if (gap <= 1) continue;
+      const bool amb = arb && pair_ambiguous(s, all[i], all[i + 1], *arb);
+      if (amb || pair_flagged(s, all[i], all[i + 1])) {
         uint64_t m = all[i].key + gap / 2;
         uint64_t got;
         if (!nearest_in_region(m, all[i].key, all[i + 1].key, nd, p, rlo, rhi, &got)) continue;
+        if (amb && !added_in(*arb, got, 2 * it + 1)) continue;
         Sample smp{};
         smp.key = got;
+        smp.origin = 2 * it + 1;
         add.push_back(smp);
       }
     }
@@ -1369,7 +1420,9 @@ static int64_t refine_impl(const Evaluator& ev, const RefineSpec* sp, int64_t ca
         uint64_t gap = sk[i + 1].first - sk[i].first;
         const Sample& A = all[sk[i].second];
         const Sample& B = all[sk[i + 1].second];
-        if (gap > 1 && pair_flagged(s, A, B)) {
+        if (gap <= 1) continue;
+        const bool amb = arb && pair_ambiguous(s, A, B, *arb);
+        if (amb || pair_flagged(s, A, B)) {
           uint64_t m = sk[i].first + gap / 2;
           uint64_t slo[3], shi[3], got;
           for (int a = 0; a < 3; ++a) {
@@ -1382,6 +1435,8 @@ static int64_t refine_impl(const Evaluator& ev, const RefineSpec* sp, int64_t ca
           for (int a = 0; a < nd; ++a) c[a] -= S;
           Sample smp{};
           smp.key = hilbert_key(c, nd, p);
+          smp.origin = 2 * it + 2;
+          if (amb && !added_in(*arb, smp.key, 2 * it + 2)) continue;
           add2.push_back(smp);
         }
       }
@@ -1403,17 +1458,19 @@ static int64_t refine_impl(const Evaluator& ev, const RefineSpec* sp, int64_t ca
     face_b[i] = all[i].face_b;
     st_f[i] = all[i].st_f;
     st_b[i] = all[i].st_b;
+    if (origin) origin[i] = all[i].origin;
   }
   return n;
 }
 
 int64_t qslref_refine(const void* fp, const Opts* o, const RefineSpec* sp, int64_t capacity, uint64_t* key,
                       double* q, double* L, int32_t* face_f, int32_t* face_b, int32_t* st_f, int32_t* st_b,
-                      int32_t* iters_out, int64_t* traced_per_iter) {
+                      int32_t* iters_out, int64_t* traced_per_iter, int32_t* origin) {
   Evaluator ev;
   ev.F = (const Field*)fp;
   ev.o = o;
-  return refine_impl(ev, sp, capacity, key, q, L, face_f, face_b, st_f, st_b, iters_out, traced_per_iter);
+  return refine_impl(ev, sp, capacity, key, q, L, face_f, face_b, st_f, st_b, iters_out, traced_per_iter, nullptr,
+                     origin);
 }
 
 // Same driver with the tracer replaced by a caller-supplied function of the
@@ -1427,6 +1484,24 @@ int64_t qslref_refine_fn(void (*fn)(int64_t, const double*, double*, double*), c
   int32_t* d = dummy.data();
   size_t c = (size_t)std::max<int64_t>(capacity, 1);
   return refine_impl(ev, sp, capacity, key, q, L, d, d + c, d + 2 * c, d + 3 * c, iters_out, traced_per_iter);
+}
+
+// Replay of a sample set (test hook, see Arbiter): the driver with values from
+// fn(n, xyz, keys, q, L), and pairs within the band of the threshold decided by
+// membership of their new cell in tie_keys (sorted). Outputs as qslref_refine_fn.
+int64_t qslref_refine_replay(void (*fn)(int64_t, const double*, const uint64_t*, double*, double*),
+                             const RefineSpec* sp, double band_abs, double band_rel, const uint64_t* tie_keys,
+                             const int32_t* tie_origin, int64_t n_tie, int64_t capacity, uint64_t* key,
+                             double* q, double* L, int32_t* origin, int32_t* iters_out,
+                             int64_t* traced_per_iter) {
+  Evaluator ev;
+  ev.fnk = fn;
+  Arbiter arb{band_abs, band_rel, tie_keys, tie_origin, n_tie};
+  std::vector<int32_t> dummy(4 * (size_t)std::max<int64_t>(capacity, 1));
+  int32_t* d = dummy.data();
+  size_t c = (size_t)std::max<int64_t>(capacity, 1);
+  return refine_impl(ev, sp, capacity, key, q, L, d, d + c, d + 2 * c, d + 3 * c, iters_out, traced_per_iter,
+                     &arb, origin);
 }
 
 // Hilbert -> rectilinear array converter (Sec. "Adaptive refinements").

@@ -253,9 +253,10 @@ __device__ __forceinline__ int64_t count_below(const uint64_t* __restrict__ a, i
 // nkey[j]. Output to o*.
 __global__ void merge_samples_kernel(const uint64_t* __restrict__ key, const float* __restrict__ q,
                                      const float* __restrict__ L, const uint8_t* __restrict__ fa,
-                                     const uint8_t* __restrict__ st, int64_t n, const uint64_t* __restrict__ nkey,
-                                     const int64_t* __restrict__ nperm, int64_t m, uint64_t* okey, float* oq,
-                                     float* oL, uint8_t* ofa, uint8_t* ost) {
+                                     const uint8_t* __restrict__ st, const int32_t* __restrict__ org, int64_t n,
+                                     const uint64_t* __restrict__ nkey, const int64_t* __restrict__ nperm,
+                                     int64_t m, uint64_t* okey, float* oq, float* oL, uint8_t* ofa, uint8_t* ost,
+                                     int32_t* oorg) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n + m; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t p, src;
     uint64_t k;
@@ -275,7 +276,13 @@ __global__ void merge_samples_kernel(const uint64_t* __restrict__ key, const flo
     ofa[2 * p] = fa[2 * src];
     ofa[2 * p + 1] = fa[2 * src + 1];
     ost[p] = st[src];
+    if (org) oorg[p] = org[src];
   }
+}
+
+__global__ void fill_i32_kernel(int32_t* p, int64_t n, int32_t v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
 }
 
 // A shifted-curve order (shifted key, length), sorted; new entries nskey
@@ -644,11 +651,13 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
   int64_t *perm = nullptr, *perm2 = nullptr, *flags = nullptr, *pos = nullptr;
   float *q2 = nullptr, *L2 = nullptr;
   uint8_t *fa2 = nullptr, *st2 = nullptr;
+  int32_t* org2 = nullptr;
   if ((rc = sc.alloc(&kA, cap)) || (rc = sc.alloc(&cand, cap)) || (rc = sc.alloc(&sk, cap)) ||
       (rc = sc.alloc(&sk2, cap)) || (rc = sc.alloc(&perm, cap)) || (rc = sc.alloc(&perm2, cap)) ||
       (rc = sc.alloc(&flags, cap)) || (rc = sc.alloc(&pos, cap)) || (rc = sc.alloc(&q2, cap)) ||
       (rc = sc.alloc(&L2, cap)) || (rc = sc.alloc(&fa2, 2 * cap)) || (rc = sc.alloc(&st2, cap)))
     return rc;
+  if (smp->origin && (rc = sc.alloc(&org2, cap))) return rc;
 
   // the criterion and the per-sample value it reads (L or Q)
   Criterion crit{sp->criterion, sp->tau, sp->q_threshold};
@@ -688,8 +697,12 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
 
   // trace samples [off, off + m) (keys already written; `sorted`: in key
   // order) and merge them into the sorted set and into the built orders
-  auto trace_and_merge = [&](int64_t off, int64_t m, bool sorted) -> int {
+  auto trace_and_merge = [&](int64_t off, int64_t m, bool sorted, int32_t pass_id) -> int {
     if (m <= 0) return QSL_OK;
+    if (smp->origin) {
+      fill_i32_kernel<<<grid_for(m), 256, 0, s>>>(smp->origin + off, m, pass_id);
+      qsl::count_launch();
+    }
     SeedSource s2 = src;
     s2.keys = smp->key + off;
     LineOutputs lo{};
@@ -744,10 +757,13 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
     }
     // main order
     int64_t tot = off + m;
-    merge_samples_kernel<<<grid_for(tot), 256, 0, s>>>(smp->key, smp->q, smp->length, smp->faces, smp->status, off,
-                                                        bkey, bperm, m, kA, q2, L2, fa2, st2);
+    merge_samples_kernel<<<grid_for(tot), 256, 0, s>>>(smp->key, smp->q, smp->length, smp->faces, smp->status,
+                                                        smp->origin, off, bkey, bperm, m, kA, q2, L2, fa2, st2,
+                                                        org2);
     qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
+    if (smp->origin)
+      QSL_CHECK_CUDA(cudaMemcpyAsync(smp->origin, org2, tot * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, kA, tot * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     QSL_CHECK_CUDA(cudaMemcpyAsync(smp->q, q2, tot * sizeof(float), cudaMemcpyDeviceToDevice, s));
     QSL_CHECK_CUDA(cudaMemcpyAsync(smp->length, L2, tot * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -796,7 +812,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
     qsl::count_launch();
     if ((rc = sort_pairs(smp->key, kA, perm, perm2, m, nd * p, s))) return rc;
     QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, kA, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-    if ((rc = trace_and_merge(0, m, true))) return rc;
+    if ((rc = trace_and_merge(0, m, true, 0))) return rc;
     n = m;
   }
   // optional proposal (fresh runs and resumed ones): every effective cell of
@@ -846,7 +862,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
         qsl::count_launch();
         if ((rc = sort_pairs(smp->key + n, kA, perm, perm2, got, nd * p, s))) return rc;
         QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key + n, kA, got * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-        if ((rc = trace_and_merge(n, got, true))) return rc;
+        if ((rc = trace_and_merge(n, got, true, 0))) return rc;
         n += got;
       }
     }
@@ -862,7 +878,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((rc = compact(n - 1, &added))) return rc;
-      if ((rc = trace_and_merge(n, added, true))) return rc;
+      if ((rc = trace_and_merge(n, added, true, 2 * it + 1))) return rc;
       n += added;
       added_total += added;
     }
@@ -889,7 +905,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((rc = compact(n - 1, &added))) return rc;
-      if ((rc = trace_and_merge(n, added, false))) return rc;
+      if ((rc = trace_and_merge(n, added, false, 2 * it + 2))) return rc;
       n += added;
       added_total += added;
     }
@@ -1175,6 +1191,10 @@ int qsl_refine(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o,
     if (smp->status) QSL_CHECK_CUDA(cudaMemcpyAsync(d.status, smp->status, c0, cudaMemcpyHostToDevice, s));
     else QSL_CHECK_CUDA(cudaMemsetAsync(d.status, 0, c0, s));
   }
+  if (smp->origin) {
+    QSL_CHECK_CUDA(qsl::alloc_async((void**)&d.origin, cap * 4, s));
+    if (c0) QSL_CHECK_CUDA(cudaMemcpyAsync(d.origin, smp->origin, c0 * 4, cudaMemcpyHostToDevice, s));
+  }
   int ext[3] = {1, 1, 1};
   for (int a = 0; a < nd; ++a) ext[a] = sp->extent[a] > 0 ? sp->extent[a] : (1 << p);
   int dd = p - oo;
@@ -1192,6 +1212,7 @@ int qsl_refine(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o,
       QSL_CHECK_CUDA(cudaMemcpyAsync(smp->length, d.length, n * 4, cudaMemcpyDeviceToHost, s));
       if (smp->faces) QSL_CHECK_CUDA(cudaMemcpyAsync(smp->faces, d.faces, n * 2, cudaMemcpyDeviceToHost, s));
       if (smp->status) QSL_CHECK_CUDA(cudaMemcpyAsync(smp->status, d.status, n, cudaMemcpyDeviceToHost, s));
+      if (smp->origin) QSL_CHECK_CUDA(cudaMemcpyAsync(smp->origin, d.origin, n * 4, cudaMemcpyDeviceToHost, s));
     }
     if (qg) QSL_CHECK_CUDA(cudaMemcpyAsync(q_grid, qg, N * 4, cudaMemcpyDeviceToHost, s));
     if (lg) QSL_CHECK_CUDA(cudaMemcpyAsync(l_grid, lg, N * 4, cudaMemcpyDeviceToHost, s));
@@ -1204,6 +1225,7 @@ int qsl_refine(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o,
   cudaFreeAsync(d.length, s);
   cudaFreeAsync(d.faces, s);
   cudaFreeAsync(d.status, s);
+  if (d.origin) cudaFreeAsync(d.origin, s);
   if (qg) cudaFreeAsync(qg, s);
   if (lg) cudaFreeAsync(lg, s);
   cudaStreamSynchronize(s);

@@ -80,7 +80,7 @@ QSL_REFINE_Q_THRESHOLD = 1
 class qsl_samples(C.Structure):
     _fields_ = [("capacity", C.c_int64), ("count", C.c_int64), ("key", C.c_void_p), ("q", C.c_void_p),
                 ("length", C.c_void_p), ("faces", C.c_void_p), ("status", C.c_void_p), ("iters", C.c_int32),
-                ("traced", C.c_int32)]
+                ("traced", C.c_int32), ("origin", C.c_void_p)]
 
 
 class qsl_batch_item(C.Structure):
@@ -386,16 +386,18 @@ def refine_spec(**kw):
 
 
 def qsl_refine(field, spec, opts, key, q, length, faces=None, status=None, count=0, q_grid=None, l_grid=None,
-               stream=None):
-    """Sample arrays (capacity = len(key)) are caller-owned; returns
-    (count, iters, traced) and raises on errors other than QSL_ECAPACITY."""
-    mem = _mem_of(key, q, length, faces, status, q_grid, l_grid)
+               stream=None, origin=None):
+    """Sample arrays (capacity = len(key)) are caller-owned; origin (optional,
+    int32) receives the pass that added each sample. Returns (count, iters,
+    traced, rc) and raises on errors other than QSL_ECAPACITY."""
+    mem = _mem_of(key, q, length, faces, status, q_grid, l_grid, origin)
     smp = qsl_samples()
     smp.capacity = key.shape[0]
     smp.count = count
     smp.key, smp.q, smp.length = (_ptr(a).value for a in (key, q, length))
     smp.faces = _ptr(faces).value if faces is not None else None
     smp.status = _ptr(status).value if status is not None else None
+    smp.origin = _ptr(origin).value if origin is not None else None
     rc = lib().qsl_refine(field.handle, C.byref(spec), C.byref(opts), C.byref(smp), _ptr(q_grid), _ptr(l_grid), mem,
                           _stream(stream))
     if rc not in (QSL_OK, QSL_ECAPACITY):

@@ -45,6 +45,7 @@ def compare_lines(gpu, ref, cell, lo, hi, q_key_gpu="q_perp", q_key_ref="q_perp"
     fails = []
     label_checked = 0
     q_checked = 0
+    floored = 0  # lines shorter than one cell: their length error is taken against one cell
     worst_q = 0.0
     worst_l = 0.0
     for i in range(n):
@@ -61,6 +62,7 @@ def compare_lines(gpu, ref, cell, lo, hi, q_key_gpu="q_perp", q_key_ref="q_perp"
                 continue
         Lr = ref["L"][i]
         if np.isfinite(Lr):
+            floored += int(Lr < cell)
             e = abs(gpu["L"][i] - Lr) / max(Lr, cell)
             worst_l = max(worst_l, e)
             if not e <= l_rtol:
@@ -73,7 +75,7 @@ def compare_lines(gpu, ref, cell, lo, hi, q_key_gpu="q_perp", q_key_ref="q_perp"
             if not e <= q_rtol:
                 fails.append(("Q", i, gpu[q_key_gpu][i], qr, e))
     rep = {"n": n, "labels_checked": label_checked, "q_checked": q_checked, "worst_q": worst_q, "worst_l": worst_l,
-           "fails": fails[:10], "n_fail": len(fails)}
+           "under_one_cell": floored, "fails": fails[:10], "n_fail": len(fails)}
     print("parity:", {k: v for k, v in rep.items() if k != "fails"}, rep["fails"][:4])
     assert not fails, rep
     return rep

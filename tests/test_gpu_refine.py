@@ -130,53 +130,132 @@ def test_refine_dense_and_values(qsl, oracle_mod):
     assert np.all(length_err(L[good], r["L"][good], Fo.cell) <= L_RTOL)
 
 
-@pytest.mark.parametrize("ndim", [2, 3])
-def test_refine_sample_set_matches_oracle(qsl, oracle_mod, ndim):
-    F, Fo = _fields(qsl, oracle_mod, n=40, seed=3)
+def _refine_case(ndim):
     if ndim == 2:
-        kw = dict(ndim=2, coarse_order=4, max_order=7, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), tau=0.05)
-        cap = 128 * 128
-    else:
-        kw = dict(ndim=3, coarse_order=2, max_order=4, extent=(16, 16, 8), lo=(-1, -1, 0), hi=(1, 1, 1), tau=0.05)
-        cap = 16 * 16 * 8
+        return dict(ndim=2, coarse_order=4, max_order=7, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0),
+                    tau=0.05), 128 * 128
+    return dict(ndim=3, coarse_order=2, max_order=4, extent=(16, 16, 8), lo=(-1, -1, 0), hi=(1, 1, 1),
+                tau=0.05), 16 * 16 * 8
+
+
+def _gpu_refine(qsl, F, kw, cap, o):
+    """qsl_refine through the C ABI; returns host copies of the sample set with
+    the pass that added each sample."""
+    b = _alloc(cap)
+    org = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    n, iters, traced, rc = qsl.qsl_refine(F, qsl.refine_spec(**kw), o, b["key"], b["q"], b["L"], b["faces"], b["st"],
+                                          origin=org)
+    assert rc == qsl.QSL_OK
+    fa = b["faces"].cpu().numpy()[:2 * n].reshape(-1, 2)
+    return {"key": b["key"].cpu().numpy()[:n].view(np.uint64).copy(), "q": b["q"].cpu().numpy()[:n],
+            "L": b["L"].cpu().numpy()[:n], "face_f": fa[:, 0], "face_b": fa[:, 1],
+            "origin": org.cpu().numpy()[:n], "iters": iters, "traced": traced}
+
+
+class _Truth:
+    """Oracle lines (tol 1e-11) of the refinement samples it is asked for,
+    remembered by key, so the replay and the comparison share one trace."""
+
+    def __init__(self, oracle_mod, Fo, length_only=False):
+        self.o, self.Fo = oracle_mod, Fo
+        self.opts = oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11, length_only=int(length_only))
+        self.lines = {}
+
+    def __call__(self, x, keys):
+        r = self.o.trace_seeds(self.Fo, x, self.opts)
+        for i, k in enumerate(keys):
+            self.lines[int(k)] = {name: r[name][i] for name in r}
+        return r["q_perp"], r["L"]
+
+    def records(self, keys):
+        return {name: np.array([self.lines[int(k)][name] for k in keys]) for name in self.lines[int(keys[0])]}
+
+
+def _band(cell):
+    """Band of the threshold within which a refinement decision may differ
+    between the GPU and the oracle: each length is within L_RTOL max(L, cell) of
+    the oracle's, so a pair's |dL| within 2 L_RTOL (max L + cell)."""
+    return 2 * L_RTOL * cell, 2 * L_RTOL
+
+
+def _check_replay(oracle_mod, g, rep, what):
+    """The replay's sample set (and the pass that added each sample) is the
+    GPU's, key for key."""
+    gk, rk = g["key"], rep["key"]
+    only_g = np.setdiff1d(gk, rk)
+    only_r = np.setdiff1d(rk, gk)
+    print("%s: %d samples, %d iterations; replay %d samples; only GPU %d, only replay %d" % (
+        what, len(gk), g["iters"], len(rk), len(only_g), len(only_r)))
+    assert len(only_g) == 0 and len(only_r) == 0, (what, only_g[:8], only_r[:8])
+    assert np.array_equal(rep["origin"], g["origin"]), what
+
+
+@pytest.mark.parametrize("integrator", ["ck", "cell"])
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_refine_length_only_decisions_replay_exactly(qsl, oracle_mod, ndim, integrator):
+    """Lengths-only refinement (the mode of the refinement passes): (1) the
+    oracle's refinement driver fed the GPU's own lengths makes the GPU's sample
+    set, key for key and pass for pass (the flagging, midpoint, shifted-curve and
+    merge logic is exact); (2) every GPU length is within the parity bar of the
+    oracle's and the end faces are the oracle's; (3) the oracle's driver on its
+    own lengths reproduces the GPU set once the pairs whose |dL| lies within the
+    GPU's stated length error of tau are decided by the GPU's choice, so every
+    key where the two sets differ comes from such a pair."""
+    from gpu_helpers import compare_lines
+    F, Fo = _fields(qsl, oracle_mod, n=40, seed=3)
+    kw, cap = _refine_case(ndim)
+    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL, length_only=1,
+                             integrator=qsl.QSL_DOPRI5_CELL if integrator == "cell" else qsl.QSL_RKCK54)
+    g = _gpu_refine(qsl, F, kw, cap, o)
+    assert g["iters"] > 0 and g["traced"] == len(g["key"])
+    spo = oracle_mod.refine_spec(**kw)
+    own = dict(zip(g["key"].tolist(), g["L"].astype(np.float64).tolist()))
+    exact = oracle_mod.refine_replay(lambda x, k: (np.full(len(k), np.nan), np.array([own.get(int(v), np.nan)
+                                                                                     for v in k])), spo)
+    _check_replay(oracle_mod, g, exact, "exact replay on GPU lengths")
+    truth = _Truth(oracle_mod, Fo, length_only=True)
+    ba, br = _band(Fo.cell)
+    rep = oracle_mod.refine_replay(truth, spo, g["key"], g["origin"], band_abs=ba, band_rel=br)
+    _check_replay(oracle_mod, g, rep, "replay on oracle lengths")
+    ref = truth.records(g["key"])
+    plain = oracle_mod.refine(Fo, spo, truth.opts)
+    print("oracle's own refinement: %d samples (symmetric difference with the GPU set %d)" % (
+        len(plain["key"]), len(np.setxor1d(plain["key"], g["key"]))))
+    compare_lines(g, ref, Fo.cell, (-1, -1, 0), (1, 1, 1))
+
+
+@pytest.mark.parametrize("integrator", ["ck", "cell"])
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_refine_sample_set_matches_oracle(qsl, oracle_mod, ndim, integrator):
+    """Default refinement (tangent-space coarse pass, lengths-only passes, one
+    tangent-space trace of the pass samples): the oracle's driver on its own
+    lines reproduces the GPU sample set key for key once the pairs within the
+    stated length error of tau follow the GPU's choice; every sample's Q, L and
+    end faces match the oracle's; the converted grids keep the sampled values."""
+    from gpu_helpers import compare_lines
+    F, Fo = _fields(qsl, oracle_mod, n=40, seed=3)
+    kw, cap = _refine_case(ndim)
+    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL,
+                             integrator=qsl.QSL_DOPRI5_CELL if integrator == "cell" else qsl.QSL_RKCK54)
     sp = qsl.refine_spec(**kw)
     b = _alloc(cap)
-    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL)
+    org = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
     qg = torch.zeros(cap, device="cuda")
     lg = torch.zeros(cap, device="cuda")
     n, iters, traced, rc = qsl.qsl_refine(F, sp, o, b["key"], b["q"], b["L"], b["faces"], b["st"], q_grid=qg,
-                                          l_grid=lg)
+                                          l_grid=lg, origin=org)
     assert rc == qsl.QSL_OK
     keys = b["key"].cpu().numpy()[:n].view(np.uint64)
     assert np.all(np.diff(keys.astype(np.int64)) > 0)
-    ref = oracle_mod.refine(Fo, oracle_mod.refine_spec(**kw), oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
-    rk = set(int(k) for k in ref["key"])
-    gk = set(int(k) for k in keys)
-    # pairs whose |dL| sits within the parity error of tau may be refined on one
-    # side only; everything else is identical
-    sym = len(rk ^ gk)
-    assert sym <= max(3, 0.02 * len(rk)), (sym, len(rk), len(gk))
-    common = np.array(sorted(rk & gk), dtype=np.uint64)
-    gi = np.searchsorted(keys, common)
-    ri = np.searchsorted(ref["key"], common)
-    q = b["q"].cpu().numpy()[:n][gi]
-    L = b["L"].cpu().numpy()[:n][gi]
-    qr, Lr = ref["q"][ri], ref["L"][ri]
-    fg = b["faces"].cpu().numpy()[:2 * n].reshape(-1, 2)[gi]
-    same = (fg[:, 0] == ref["face_f"][ri]) & (fg[:, 1] == ref["face_b"][ri])
-    # end labels may differ only for lines ending at a face edge (not reported
-    # by qsl_refine); they are few
-    assert (~same).sum() <= max(2, 0.002 * len(same)), (~same).sum()
-    ok = np.isfinite(qr) & (qr < 1e6) & same
-    eq = np.abs(q[ok] / qr[ok] - 1)
-    print("refine parity: n=%d worst Q %.2e" % (ok.sum(), eq.max()), np.sort(eq)[-5:])
-    assert np.all(eq <= Q_RTOL)
-    good = np.isfinite(Lr) & same
-    el = length_err(L[good], Lr[good], Fo.cell)
-    w = np.argsort(el)[-5:]
-    gi_good = np.where(good)[0][w]
-    assert np.all(el <= L_RTOL), (el[w], L[good][w], Lr[good][w], common[gi_good], fg[gi_good],
-                                  ref["lam_f"][ri][gi_good] if "lam_f" in ref else None)
+    fa = b["faces"].cpu().numpy()[:2 * n].reshape(-1, 2)
+    g = {"key": keys.copy(), "q_perp": b["q"].cpu().numpy()[:n], "L": b["L"].cpu().numpy()[:n], "face_f": fa[:, 0],
+         "face_b": fa[:, 1], "origin": org.cpu().numpy()[:n], "iters": iters}
+    spo = oracle_mod.refine_spec(**kw)
+    truth = _Truth(oracle_mod, Fo)
+    ba, br = _band(Fo.cell)
+    rep = oracle_mod.refine_replay(truth, spo, keys, g["origin"], band_abs=ba, band_rel=br)
+    _check_replay(oracle_mod, g, rep, "replay on oracle lines")
+    compare_lines(g, truth.records(keys), Fo.cell, (-1, -1, 0), (1, 1, 1))
     # converted grids keep the sampled values in their cells
     c = np.zeros((n, ndim), dtype=np.uint32)
     qsl.qsl_hilbert_decode(keys, ndim, sp.max_order, c)
@@ -286,43 +365,31 @@ def test_refine_time_accounting(qsl, oracle_mod):
 
 @pytest.mark.parametrize("ndim", [2, 3])
 def test_refine_q_threshold_criterion_matches_oracle(qsl, oracle_mod, ndim):
-    """The Q-threshold criterion (QSL_REFINE_Q_THRESHOLD) gives the oracle's
-    sample set (up to pairs whose Q sits within the parity error of the
-    threshold) and the oracle's values on the common samples."""
+    """The Q-threshold criterion (QSL_REFINE_Q_THRESHOLD): the oracle's driver
+    on its own lines reproduces the GPU sample set key for key once the pairs
+    whose Q lies within the Q parity bar of the threshold follow the GPU's
+    choice; every sample matches the oracle's line; at termination no pair with
+    a gap has a sample above the threshold."""
+    from gpu_helpers import compare_lines
     F, Fo = _fields(qsl, oracle_mod, n=40, seed=3)
-    if ndim == 2:
-        kw = dict(ndim=2, coarse_order=4, max_order=7, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), tau=0.05)
-        cap = 128 * 128
-    else:
-        kw = dict(ndim=3, coarse_order=2, max_order=4, extent=(16, 16, 8), lo=(-1, -1, 0), hi=(1, 1, 1), tau=0.05)
-        cap = 16 * 16 * 8
+    kw, cap = _refine_case(ndim)
     thr = 30.0 if ndim == 2 else 10.0  # the 3D coarse samples stay below 30
     kw.update(criterion=qsl.QSL_REFINE_Q_THRESHOLD, q_threshold=thr)
-    sp = qsl.refine_spec(**kw)
-    b = _alloc(cap)
     o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL)
-    n, iters, traced, rc = qsl.qsl_refine(F, sp, o, b["key"], b["q"], b["L"], b["faces"], b["st"])
-    assert rc == qsl.QSL_OK and iters > 0
-    keys = b["key"].cpu().numpy()[:n].view(np.uint64)
-    ref = oracle_mod.refine(Fo, oracle_mod.refine_spec(**kw), oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
-    rk = set(int(k) for k in ref["key"])
-    gk = set(int(k) for k in keys)
-    assert len(rk) > (1 << (kw["coarse_order"] * ndim)) * 1.05  # it refined
-    sym = len(rk ^ gk)
-    assert sym <= max(3, 0.02 * len(rk)), (sym, len(rk), len(gk))
-    common = np.array(sorted(rk & gk), dtype=np.uint64)
-    gi = np.searchsorted(keys, common)
-    ri = np.searchsorted(ref["key"], common)
-    q = b["q"].cpu().numpy()[:n][gi]
-    qr = ref["q"][ri]
-    ok = np.isfinite(qr) & (qr < 1e6)
-    assert np.all(np.abs(q[ok] / qr[ok] - 1) <= Q_RTOL)
-    # termination: no pair adjacent along the curve with a gap has a sample above the threshold
-    qa = b["q"].cpu().numpy()[:n]
+    g = _gpu_refine(qsl, F, kw, cap, o)
+    assert g["iters"] > 0
+    assert len(g["key"]) > (1 << (kw["coarse_order"] * ndim)) * 1.05  # it refined
+    spo = oracle_mod.refine_spec(**kw)
+    truth = _Truth(oracle_mod, Fo)
+    rep = oracle_mod.refine_replay(truth, spo, g["key"], g["origin"], band_rel=Q_RTOL / (1 - Q_RTOL))
+    _check_replay(oracle_mod, g, rep, "replay on oracle Q")
+    gd = dict(g, q_perp=g["q"])
+    compare_lines(gd, truth.records(g["key"]), Fo.cell, (-1, -1, 0), (1, 1, 1))
+    qa, keys = g["q"], g["key"]
     hot = (np.nan_to_num(qa[:-1]) > thr) | (np.nan_to_num(qa[1:]) > thr)
     gaps = np.diff(keys.astype(np.int64))
     if ndim == 2:  # full square lattice: every gap has cells to insert
-        assert not np.any(hot & (gaps > 1) & (iters < sp.max_iters))
+        assert not np.any(hot & (gaps > 1) & (g["iters"] < kw.get("max_iters", 64)))
 
 
 def test_bench_refined_map_full_size_sampled(qsl, oracle_mod):

@@ -314,3 +314,62 @@ def test_higher_order_euler_and_argument_checks(qsl, oracle_mod):
     with pytest.raises(qsl.QslError) as e:
         qsl.qsl_trace_seeds(Fn, np.array([[0.5, 0.5, 0.5]]), qsl.qsl_opts_default(interp_order=2))
     assert e.value.code == qsl.QSL_EINVAL
+
+
+@pytest.mark.parametrize("mode,lanes", [(0, 1), (0, 3), (1, 1), (1, 3)])
+def test_length_only_matches_oracle(qsl, oracle_mod, mode, lanes):
+    """Lengths only (qsl_opts.length_only, the mode of the refinement passes)
+    on the cell-wise kernels: one lane per line and the three-lane kernel, whose
+    normalise-first stages evaluate the cell's trilinear polynomial. Lengths
+    and end faces against the oracle's lengths-only trace; Q outputs are NaN."""
+    ch = inputs.random_charges(4, 2)
+    gf = inputs.charge_field(ch, 64, dtype=torch.float32)
+    F = _gpu_field(qsl, gf, mode)
+    Fo = _oracle_field(oracle_mod, gf, mode)
+    seeds = inputs.random_seeds(600, 41)
+    seeds[:200, 2] = 0.0     # footpoints on the bottom face
+    seeds[200:210, 1] = -1.0  # on the y- face
+    o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL, integrator=qsl.QSL_DOPRI5_CELL, line_lanes=lanes,
+                             length_only=1)
+    rec = qsl.lines_to_numpy(qsl.qsl_trace_seeds(F, torch.as_tensor(seeds).cuda(), o))
+    ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11, length_only=1))
+    assert np.all(np.isnan(rec["q_perp"])) and np.all(np.isnan(ref["q_perp"]))
+    rep = compare_lines(_rec_to_dict(rec), ref, 1.0 / 63, BOX_LO, BOX_HI)
+    assert rep["labels_checked"] > 550
+    assert np.array_equal(rec["status_f"], ref["st_f"]) and np.array_equal(rec["status_b"], ref["st_b"])
+
+
+@pytest.mark.parametrize("integ,lanes", [(0, 0), (2, 1), (2, 3)])
+def test_watchdog_expires_and_handle_stays_usable(qsl, oracle_mod, integ, lanes):
+    """The device watchdog (qsl_opts.timeout_s): with a limit of one
+    microsecond every tracer kernel stops its lines after its next check (every
+    64 loop iterations), lines still running end with QSL_LINE_TIMEOUT,
+    qsl_last_stats reports QSL_ETIMEOUT, and the next call on the same field
+    handle runs to completion. Nothing waits on anything: the kernels only
+    return early."""
+    ch = inputs.random_charges(4, 2)
+    gf = inputs.charge_field(ch, 64, dtype=torch.float32)
+    F = _gpu_field(qsl, gf, 0)
+    seeds = inputs.random_seeds(4000, 43)
+    seeds[:, 2] = 0.0
+    sd = torch.as_tensor(seeds).cuda()
+    o = qsl.qsl_opts_default(tol_abs=1e-9, tol_rel=1e-9, integrator=integ, line_lanes=lanes, retrace_q=0.0,
+                             timeout_s=1e-6)
+    rec = qsl.lines_to_numpy(qsl.qsl_trace_seeds(F, sd, o))
+    with pytest.raises(qsl.QslError) as e:
+        qsl.qsl_last_stats()
+    assert e.value.code == qsl.QSL_ETIMEOUT
+    st = np.concatenate([rec["status_f"], rec["status_b"]])
+    assert np.sum(st == qsl.QSL_LINE_TIMEOUT) > 100
+    assert np.all((st == qsl.QSL_LINE_TIMEOUT) | (st == qsl.QSL_LINE_OK))
+    timed = (rec["status_f"] == qsl.QSL_LINE_TIMEOUT) | (rec["status_b"] == qsl.QSL_LINE_TIMEOUT)
+    assert np.all(rec["face_f"][rec["status_f"] == qsl.QSL_LINE_TIMEOUT] == qsl.QSL_NO_FACE)
+    o.timeout_s = 0.0
+    rec2 = qsl.lines_to_numpy(qsl.qsl_trace_seeds(F, sd, o))
+    qsl.qsl_last_stats()  # no watchdog: no error
+    assert np.all(rec2["status_f"] == qsl.QSL_LINE_OK) and np.all(rec2["status_b"] == qsl.QSL_LINE_OK)
+    # lines the watchdog did not reach are the same as without it
+    done = ~timed
+    assert done.sum() > 0
+    assert np.array_equal(rec["face_f"][done], rec2["face_f"][done])
+    assert np.allclose(rec["length"][done], rec2["length"][done], rtol=1e-6)

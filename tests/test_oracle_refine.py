@@ -159,3 +159,62 @@ def test_q_threshold_criterion_refines_the_high_q_region(oracle_mod):
     # the FLL criterion ignores Q
     r3 = oracle_mod.refine_fn(ring_q_map, oracle_mod.refine_spec(criterion=0, tau=0.05, **base))
     assert len(r3["key"]) == (1 << p0) ** 2
+
+
+def ramp_map(x):
+    """A steep smooth front: pair differences |dL| take a continuum of values,
+    so some lie close to tau."""
+    r = np.hypot(x[:, 0] - 0.1, x[:, 1] + 0.05)
+    return 10.0 + 100.0 * np.tanh((r - 0.45) / 0.05), 1.0 + np.tanh((r - 0.45) / 0.05)
+
+
+def _noisy(fn, eps, seed):
+    """fn with a deterministic per-cell error of at most eps on q (relative) and L (absolute)."""
+    def g(x, keys):
+        q, L = fn(x)
+        u = np.array([((int(k) * 2654435761 + seed) % 1000003) / 1000003.0 for k in keys])
+        return q * (1 + eps * (2 * u - 1)), L + eps * (2 * u[::-1] - 1)
+    return g
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_replay_reproduces_a_noisy_run_from_exact_values(oracle_mod, ndim):
+    """The replay hook of the refinement driver: a run on values with an error
+    of at most eps is reproduced exactly by a run on the exact values when the
+    pairs within 2 eps of tau are decided by the noisy run's sample set; without
+    the band the two sets differ (the noise flips decisions), and with a zero
+    band and no tie keys the replay is the plain driver."""
+    if ndim == 2:
+        kw = dict(ndim=2, coarse_order=3, max_order=7, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), tau=0.05)
+    else:
+        kw = dict(ndim=3, coarse_order=2, max_order=4, extent=(16, 16, 8), lo=(-1, -1, 0), hi=(1, 1, 1), tau=0.05)
+    sp = oracle_mod.refine_spec(**kw)
+    exact = lambda x, k: ramp_map(x)
+    plain = oracle_mod.refine_fn(ramp_map, sp)
+    r0 = oracle_mod.refine_replay(exact, sp)
+    assert np.array_equal(r0["key"], plain["key"]) and r0["iters"] == plain["iters"]
+    eps = 0.01
+    noisy = oracle_mod.refine_replay(_noisy(ramp_map, eps, 7), sp)
+    assert not np.array_equal(noisy["key"], plain["key"])
+    rep = oracle_mod.refine_replay(exact, sp, noisy["key"], noisy["origin"], band_abs=2 * eps)
+    assert np.array_equal(rep["key"], noisy["key"]) and np.array_equal(rep["origin"], noisy["origin"])
+    # a band narrower than the error leaves decisions that only the noise explains
+    narrow = oracle_mod.refine_replay(exact, sp, noisy["key"], noisy["origin"], band_abs=0.2 * eps)
+    assert not np.array_equal(narrow["key"], noisy["key"])
+
+
+def test_replay_q_threshold_band(oracle_mod):
+    """Same for the Q-threshold criterion with a relative band on Q."""
+    kw = dict(ndim=2, coarse_order=3, max_order=7, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), tau=0.05,
+              criterion=1, q_threshold=60.0)
+    sp = oracle_mod.refine_spec(**kw)
+    exact = lambda x, k: ramp_map(x)
+    plain = oracle_mod.refine_fn(ramp_map, sp)
+    assert len(plain["key"]) > 64 * 1.5
+    eps = 0.02
+    noisy = oracle_mod.refine_replay(_noisy(ramp_map, eps, 3), sp)
+    assert not np.array_equal(noisy["key"], plain["key"])
+    rep = oracle_mod.refine_replay(exact, sp, noisy["key"], noisy["origin"], band_rel=1.01 * eps / (1 - eps))
+    assert np.array_equal(rep["key"], noisy["key"])
+    narrow = oracle_mod.refine_replay(exact, sp, noisy["key"], noisy["origin"], band_rel=0.1 * eps)
+    assert not np.array_equal(narrow["key"], noisy["key"])

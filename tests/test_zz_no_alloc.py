@@ -47,6 +47,34 @@ def test_noalloc_matches_trace_seeds_twice(integrator):
         assert _close(got["q_foot"], want["q_foot"], Q_RTOL)
 
 
+def test_noalloc_leaves_device_memory_unchanged():
+    """Free device memory (cudaMemGetInfo) is the same before and after two
+    calls, once the first call has looked up the array's address and loaded
+    the kernels; the same check catches qsl_trace_seeds, whose scratch comes
+    from the library's stream-ordered pool (kept cached after the call)."""
+    from paper_1609_00724_gb300 import qsl
+    F = _field(qsl)
+    o = qsl.qsl_opts_default(tol_abs=1e-7, tol_rel=1e-7, integrator=2, retrace_q=0.0)
+    n = 5000
+    sd = torch.as_tensor(inputs.random_seeds(n, 33)).cuda()
+    out = torch.empty(n * qsl.QSL_LINE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    qsl.qsl_trace_seeds_noalloc(F, sd, o, out)  # first call on this device
+    torch.cuda.synchronize()
+    qsl.qsl_trim_pool()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        qsl.qsl_trace_seeds_noalloc(F, sd, o, out)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
+    qsl.qsl_trace_seeds(F, sd, o, out=out)
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    assert free2 < free1
+    qsl.qsl_trim_pool()
+
+
 def test_noalloc_rejects_oversize_and_host_memory():
     from paper_1609_00724_gb300 import qsl
     F = _field(qsl)
