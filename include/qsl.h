@@ -256,9 +256,12 @@ typedef struct qsl_samples {
  * qsl_q_volume_3d over the effective lattice. With samples->count > 0 the
  * call resumes from those (sorted) samples instead of the coarse pass.
  * QSL_ECAPACITY when the capacity is reached (samples so far are valid).
- * With the FLL-jump criterion the refinement passes trace lengths only (the
- * criterion reads L) and the pass samples' Q, L, end faces and status come
- * from one tangent-space trace after the last iteration. */
+ * With the FLL-jump criterion and QSL_DOPRI5_CELL on a uniform grid the
+ * refinement passes trace lengths only (the criterion reads L) and the pass
+ * samples' Q, L, end faces and status come from one tangent-space trace after
+ * the last iteration; the Cash-Karp stepper, whose lengths-only traces miss
+ * the length accuracy of its tangent-space ones, traces its passes in
+ * tangent space. */
 int qsl_refine(const qsl_field* field, const qsl_refine_spec* spec, const qsl_opts* opts, qsl_samples* samples,
                float* q_grid, float* l_grid, int mem, void* stream);
 

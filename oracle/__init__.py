@@ -290,12 +290,13 @@ def refine_fn(fn, spec, capacity=None):
 
 
 _EVAL_KFN = C.CFUNCTYPE(None, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_double),
-                        C.POINTER(C.c_double))
+                        C.POINTER(C.c_double), C.POINTER(C.c_int32))
 
 
 def refine_replay(fn, spec, tie_keys=(), tie_origin=(), band_abs=0.0, band_rel=0.0, capacity=None):
     """Refinement driver (test hook) with values from fn(xyz[n,3], keys[n]) ->
-    (q[n], L[n]); a pair whose criterion value lies within the band of the
+    (q[n], L[n]) or (q[n], L[n], unsure[n]); a pair with an unsure sample, or
+    whose criterion value lies within the band of the
     threshold (| |dL| - tau | <= band_abs + band_rel max(|L|), or Q within
     band_rel of q_threshold) is refined exactly when another run added its new
     cell in the same pass (tie_keys sorted, tie_origin the pass that added each:
@@ -314,12 +315,14 @@ def refine_replay(fn, spec, tie_keys=(), tie_origin=(), band_abs=0.0, band_rel=0
     order = np.argsort(tk, kind="stable")
     tk, to = np.ascontiguousarray(tk[order]), np.ascontiguousarray(to[order])
 
-    def cb(n, xyz, keys, q, L):
+    def cb(n, xyz, keys, q, L, unsure):
         x = np.ctypeslib.as_array(xyz, shape=(n, 3)).copy()
         k = np.ctypeslib.as_array(keys, shape=(n,)).copy()
-        qq, ll = fn(x, k)
-        np.ctypeslib.as_array(q, shape=(n,))[:] = qq
-        np.ctypeslib.as_array(L, shape=(n,))[:] = ll
+        r = fn(x, k)
+        np.ctypeslib.as_array(q, shape=(n,))[:] = r[0]
+        np.ctypeslib.as_array(L, shape=(n,))[:] = r[1]
+        if len(r) > 2:
+            np.ctypeslib.as_array(unsure, shape=(n,))[:] = np.asarray(r[2], dtype=np.int32)
 
     cfn = _EVAL_KFN(cb)
     key = np.zeros(capacity, dtype=np.uint64)

@@ -1152,6 +1152,7 @@ struct Sample {
   double q, L;
   int face_f, face_b, st_f, st_b;
   int origin;  // pass that added it: 0 coarse pass, 2i + 1 / 2i + 2 pass A / B of iteration i
+  int unsure;  // test hook: the evaluator could not determine the value
 };
 
 // Position of the centre of effective-lattice cell c.
@@ -1175,8 +1176,9 @@ struct Evaluator {
   const Field* F = nullptr;
   const Opts* o = nullptr;
   void (*fn)(int64_t, const double*, double*, double*) = nullptr;  // test hook: (n, xyz, q, L)
-  // test hook with the samples' keys: (n, xyz, keys, q, L)
-  void (*fnk)(int64_t, const double*, const uint64_t*, double*, double*) = nullptr;
+  // test hook with the samples' keys: (n, xyz, keys, q, L, unsure); unsure[i] != 0
+  // marks a sample whose value the caller cannot determine (see Arbiter)
+  void (*fnk)(int64_t, const double*, const uint64_t*, double*, double*, int32_t*) = nullptr;
 };
 
 // Test hook of the refinement driver (no counterpart in the paper): pairs
@@ -1190,6 +1192,9 @@ struct Evaluator {
 //  - Q threshold: a sample is ambiguous when its Q is finite and
 //    |Q / q_threshold - 1| <= band_rel; a pair is ambiguous when neither sample
 //    is clearly above the threshold and one of them is ambiguous.
+//  - Either criterion: a pair is ambiguous when the evaluator marks one of its
+//    samples as undetermined (a line whose end changes under a perturbation of
+//    its seed below the other run's error).
 struct Arbiter {
   double band_abs, band_rel;
   const uint64_t* keys;   // sorted ascending
@@ -1266,10 +1271,11 @@ void trace_samples(const Evaluator& ev, const RefineSpec& s, std::vector<Sample>
   }
   if (ev.fn || ev.fnk) {
     std::vector<double> q(v.size()), L(v.size());
+    std::vector<int32_t> unsure(v.size(), 0);
     if (ev.fnk) {
       std::vector<uint64_t> keys(v.size());
       for (size_t i = 0; i < v.size(); ++i) keys[i] = v[i].key;
-      ev.fnk((int64_t)v.size(), seeds.data(), keys.data(), q.data(), L.data());
+      ev.fnk((int64_t)v.size(), seeds.data(), keys.data(), q.data(), L.data(), unsure.data());
     } else {
       ev.fn((int64_t)v.size(), seeds.data(), q.data(), L.data());
     }
@@ -1278,6 +1284,7 @@ void trace_samples(const Evaluator& ev, const RefineSpec& s, std::vector<Sample>
       v[i].L = L[i];
       v[i].face_f = v[i].face_b = NO_FACE;
       v[i].st_f = v[i].st_b = ST_OK;
+      v[i].unsure = unsure[i];
     }
     return;
   }
@@ -1333,6 +1340,7 @@ static bool pair_flagged(const RefineSpec& s, const Sample& A, const Sample& B) 
 // The decision with the test hook: the comparison, or, for a pair within the
 // band, whether its new cell `cand` is in the arbiter's key set.
 static bool pair_ambiguous(const RefineSpec& s, const Sample& A, const Sample& B, const Arbiter& arb) {
+  if (A.unsure || B.unsure) return true;
   if (s.criterion == 1) {
     auto clear_above = [&](double q) { return std::isfinite(q) && q / s.q_threshold - 1.0 > arb.band_rel; };
     auto near = [&](double q) { return std::isfinite(q) && std::fabs(q / s.q_threshold - 1.0) <= arb.band_rel; };
@@ -1489,7 +1497,7 @@ int64_t qslref_refine_fn(void (*fn)(int64_t, const double*, double*, double*), c
 // Replay of a sample set (test hook, see Arbiter): the driver with values from
 // fn(n, xyz, keys, q, L), and pairs within the band of the threshold decided by
 // membership of their new cell in tie_keys (sorted). Outputs as qslref_refine_fn.
-int64_t qslref_refine_replay(void (*fn)(int64_t, const double*, const uint64_t*, double*, double*),
+int64_t qslref_refine_replay(void (*fn)(int64_t, const double*, const uint64_t*, double*, double*, int32_t*),
                              const RefineSpec* sp, double band_abs, double band_rel, const uint64_t* tie_keys,
                              const int32_t* tie_origin, int64_t n_tie, int64_t capacity, uint64_t* key,
                              double* q, double* L, int32_t* origin, int32_t* iters_out,

@@ -183,8 +183,9 @@ __global__ void pack_kernel(const T* bx, const T* by, const T* bz, size_t n, int
       B[0] = B[1] = B[2] = 0;
     }
     double m = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    const double rm = m > 0 ? 1.0 / m : 0.0;  // one FP64 division per vertex
     double o[3];
-    for (int a = 0; a < 3; ++a) o[a] = raw ? B[a] : (m > 0 ? B[a] / m : 0.0);
+    for (int a = 0; a < 3; ++a) o[a] = raw ? B[a] : B[a] * rm;
     v32[i] = make_float4((float)o[0], (float)o[1], (float)o[2], (float)m);
     v64[i] = make_double4_32a(o[0], o[1], o[2], m);
   }
@@ -268,15 +269,20 @@ int qsl_load_field(const void* bx, const void* by, const void* bz, int dtype, in
   void* staged[3] = {nullptr, nullptr, nullptr};
   int* bad = nullptr;
   int bad_h = 0;
+  // every buffer comes from the library's stream-ordered pool on `stream`, so
+  // loading fields of the same size again reuses cached blocks (no driver
+  // allocation); releases go back to the pool on the same stream
   auto fail = [&](int code) {
+    cudaStreamSynchronize(stream);
     for (int a = 0; a < 3; ++a) {
-      if (staged[a]) cudaFree(staged[a]);
-      if (f->axis64[a]) cudaFree(f->axis64[a]);
-      if (f->axis32[a]) cudaFree(f->axis32[a]);
+      if (staged[a]) cudaFreeAsync(staged[a], stream);
+      if (f->axis64[a]) cudaFreeAsync(f->axis64[a], stream);
+      if (f->axis32[a]) cudaFreeAsync(f->axis32[a], stream);
     }
-    if (bad) cudaFree(bad);
-    if (f->v32) cudaFree(f->v32);
-    if (f->v64) cudaFree(f->v64);
+    if (bad) cudaFreeAsync(bad, stream);
+    if (f->v32) cudaFreeAsync(f->v32, stream);
+    if (f->v64) cudaFreeAsync(f->v64, stream);
+    cudaStreamSynchronize(stream);
     delete f;
     return code;
   };
@@ -288,21 +294,22 @@ int qsl_load_field(const void* bx, const void* by, const void* bz, int dtype, in
       return fail(e_ == cudaErrorMemoryAllocation ? QSL_ENOMEM : QSL_ECUDA);                   \
     }                                                                                          \
   } while (0)
-  TRY(cudaMalloc((void**)&f->v32, N * sizeof(float4)));
-  TRY(cudaMalloc((void**)&f->v64, N * sizeof(double4_32a)));
-  TRY(cudaMalloc((void**)&bad, sizeof(int)));
+  TRY(qsl::alloc_async((void**)&f->v32, N * sizeof(float4), stream));
+  TRY(qsl::alloc_async((void**)&f->v64, N * sizeof(double4_32a), stream));
+  TRY(qsl::alloc_async((void**)&bad, sizeof(int), stream));
   TRY(cudaMemsetAsync(bad, 0, sizeof(int), stream));
   for (int a = 0; a < 3; ++a) {
-    TRY(cudaMalloc((void**)&f->axis64[a], n[a] * sizeof(double)));
-    TRY(cudaMalloc((void**)&f->axis32[a], n[a] * sizeof(float)));
+    TRY(qsl::alloc_async((void**)&f->axis64[a], n[a] * sizeof(double), stream));
+    TRY(qsl::alloc_async((void**)&f->axis32[a], n[a] * sizeof(float), stream));
     TRY(cudaMemcpyAsync(f->axis64[a], ax[a], n[a] * sizeof(double), cudaMemcpyHostToDevice, stream));
     float* tmp = new float[n[a]];
     for (int i = 0; i < n[a]; ++i) tmp[i] = (float)ax[a][i];
-    cudaError_t e = cudaMemcpy(f->axis32[a], tmp, n[a] * sizeof(float), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpyAsync(f->axis32[a], tmp, n[a] * sizeof(float), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // tmp is pageable and freed next
     delete[] tmp;
     TRY(e);
     if (mem == QSL_MEM_HOST) {
-      TRY(cudaMalloc(&staged[a], N * esz));
+      TRY(qsl::alloc_async(&staged[a], N * esz, stream));
       TRY(cudaMemcpyAsync(staged[a], src[a], N * esz, cudaMemcpyHostToDevice, stream));
     }
   }
@@ -322,14 +329,14 @@ int qsl_load_field(const void* bx, const void* by, const void* bz, int dtype, in
   qsl::count_launch();
   TRY(cudaGetLastError());
   TRY(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, stream));
-  TRY(cudaStreamSynchronize(stream));
   for (int a = 0; a < 3; ++a)
     if (staged[a]) {
-      cudaFree(staged[a]);
+      TRY(cudaFreeAsync(staged[a], stream));
       staged[a] = nullptr;
     }
-  cudaFree(bad);
+  TRY(cudaFreeAsync(bad, stream));
   bad = nullptr;
+  TRY(cudaStreamSynchronize(stream));
   if (bad_h) {
     set_error("field contains non-finite values");
     return fail(QSL_ENONFINITE);
@@ -341,12 +348,17 @@ int qsl_load_field(const void* bx, const void* by, const void* bz, int dtype, in
 
 void qsl_free_field(qsl_field* f) {
   if (!f) return;
-  cudaFree(f->v32);
-  cudaFree(f->v64);
-  for (int a = 0; a < 3; ++a) {
-    cudaFree(f->axis64[a]);
-    cudaFree(f->axis32[a]);
-  }
+  // work on any stream may still read the field: wait for the device to be
+  // idle (as cudaFree does), then hand the blocks back to the pool
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != f->device) cudaSetDevice(f->device);
+  cudaDeviceSynchronize();
+  void* bufs[8] = {f->v32, f->v64, f->axis64[0], f->axis64[1], f->axis64[2], f->axis32[0], f->axis32[1], f->axis32[2]};
+  for (void* b : bufs)
+    if (b) cudaFreeAsync(b, 0);
+  cudaStreamSynchronize(0);
+  if (cur != f->device) cudaSetDevice(cur);
   delete f;
 }
 

@@ -173,7 +173,7 @@ __device__ __forceinline__ bool pair_flagged(const Criterion& cr, float va, floa
 }
 
 __global__ void flag_pairs_kernel(const uint64_t* __restrict__ keys, const float* __restrict__ V, int64_t n,
-                                  Criterion cr, int nd, int bits, Region reg, uint64_t* cand) {
+                                  Criterion cr, int nd, int bits, Region reg, uint64_t* cand, int64_t* flags) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + 1 < n; i += (int64_t)gridDim.x * blockDim.x) {
     uint64_t a = keys[i], b = keys[i + 1];
     uint64_t out = NONE;
@@ -182,6 +182,7 @@ __global__ void flag_pairs_kernel(const uint64_t* __restrict__ keys, const float
       if (nearest_in_region(a + (b - a) / 2, a, b, nd, bits, reg, &got)) out = got;
     }
     cand[i] = out;
+    flags[i] = out != NONE;
   }
 }
 
@@ -199,7 +200,8 @@ __global__ void shift_keys_kernel(const uint64_t* __restrict__ keys, int64_t n, 
 
 // Pass B flags along the shifted curve; candidates are keys on the original curve.
 __global__ void flag_shifted_kernel(const uint64_t* __restrict__ skeys, const float* __restrict__ sV, int64_t n,
-                                    Criterion cr, int nd, int bits, uint32_t S, Region sreg, uint64_t* cand) {
+                                    Criterion cr, int nd, int bits, uint32_t S, Region sreg, uint64_t* cand,
+                                    int64_t* flags) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i + 1 < n; i += (int64_t)gridDim.x * blockDim.x) {
     uint64_t a = skeys[i], b = skeys[i + 1];
     uint64_t out = NONE;
@@ -213,15 +215,33 @@ __global__ void flag_shifted_kernel(const uint64_t* __restrict__ skeys, const fl
       }
     }
     cand[i] = out;
+    flags[i] = out != NONE;
   }
 }
 
-// Stream compaction of candidates != NONE (exclusive scan of flags).
-__global__ void cand_flags_kernel(const uint64_t* __restrict__ cand, int64_t n, int64_t* flags) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    flags[i] = cand[i] != NONE;
+// Shifted keys of samples given by key, with their criterion values looked up
+// in the sorted set (key[0..n), V), perm = identity.
+__global__ void shift_lookup_kernel(const uint64_t* __restrict__ qkeys, int64_t m, int nd, int bits, uint32_t S,
+                                    const uint64_t* __restrict__ key, int64_t n, const float* __restrict__ V,
+                                    uint64_t* skeys, float* vals, int64_t* perm) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = qkeys[i];
+    uint32_t c[3] = {0, 0, 0};
+    hilbert_coords_dev(k, nd, bits, c);
+    for (int a = 0; a < nd; ++a) c[a] += S;
+    skeys[i] = hilbert_key_dev(c, nd, bits + 1);
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if (key[mid] < k) lo = mid + 1;
+      else hi = mid;
+    }
+    vals[i] = (lo < n && key[lo] == k) ? V[lo] : __int_as_float(0x7fc00000);
+    perm[i] = i;
+  }
 }
 
+// Stream compaction of candidates != NONE: scatter by the exclusive scan of their flags.
 __global__ void cand_scatter_kernel(const uint64_t* __restrict__ cand, const int64_t* __restrict__ pos, int64_t n,
                                     int64_t limit, uint64_t* out, int64_t* count) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -374,56 +394,62 @@ __global__ void convert_kernel(const uint64_t* __restrict__ keys, const float* _
 
 // Converter for an output lattice equal to the sample lattice (one lattice
 // cell per output cell): same rule as convert_kernel, tiled along the curve.
-// A block takes CK consecutive curve keys, finds its samples (and one
-// neighbour on each side) with one binary search, stages their keys, values,
-// log10 values and key-gap reciprocals in shared memory, then resolves each
-// key with a short search there. Keys outside the extent are skipped.
+// A block takes CK consecutive curve keys; its samples (and one neighbour on
+// each side) are found from the chunk bounds (one binary search per chunk,
+// all chunks in parallel, in chunk_bounds_kernel), staged in shared memory
+// with their log10 values (FP64) and key-gap reciprocals, and each key is
+// resolved there. Keys outside the extent are skipped. Q is interpolated in
+// log10 in FP64 and the power evaluated as 2^(integer part) * 2^(fraction),
+// the fraction by exp2f and the integer part exactly (ldexpf): a few FP32
+// ulps, against one FP64 exp10 per empty cell.
 constexpr int CK = 1024;
 constexpr int CS = CK + 2;
+
+__global__ void chunk_bounds_kernel(const uint64_t* __restrict__ keys, int64_t n, uint64_t nchunks,
+                                    int64_t* __restrict__ start) {
+  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c <= nchunks; c += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k0 = c * CK;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if (keys[mid] < k0) lo = mid + 1;
+      else hi = mid;
+    }
+    start[c] = lo;
+  }
+}
+
+__device__ __forceinline__ float pow10_of(double x) {
+  if (!isfinite(x)) return (float)exp10(x);
+  const double y = x * 3.321928094887362347870319429489390175864831393;  // log2(10)
+  const double yi = floor(y);
+  return ldexpf(exp2f((float)(y - yi)), (int)yi);
+}
 
 __global__ void __launch_bounds__(256) convert_tiled_kernel(const uint64_t* __restrict__ keys,
                                                             const float* __restrict__ vals, int64_t n, int nd,
                                                             int bits, int e0, int e1, int e2, int log_interp,
-                                                            uint64_t nkeys, float* out) {
+                                                            uint64_t nkeys, const int64_t* __restrict__ start,
+                                                            float* out) {
   __shared__ uint64_t sk[CS];
   __shared__ float sv[CS];
   __shared__ double sl[CS];
   __shared__ double sinv[CS];
-  __shared__ int64_t s_lo;
-  __shared__ int s_cnt;
   for (uint64_t c0 = (uint64_t)blockIdx.x * CK; c0 < nkeys; c0 += (uint64_t)gridDim.x * CK) {
     const uint64_t c1 = c0 + CK < nkeys ? c0 + CK : nkeys;
-    if (threadIdx.x == 0) {
-      int64_t lo = 0, hi = n;
-      while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (keys[mid] < c0) lo = mid + 1;
-        else hi = mid;
-      }
-      int64_t a = lo;
-      hi = n;
-      while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (keys[mid] < c1) lo = mid + 1;
-        else hi = mid;
-      }
-      int64_t b = lo;
-      if (a > 0) a -= 1;  // predecessor of the chunk
-      if (b < n) b += 1;  // successor of the chunk
-      s_lo = a;
-      s_cnt = (int)(b - a);
-    }
-    __syncthreads();
-    const int cnt = s_cnt;
-    const int64_t base = s_lo;
+    const uint64_t ci = c0 / CK;
+    int64_t a = start[ci], b = start[ci + 1];
+    if (a > 0) a -= 1;  // predecessor of the chunk
+    if (b < n) b += 1;  // successor of the chunk
+    const int cnt = (int)(b - a);
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      sk[i] = keys[base + i];
-      sv[i] = vals[base + i];
+      sk[i] = keys[a + i];
+      sv[i] = vals[a + i];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
       if (log_interp) sl[i] = log10((double)sv[i]);
-      if (i + 1 < cnt) sinv[i] = 1.0 / ((double)sk[i + 1] - (double)sk[i]);
+      if (i + 1 < cnt) sinv[i] = 1.0 / (double)(sk[i + 1] - sk[i]);
     }
     __syncthreads();
     for (uint64_t k = c0 + threadIdx.x; k < c1; k += blockDim.x) {
@@ -446,9 +472,9 @@ __global__ void __launch_bounds__(256) convert_tiled_kernel(const uint64_t* __re
         } else if (j < 0) {
           res = sv[0];  // before the first sample
         } else {
-          const double t = ((double)k - (double)sk[j]) * sinv[j];
+          const double t = (double)(k - sk[j]) * sinv[j];
           if (log_interp)
-            res = (float)exp10((1 - t) * sl[j] + t * sl[j + 1]);
+            res = pow10_of((1 - t) * sl[j] + t * sl[j + 1]);
           else
             res = (float)((1 - t) * (double)sv[j] + t * (double)sv[j + 1]);
         }
@@ -527,10 +553,17 @@ int convert_device(const uint64_t* keys, const float* vals, int64_t n, int nd, i
     QSL_CHECK_CUDA(cudaGetDevice(&dev));
     QSL_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     uint64_t chunks = (nkeys + CK - 1) / CK;
-    int blocks = chunks < (uint64_t)sms * 8 ? (int)chunks : sms * 8;
-    convert_tiled_kernel<<<blocks, 256, 0, s>>>(keys, vals, n, nd, p, eo[0], eo[1], eo[2], log_interp, nkeys, out);
+    int64_t* start = nullptr;
+    QSL_CHECK_CUDA(qsl::alloc_async((void**)&start, (chunks + 1) * sizeof(int64_t), s));
+    chunk_bounds_kernel<<<grid_for((int64_t)chunks + 1), 256, 0, s>>>(keys, n, chunks, start);
     qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
+    int blocks = chunks < (uint64_t)sms * 8 ? (int)chunks : sms * 8;
+    convert_tiled_kernel<<<blocks, 256, 0, s>>>(keys, vals, n, nd, p, eo[0], eo[1], eo[2], log_interp, nkeys, start,
+                                                out);
+    qsl::count_launch();
+    QSL_CHECK_CUDA(cudaGetLastError());
+    QSL_CHECK_CUDA(cudaFreeAsync(start, s));
   } else if (N > 0) {
     convert_kernel<<<grid_for(N), 256, 0, s>>>(keys, vals, n, nd, p, d, eo[0], eo[1], eo[2], log_interp, out);
     qsl::count_launch();
@@ -553,6 +586,7 @@ struct RefineClock {
   int iters = 0;
   static constexpr int kSnaps = 512;
   DeviceStats* snap = nullptr;  // device, one per trace call (the first kSnaps)
+  int64_t* count_h = nullptr;   // pinned host word for the per-pass sample counts
   cudaStream_t stream = nullptr;
   bool valid = false;
   int device = -1;
@@ -583,6 +617,7 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
       rk.device = dev;
     }
     if (!rk.snap) QSL_CHECK_CUDA(cudaMalloc((void**)&rk.snap, sizeof(DeviceStats) * RefineClock::kSnaps));
+    if (!rk.count_h) QSL_CHECK_CUDA(cudaMallocHost((void**)&rk.count_h, sizeof(int64_t)));
   }
   rk.used = 0;
   rk.kind.clear();
@@ -602,6 +637,18 @@ int refine_device(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts*
   rk.valid = true;
   return rc_all;
 }
+
+// The sorted sample set sits in one of two sets of arrays (the caller's and a
+// scratch set): each merge reads one and writes the other, and the caller's
+// arrays receive the set once at the end if it ended in the scratch set.
+struct SampleArrays {
+  uint64_t* key;
+  float* q;
+  float* L;
+  uint8_t* fa;
+  uint8_t* st;
+  int32_t* org;  // optional
+};
 
 int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o, qsl_samples* smp,
                 float* q_grid, float* l_grid, int mem_proposal, cudaStream_t s) {
@@ -635,13 +682,8 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
   int64_t cap = smp->capacity;
   int64_t n = smp->count;
   int rc;
-  int64_t* cnt = nullptr;  // device counter
-  int64_t* cnt_h = nullptr;
-  QSL_CHECK_CUDA(cudaMallocHost((void**)&cnt_h, sizeof(int64_t)));
-  struct HostFree {
-    int64_t* p;
-    ~HostFree() { cudaFreeHost(p); }
-  } hf{cnt_h};
+  int64_t* cnt = nullptr;        // device counter
+  int64_t* cnt_h = rk.count_h;   // pinned host copy (kept per thread and device)
   if ((rc = sc.alloc(&cnt, 1))) return rc;
   int64_t traced = 0;
   bool cap_hit = false;
@@ -649,7 +691,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
   // temporaries sized to the capacity
   uint64_t *kA = nullptr, *cand = nullptr, *sk = nullptr, *sk2 = nullptr;
   int64_t *perm = nullptr, *perm2 = nullptr, *flags = nullptr, *pos = nullptr;
-  float *q2 = nullptr, *L2 = nullptr;
+  float *q2 = nullptr, *L2 = nullptr, *pvals = nullptr;
   uint8_t *fa2 = nullptr, *st2 = nullptr;
   int32_t* org2 = nullptr;
   if ((rc = sc.alloc(&kA, cap)) || (rc = sc.alloc(&cand, cap)) || (rc = sc.alloc(&sk, cap)) ||
@@ -658,14 +700,18 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
       (rc = sc.alloc(&L2, cap)) || (rc = sc.alloc(&fa2, 2 * cap)) || (rc = sc.alloc(&st2, cap)))
     return rc;
   if (smp->origin && (rc = sc.alloc(&org2, cap))) return rc;
+  const SampleArrays user{smp->key, smp->q, smp->length, smp->faces, smp->status, smp->origin};
+  SampleArrays cur = user;                                // the set: rows [0, n) sorted, new rows after
+  SampleArrays alt{kA, q2, L2, fa2, st2, smp->origin ? org2 : nullptr};  // the other array set
 
   // the criterion and the per-sample value it reads (L or Q)
   Criterion crit{sp->criterion, sp->tau, sp->q_threshold};
-  auto crit_values = [&]() -> float* { return sp->criterion == QSL_REFINE_Q_THRESHOLD ? smp->q : smp->length; };
+  auto crit_values = [&]() -> float* { return sp->criterion == QSL_REFINE_Q_THRESHOLD ? cur.q : cur.L; };
 
   // Shifted-curve orders (shifted key, criterion value) for the two alternating
-  // shifts of pass B, built on first use and then kept sorted by merging each
-  // batch of new samples (as the main order is), so no pass re-sorts the set.
+  // shifts of pass B, built on first use and then kept sorted: before each use
+  // the samples added since the last one are sorted and merged in at once, so
+  // no pass re-sorts the set.
   const uint32_t half = 1u << (p - 1 >= 0 ? p - 1 : 0);
   const uint32_t dsh = (uint32_t)(R / 2 > 1 ? R / 2 : 1);
   const uint32_t shiftS[2] = {half + dsh, half - (dsh < half ? dsh : half)};
@@ -674,11 +720,13 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
   uint64_t* ord_ktmp = nullptr;
   float* ord_Ltmp = nullptr;
   bool ord_built[2] = {false, false};
+  int64_t ord_n[2] = {0, 0}, ord_mark[2] = {0, 0};  // entries; pass samples (pkeys) merged so far
   int64_t* nperm = nullptr;
   uint64_t* nkey = nullptr;
   if (sp->shift) {
     if ((rc = sc.alloc(&ord_key[0], cap)) || (rc = sc.alloc(&ord_key[1], cap)) || (rc = sc.alloc(&ord_L[0], cap)) ||
-        (rc = sc.alloc(&ord_L[1], cap)) || (rc = sc.alloc(&ord_ktmp, cap)) || (rc = sc.alloc(&ord_Ltmp, cap)))
+        (rc = sc.alloc(&ord_L[1], cap)) || (rc = sc.alloc(&ord_ktmp, cap)) || (rc = sc.alloc(&ord_Ltmp, cap)) ||
+        (rc = sc.alloc(&pvals, cap)))
       return rc;
   }
   if ((rc = sc.alloc(&nperm, cap)) || (rc = sc.alloc(&nkey, cap))) return rc;
@@ -687,29 +735,34 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
   // length-only mode, and one launch after the last iteration traces every
   // pass sample with the deviation equations; its Q, L, end faces and status
   // (FP64 retrace above retrace_q included) replace the pass values, whose
-  // lengths only decided the refinement.
-  const bool decouple = sp->criterion == QSL_REFINE_FLL_JUMP && !o->length_only;
+  // lengths only decided the refinement. Only the cell-wise integrator keeps
+  // its length accuracy in length-only mode: the Cash-Karp stepper across the
+  // kinks of the trilinear field is held to its tolerance by the deviation
+  // components, and without them its lengths are tens of times less accurate,
+  // so its passes trace the deviations too.
+  const bool decouple = sp->criterion == QSL_REFINE_FLL_JUMP && !o->length_only &&
+                        o->integrator == QSL_DOPRI5_CELL && f->uniform;
   qsl_opts o_len = *o;
   o_len.length_only = 1;
-  uint64_t* pkeys = nullptr;
+  uint64_t* pkeys = nullptr;  // keys of the pass samples in the order traced
   int64_t n_pass = 0;
-  if (decouple && (rc = sc.alloc(&pkeys, cap))) return rc;
+  if ((rc = sc.alloc(&pkeys, cap))) return rc;
 
-  // trace samples [off, off + m) (keys already written; `sorted`: in key
-  // order) and merge them into the sorted set and into the built orders
+  // trace samples [off, off + m) of the current arrays (keys already written;
+  // `sorted`: in key order) and merge them into the sorted set
   auto trace_and_merge = [&](int64_t off, int64_t m, bool sorted, int32_t pass_id) -> int {
     if (m <= 0) return QSL_OK;
-    if (smp->origin) {
-      fill_i32_kernel<<<grid_for(m), 256, 0, s>>>(smp->origin + off, m, pass_id);
+    if (cur.org) {
+      fill_i32_kernel<<<grid_for(m), 256, 0, s>>>(cur.org + off, m, pass_id);
       qsl::count_launch();
     }
     SeedSource s2 = src;
-    s2.keys = smp->key + off;
+    s2.keys = cur.key + off;
     LineOutputs lo{};
-    lo.q = smp->q + off;
-    lo.length = smp->length + off;
-    lo.faces = smp->faces + 2 * off;
-    lo.status = smp->status + off;
+    lo.q = cur.q + off;
+    lo.length = cur.L + off;
+    lo.faces = cur.fa + 2 * off;
+    lo.status = cur.st + off;
     lo.q_form = o->q_form;
     lo.skip_open = o->skip_open;
     cudaEvent_t e0, e1;
@@ -720,9 +773,9 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
     r = run_lines(f, s2, m, len_only ? &o_len : o, lo, s);
     if (r) return r;
     QSL_CHECK_CUDA(cudaEventRecord(e1, s));
-    if (len_only) {
+    if (trace_kind == 1) {
       QSL_CHECK_CUDA(
-          cudaMemcpyAsync(pkeys + n_pass, smp->key + off, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+          cudaMemcpyAsync(pkeys + n_pass, cur.key + off, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
       n_pass += m;
     }
     if (rk.kind.size() < (size_t)RefineClock::kSnaps)
@@ -732,56 +785,32 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
     rk.lines.push_back(m);
     traced += m;
     // the batch in key order
-    const uint64_t* bkey = smp->key + off;
+    const uint64_t* bkey = cur.key + off;
     const int64_t* bperm = nullptr;
     if (!sorted) {
       iota_kernel<<<grid_for(m), 256, 0, s>>>(perm, m);
       qsl::count_launch();
-      if ((r = sort_pairs(smp->key + off, nkey, perm, nperm, m, nd * p, s))) return r;
+      if ((r = sort_pairs(cur.key + off, nkey, perm, nperm, m, nd * p, s))) return r;
       bkey = nkey;
       bperm = nperm;
     }
-    // shifted orders
-    for (int b = 0; b < 2; ++b) {
-      if (!ord_built[b]) continue;
-      shift_keys_kernel<<<grid_for(m), 256, 0, s>>>(smp->key + off, m, nd, p, shiftS[b], sk, perm);
-      qsl::count_launch();
-      QSL_CHECK_CUDA(cudaGetLastError());
-      if ((r = sort_pairs(sk, sk2, perm, perm2, m, nd * (p + 1), s))) return r;
-      merge_order_kernel<<<grid_for(off + m), 256, 0, s>>>(ord_key[b], ord_L[b], off, sk2, perm2, crit_values() + off,
-                                                            m, ord_ktmp, ord_Ltmp);
-      qsl::count_launch();
-      QSL_CHECK_CUDA(cudaGetLastError());
-      std::swap(ord_key[b], ord_ktmp);
-      std::swap(ord_L[b], ord_Ltmp);
-    }
-    // main order
     int64_t tot = off + m;
-    merge_samples_kernel<<<grid_for(tot), 256, 0, s>>>(smp->key, smp->q, smp->length, smp->faces, smp->status,
-                                                        smp->origin, off, bkey, bperm, m, kA, q2, L2, fa2, st2,
-                                                        org2);
+    merge_samples_kernel<<<grid_for(tot), 256, 0, s>>>(cur.key, cur.q, cur.L, cur.fa, cur.st, cur.org, off, bkey,
+                                                        bperm, m, alt.key, alt.q, alt.L, alt.fa, alt.st, alt.org);
     qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
-    if (smp->origin)
-      QSL_CHECK_CUDA(cudaMemcpyAsync(smp->origin, org2, tot * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, kA, tot * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->q, q2, tot * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->length, L2, tot * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->faces, fa2, 2 * tot, cudaMemcpyDeviceToDevice, s));
-    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->status, st2, tot, cudaMemcpyDeviceToDevice, s));
+    std::swap(cur, alt);
     return QSL_OK;
   };
 
-  // compact candidates cand[0..m) into smp->key[n..), returns the number added
+  // compact candidates cand[0..m) (flags[i] = cand[i] is one) into the rows
+  // after the set, returns the number added
   auto compact = [&](int64_t m, int64_t* added) -> int {
     *added = 0;
     if (m <= 0) return QSL_OK;
-    cand_flags_kernel<<<grid_for(m), 256, 0, s>>>(cand, m, flags);
-    qsl::count_launch();
-    QSL_CHECK_CUDA(cudaGetLastError());
     int r = exclusive_sum(flags, pos, m, s);
     if (r) return r;
-    cand_scatter_kernel<<<grid_for(m), 256, 0, s>>>(cand, pos, m, cap - n, smp->key + n, cnt);
+    cand_scatter_kernel<<<grid_for(m), 256, 0, s>>>(cand, pos, m, cap - n, cur.key + n, cnt);
     qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
     QSL_CHECK_CUDA(cudaMemcpyAsync(cnt_h, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -804,14 +833,14 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
       set_error("capacity %lld below the %lld coarse samples", (long long)cap, (long long)m);
       return QSL_ECAPACITY;
     }
-    coarse_keys_kernel<<<grid_for(m), 256, 0, s>>>(m, nd, p, R, nc[0], nc[1], smp->key);
+    coarse_keys_kernel<<<grid_for(m), 256, 0, s>>>(m, nd, p, R, nc[0], nc[1], cur.key);
     qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
     // trace in curve order (neighbouring seeds on neighbouring lanes)
     iota_kernel<<<grid_for(m), 256, 0, s>>>(perm, m);
     qsl::count_launch();
-    if ((rc = sort_pairs(smp->key, kA, perm, perm2, m, nd * p, s))) return rc;
-    QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key, kA, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    if ((rc = sort_pairs(cur.key, nkey, perm, perm2, m, nd * p, s))) return rc;
+    QSL_CHECK_CUDA(cudaMemcpyAsync(cur.key, nkey, m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     if ((rc = trace_and_merge(0, m, true, 0))) return rc;
     n = m;
   }
@@ -849,8 +878,8 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
       if ((rc = sc.alloc(&ncd, 1))) return rc;
       QSL_CHECK_CUDA(cudaMemcpyAsync(ncd, cnt, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
       QSL_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t), s));
-      proposal_keys_kernel<<<grid_for(want), 256, 0, s>>>(cells, ncd, nd, p, R, nc[0], nc[1], smp->key, n,
-                                                            smp->key + n, cnt);
+      proposal_keys_kernel<<<grid_for(want), 256, 0, s>>>(cells, ncd, nd, p, R, nc[0], nc[1], cur.key, n,
+                                                            cur.key + n, cnt);
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       QSL_CHECK_CUDA(cudaMemcpyAsync(cnt_h, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -860,8 +889,8 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
         // trace the new cells in curve order (neighbouring seeds on neighbouring lanes)
         iota_kernel<<<grid_for(got), 256, 0, s>>>(perm, got);
         qsl::count_launch();
-        if ((rc = sort_pairs(smp->key + n, kA, perm, perm2, got, nd * p, s))) return rc;
-        QSL_CHECK_CUDA(cudaMemcpyAsync(smp->key + n, kA, got * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        if ((rc = sort_pairs(cur.key + n, nkey, perm, perm2, got, nd * p, s))) return rc;
+        QSL_CHECK_CUDA(cudaMemcpyAsync(cur.key + n, nkey, got * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
         if ((rc = trace_and_merge(n, got, true, 0))) return rc;
         n += got;
       }
@@ -874,7 +903,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
     int64_t added_total = 0, added = 0;
     // (A) along the curve (candidates come out in key order)
     if (n > 1) {
-      flag_pairs_kernel<<<grid_for(n - 1), 256, 0, s>>>(smp->key, crit_values(), n, crit, nd, p, reg, cand);
+      flag_pairs_kernel<<<grid_for(n - 1), 256, 0, s>>>(cur.key, crit_values(), n, crit, nd, p, reg, cand, flags);
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((rc = compact(n - 1, &added))) return rc;
@@ -887,7 +916,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
       const int b = it % 2;
       const uint32_t S = shiftS[b];
       if (!ord_built[b]) {
-        shift_keys_kernel<<<grid_for(n), 256, 0, s>>>(smp->key, n, nd, p, S, sk, perm);
+        shift_keys_kernel<<<grid_for(n), 256, 0, s>>>(cur.key, n, nd, p, S, sk, perm);
         qsl::count_launch();
         QSL_CHECK_CUDA(cudaGetLastError());
         if ((rc = sort_pairs(sk, ord_key[b], perm, perm2, n, nd * (p + 1), s))) return rc;
@@ -895,13 +924,36 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
         qsl::count_launch();
         QSL_CHECK_CUDA(cudaGetLastError());
         ord_built[b] = true;
+        ord_n[b] = n;
+        ord_mark[b] = n_pass;
+      } else if (ord_mark[b] < n_pass) {
+        // the pass samples added since this order's last use, at once
+        const int64_t m2 = n_pass - ord_mark[b];
+        shift_lookup_kernel<<<grid_for(m2), 256, 0, s>>>(pkeys + ord_mark[b], m2, nd, p, S, cur.key, n,
+                                                          crit_values(), sk, pvals, perm);
+        qsl::count_launch();
+        QSL_CHECK_CUDA(cudaGetLastError());
+        if ((rc = sort_pairs(sk, sk2, perm, perm2, m2, nd * (p + 1), s))) return rc;
+        merge_order_kernel<<<grid_for(ord_n[b] + m2), 256, 0, s>>>(ord_key[b], ord_L[b], ord_n[b], sk2, perm2,
+                                                                     pvals, m2, ord_ktmp, ord_Ltmp);
+        qsl::count_launch();
+        QSL_CHECK_CUDA(cudaGetLastError());
+        std::swap(ord_key[b], ord_ktmp);
+        std::swap(ord_L[b], ord_Ltmp);
+        ord_n[b] += m2;
+        ord_mark[b] = n_pass;
+      }
+      if (ord_n[b] != n) {
+        set_error("internal: shifted order holds %lld of %lld samples", (long long)ord_n[b], (long long)n);
+        return QSL_ECUDA;
       }
       Region sreg;
       for (int a = 0; a < 3; ++a) {
         sreg.lo[a] = reg.lo[a] + (a < nd ? S : 0);
         sreg.hi[a] = reg.hi[a] + (a < nd ? S : 0);
       }
-      flag_shifted_kernel<<<grid_for(n - 1), 256, 0, s>>>(ord_key[b], ord_L[b], n, crit, nd, p, S, sreg, cand);
+      flag_shifted_kernel<<<grid_for(n - 1), 256, 0, s>>>(ord_key[b], ord_L[b], n, crit, nd, p, S, sreg, cand,
+                                                           flags);
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
       if ((rc = compact(n - 1, &added))) return rc;
@@ -941,17 +993,26 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
                                      cudaMemcpyDeviceToDevice, s));
     rk.kind.push_back(2);
     rk.lines.push_back(n_pass);
-    scatter_by_key_kernel<<<grid_for(n_pass), 256, 0, s>>>(nkey, n_pass, smp->key, n, q_s, L_s, fa_s, st_s,
-                                                            smp->q, smp->length, smp->faces, smp->status);
+    scatter_by_key_kernel<<<grid_for(n_pass), 256, 0, s>>>(nkey, n_pass, cur.key, n, q_s, L_s, fa_s, st_s, cur.q,
+                                                            cur.L, cur.fa, cur.st);
     qsl::count_launch();
     QSL_CHECK_CUDA(cudaGetLastError());
+  }
+  if (cur.key != user.key && n > 0) {
+    // the set ended in the scratch arrays
+    QSL_CHECK_CUDA(cudaMemcpyAsync(user.key, cur.key, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync(user.q, cur.q, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync(user.L, cur.L, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync(user.fa, cur.fa, 2 * n, cudaMemcpyDeviceToDevice, s));
+    QSL_CHECK_CUDA(cudaMemcpyAsync(user.st, cur.st, n, cudaMemcpyDeviceToDevice, s));
+    if (user.org) QSL_CHECK_CUDA(cudaMemcpyAsync(user.org, cur.org, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   }
   smp->count = n;
   smp->iters = it;
   smp->traced = (int32_t)(traced & 0x7fffffff);
   int out_order = sp->out_order > 0 ? sp->out_order : p;
-  if (q_grid && (rc = convert_device(smp->key, smp->q, n, nd, p, ext, out_order, 1, q_grid, s))) return rc;
-  if (l_grid && (rc = convert_device(smp->key, smp->length, n, nd, p, ext, out_order, 0, l_grid, s))) return rc;
+  if (q_grid && (rc = convert_device(user.key, user.q, n, nd, p, ext, out_order, 1, q_grid, s))) return rc;
+  if (l_grid && (rc = convert_device(user.key, user.L, n, nd, p, ext, out_order, 0, l_grid, s))) return rc;
   if (cap_hit) {
     set_error("sample capacity %lld reached", (long long)cap);
     return QSL_ECAPACITY;

@@ -958,6 +958,13 @@ constexpr double DD1 = -12715105075.0 / 11282082432.0, DD3 = 87487479700.0 / 327
                  DD4 = -10690763975.0 / 1880347072.0, DD5 = 701980252875.0 / 199316789632.0,
                  DD6 = -1453857185.0 / 822651844.0, DD7 = 69997945.0 / 29380423.0;
 
+// Component c of (a, b, d) without indexing a local array (which would place
+// it in local memory).
+template <class R>
+__device__ __forceinline__ R sel3(int c, R a, R b, R d) {
+  return c == 0 ? a : (c == 1 ? b : d);
+}
+
 // Quotient for safeguarded iterations and step-size estimates: the fast
 // single-precision division (FP64 keeps the IEEE one).
 __device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
@@ -1020,6 +1027,102 @@ __device__ __forceinline__ void cell_rhs(const R* __restrict__ cs, int st, bool 
 #pragma unroll
       for (int i = 0; i < 3; ++i)
         k[3 + 3 * v2 + i] = g[i][0] * y[3 + 3 * v2] + g[i][1] * y[4 + 3 * v2] + g[i][2] * y[5 + 3 * v2];
+  }
+}
+
+// Lengths only, normalise-first field: the stage derivative of the lane's axis
+// is component c of the trilinear interpolant, a polynomial in the in-cell
+// coordinates, f = a0 + a1 u + a2 v + a3 w + a4 uv + a5 uw + a6 vw + a7 uvw
+// (coefficients from the cell's 8 corner values, scaled by 1/h_c once per
+// cell). Nested, it is three dependent FMAs after the shuffles, against the
+// differences and interpolations of the corner form.
+template <class R>
+__device__ __forceinline__ void trilinear_coeffs(const R* cv, R ihc, R* a) {
+  a[0] = cv[0] * ihc;
+  a[1] = (cv[1] - cv[0]) * ihc;
+  a[2] = (cv[2] - cv[0]) * ihc;
+  a[3] = (cv[4] - cv[0]) * ihc;
+  a[4] = ((cv[3] - cv[1]) - (cv[2] - cv[0])) * ihc;
+  a[5] = ((cv[5] - cv[1]) - (cv[4] - cv[0])) * ihc;
+  a[6] = ((cv[6] - cv[2]) - (cv[4] - cv[0])) * ihc;
+  a[7] = (((cv[7] - cv[6]) - (cv[5] - cv[4])) - ((cv[3] - cv[2]) - (cv[1] - cv[0]))) * ihc;
+}
+
+// Right-hand side inside one cell from the coefficients of the cell's
+// trilinear polynomials (8 per component c, corner form turned into
+// a0 + a1 u + a2 v + a3 w + a4 uv + a5 uw + a6 vw + a7 uvw once per cell entry),
+// held in shared memory with a stride of one block. Deviations are carried in
+// cell units (du_j = dx_j / h_j). Normalise-first fields: the coefficients of
+// component c are pre-scaled by 1/h_c, so the polynomial's value is the
+// position derivative in cell units and its gradient in (u, v, w), applied to
+// the deviations, their derivative in cell units; no scaling per stage. Raw
+// fields (unscaled coefficients of B): b = B/|B| and its gradient
+// (I - b b^T) grad B / |B| at the point, then the 1/h_c row scaling.
+template <class R, int NC>
+__device__ __forceinline__ void cell_rhs_poly(const R* __restrict__ cs, int st, bool raw, const R* ih, const R* y,
+                                              R* k) {
+  const R u = y[0], v = y[1], w = y[2];
+  R val[3], d[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R* a = cs + (8 * c) * st;
+    const R a0 = a[0], a1 = a[st], a2 = a[2 * st], a3 = a[3 * st], a4 = a[4 * st], a5 = a[5 * st], a6 = a[6 * st],
+            a7 = a[7 * st];
+    const R p0 = fma(a1, u, a0), p1 = fma(a4, u, a2), p2 = fma(a5, u, a3), p3 = fma(a7, u, a6);
+    const R q1 = fma(p3, v, p2);
+    val[c] = fma(q1, w, fma(p1, v, p0));
+    if (NC == 9) {
+      d[c][0] = fma(fma(a7, v, a5), w, fma(a4, v, a1));
+      d[c][1] = fma(p3, w, p1);
+      d[c][2] = q1;
+    }
+  }
+  if (!raw) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) k[c] = val[c];
+    if (NC == 9) {
+#pragma unroll
+      for (int v2 = 0; v2 < 2; ++v2)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          k[3 + 3 * v2 + i] = fma(d[i][0], y[3 + 3 * v2], fma(d[i][1], y[4 + 3 * v2], d[i][2] * y[5 + 3 * v2]));
+    }
+  } else {
+    const R m = sqrt(val[0] * val[0] + val[1] * val[1] + val[2] * val[2]);
+    const R rm = (m > R(0)) ? R(1) / m : R(0);
+    R b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) b[c] = val[c] * rm;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) k[c] = b[c] * ih[c];
+    if (NC == 9) {
+      R g[3][3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const R t = b[0] * d[0][j] + b[1] * d[1][j] + b[2] * d[2][j];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) g[i][j] = (d[i][j] - b[i] * t) * rm;
+      }
+#pragma unroll
+      for (int v2 = 0; v2 < 2; ++v2)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          k[3 + 3 * v2 + i] =
+              ih[i] * fma(g[i][0], y[3 + 3 * v2], fma(g[i][1], y[4 + 3 * v2], g[i][2] * y[5 + 3 * v2]));
+    }
+  }
+}
+
+// Deviations of a line state from cell units to domain units (before its end
+// record is written).
+template <class R, int NC>
+__device__ __forceinline__ void dev_to_domain(R* y, const R* hh3) {
+  if (NC == 9) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      y[3 + i] *= hh3[i];
+      y[6 + i] *= hh3[i];
+    }
   }
 }
 
@@ -1135,6 +1238,11 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
                   y[6] = u0[1] * av[2] - u0[2] * av[1];
                   y[7] = u0[2] * av[0] - u0[0] * av[2];
                   y[8] = u0[0] * av[1] - u0[1] * av[0];
+#pragma unroll
+                  for (int i = 0; i < 3; ++i) {  // deviations in cell units
+                    y[3 + i] *= ih[i];
+                    y[6 + i] *= ih[i];
+                  }
                 }
 #pragma unroll
                 for (int f = 0; f < 6; ++f) {
@@ -1151,6 +1259,7 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
             }
             h = E->h_init;
             if (status != ST_RUNNING) {
+              dev_to_domain<R, NC>(y, hh3);
               write_end<R, NC, true>(P, E, unit, y, ic, R(0), lface, status, 0);
               active = false;
             }
@@ -1189,12 +1298,15 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
         q[6] = ldg4(p + sz + sy);
         q[7] = ldg4(p + sz + sy + 1);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          cs[c * st] = q[c].x;
-          cs[(8 + c) * st] = q[c].y;
-          cs[(16 + c) * st] = q[c].z;
+        for (int c = 0; c < 3; ++c) {
+          R cv[8], co[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) cv[j] = R(c == 0 ? q[j].x : (c == 1 ? q[j].y : q[j].z));
+          trilinear_coeffs<R>(cv, E->F.raw ? R(1) : ih[c], co);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) cs[(8 * c + j) * st] = co[j];
         }
-        cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], y, k1);
+        cell_rhs_poly<R, NC>(cs, st, E->F.raw, ih, y, k1);
         c_stage += 1;
         kvalid = true;
       }
@@ -1225,32 +1337,36 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
         capped = false;
       }
       R hh = sgn * hs;
+      // stage combinations with the step folded into the coefficients; each
+      // stage's newest term is the last FMA
+      const R c21 = hh * R(DA21), c31 = hh * R(DA31), c32 = hh * R(DA32), c41 = hh * R(DA41), c42 = hh * R(DA42),
+              c43 = hh * R(DA43), c51 = hh * R(DA51), c52 = hh * R(DA52), c53 = hh * R(DA53), c54 = hh * R(DA54),
+              c61 = hh * R(DA61), c62 = hh * R(DA62), c63 = hh * R(DA63), c64 = hh * R(DA64), c65 = hh * R(DA65);
+      const R b1 = hh * R(DB1), b3 = hh * R(DB3), b4 = hh * R(DB4), b5 = hh * R(DB5), b6 = hh * R(DB6);
       R k2[NC], k3[NC], k4[NC], k5[NC], k6[NC], k7[NC], t[NC];
 #pragma unroll
-      for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(DA21) * k1[i], y[i]);
-      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k2);
+      for (int i = 0; i < NC; ++i) t[i] = fma(c21, k1[i], y[i]);
+      cell_rhs_poly<R, NC>(cs, st, E->F.raw, ih, t, k2);
 #pragma unroll
-      for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(DA31) * k1[i] + R(DA32) * k2[i], y[i]);
-      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k3);
+      for (int i = 0; i < NC; ++i) t[i] = fma(c32, k2[i], fma(c31, k1[i], y[i]));
+      cell_rhs_poly<R, NC>(cs, st, E->F.raw, ih, t, k3);
 #pragma unroll
-      for (int i = 0; i < NC; ++i) t[i] = fma(hh, R(DA41) * k1[i] + R(DA42) * k2[i] + R(DA43) * k3[i], y[i]);
-      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k4);
+      for (int i = 0; i < NC; ++i) t[i] = fma(c43, k3[i], fma(c42, k2[i], fma(c41, k1[i], y[i])));
+      cell_rhs_poly<R, NC>(cs, st, E->F.raw, ih, t, k4);
+#pragma unroll
+      for (int i = 0; i < NC; ++i) t[i] = fma(c54, k4[i], fma(c53, k3[i], fma(c52, k2[i], fma(c51, k1[i], y[i]))));
+      cell_rhs_poly<R, NC>(cs, st, E->F.raw, ih, t, k5);
 #pragma unroll
       for (int i = 0; i < NC; ++i)
-        t[i] = fma(hh, R(DA51) * k1[i] + R(DA52) * k2[i] + R(DA53) * k3[i] + R(DA54) * k4[i], y[i]);
-      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k5);
-#pragma unroll
-      for (int i = 0; i < NC; ++i)
-        t[i] = fma(hh, R(DA61) * k1[i] + R(DA62) * k2[i] + R(DA63) * k3[i] + R(DA64) * k4[i] + R(DA65) * k5[i],
-                   y[i]);
-      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k6);
+        t[i] = fma(c65, k5[i], fma(c64, k4[i], fma(c63, k3[i], fma(c62, k2[i], fma(c61, k1[i], y[i])))));
+      cell_rhs_poly<R, NC>(cs, st, E->F.raw, ih, t, k6);
       R dy[NC];
 #pragma unroll
       for (int i = 0; i < NC; ++i) {
-        dy[i] = hh * (R(DB1) * k1[i] + R(DB3) * k3[i] + R(DB4) * k4[i] + R(DB5) * k5[i] + R(DB6) * k6[i]);
+        dy[i] = fma(b6, k6[i], fma(b5, k5[i], fma(b4, k4[i], fma(b3, k3[i], b1 * k1[i]))));
         t[i] = y[i] + dy[i];
       }
-      cell_rhs<R, NC>(cs, st, E->F.raw, ih[0], ih[1], ih[2], t, k7);
+      cell_rhs_poly<R, NC>(cs, st, E->F.raw, ih, t, k7);
       c_stage += 6;
       steps += 1;
       R err = 0;
@@ -1260,12 +1376,17 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
         R e = fabs(hh * (R(DE1) * k1[i] + R(DE3) * k3[i] + R(DE4) * k4[i] + R(DE5) * k5[i] + R(DE6) * k6[i] +
                          R(DE7) * k7[i]));
         if (!isfinite(t[i])) finite = false;
-        R ya = fabs(y[i]), yb = fabs(t[i]);
+        R ya, yb;
         if (i < 3) {
           R base = R(E->F.org[i]) + R(ic[i]) * hh3[i];
           e *= hh3[i];
           ya = fabs(base + y[i] * hh3[i]);
           yb = fabs(base + t[i] * hh3[i]);
+        } else {  // deviations, in domain units
+          const R hc = hh3[i % 3];
+          e *= hc;
+          ya = fabs(y[i]) * hc;
+          yb = fabs(t[i]) * hc;
         }
         err = fmax(err, cdiv(e, P.tol_abs + P.tol_rel * fmax(ya, yb)));
       }
@@ -1375,8 +1496,8 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
             y[i] += y_at<R>(th, dy[i], hh * k1[i], hh * k7[i],
                             hh * (R(DD1) * k1[i] + R(DD3) * k3[i] + R(DD4) * k4[i] + R(DD5) * k5[i] +
                                   R(DD6) * k6[i] + R(DD7) * k7[i]));
-          bool dom = up_c ? hi_dom[ax_c] : lo_dom[ax_c];
-          R target = up_c ? hi_pl[ax_c] : lo_pl[ax_c];
+          bool dom = up_c ? sel3(ax_c, hi_dom[0], hi_dom[1], hi_dom[2]) : sel3(ax_c, lo_dom[0], lo_dom[1], lo_dom[2]);
+          R target = up_c ? sel3(ax_c, hi_pl[0], hi_pl[1], hi_pl[2]) : sel3(ax_c, lo_pl[0], lo_pl[1], lo_pl[2]);
           if (ax_c == 0) y[0] = target;
           else if (ax_c == 1) y[1] = target;
           else y[2] = target;
@@ -1391,13 +1512,15 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
           } else {
             // enter the neighbouring cell
             zc = (dl < tiny) ? zc + 1 : 0;
-            int na = ic[ax_c] + (up_c ? 1 : -1);
-            if (zc > 3 || na < 0 || na > E->F.n[ax_c] - 2) {
+            int na = sel3(ax_c, ic[0], ic[1], ic[2]) + (up_c ? 1 : -1);
+            if (zc > 3 || na < 0 || na > sel3(ax_c, E->F.n[0], E->F.n[1], E->F.n[2]) - 2) {
               // grazing a face back and forth: stay in this cell for one step
               // (the cell's polynomial continued across the face)
               zc = 0;
             } else {
-              ic[ax_c] = na;
+              if (ax_c == 0) ic[0] = na;
+              else if (ax_c == 1) ic[1] = na;
+              else ic[2] = na;
               if (ax_c == 0) y[0] = up_c ? R(0) : R(1);
               else if (ax_c == 1) y[1] = up_c ? R(0) : R(1);
               else y[2] = up_c ? R(0) : R(1);
@@ -1409,6 +1532,7 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
       }
     }
     if (status != ST_RUNNING) {
+      dev_to_domain<R, NC>(y, hh3);
       write_end<R, NC, true>(P, E, unit, y, ic, mu, lface, status, steps);
       active = false;
     }
@@ -1469,10 +1593,6 @@ __device__ __forceinline__ R gbc(unsigned m, R v, int src) {
 }
 
 
-template <class R>
-__device__ __forceinline__ R sel3(int c, R a, R b, R d) {
-  return c == 0 ? a : (c == 1 ? b : d);
-}
 
 // Stage derivative of the lane's components: k[0] = d(x_c)/dlambda (cell
 // units), k[1], k[2] = row c of grad b applied to the two deviations.
@@ -1507,24 +1627,6 @@ __device__ __forceinline__ void coop_rhs(unsigned gm, int gb, const R* cv, bool 
     k[1] = d0 * a0 + d1 * a1 + d2 * a2;
     k[2] = d0 * b0 + d1 * b1 + d2 * b2;
   }
-}
-
-// Lengths only, normalise-first field: the stage derivative of the lane's axis
-// is component c of the trilinear interpolant, a polynomial in the in-cell
-// coordinates, f = a0 + a1 u + a2 v + a3 w + a4 uv + a5 uw + a6 vw + a7 uvw
-// (coefficients from the cell's 8 corner values, scaled by 1/h_c once per
-// cell). Nested, it is three dependent FMAs after the shuffles, against the
-// differences and interpolations of the corner form.
-template <class R>
-__device__ __forceinline__ void trilinear_coeffs(const R* cv, R ihc, R* a) {
-  a[0] = cv[0] * ihc;
-  a[1] = (cv[1] - cv[0]) * ihc;
-  a[2] = (cv[2] - cv[0]) * ihc;
-  a[3] = (cv[4] - cv[0]) * ihc;
-  a[4] = ((cv[3] - cv[1]) - (cv[2] - cv[0])) * ihc;
-  a[5] = ((cv[5] - cv[1]) - (cv[4] - cv[0])) * ihc;
-  a[6] = ((cv[6] - cv[2]) - (cv[4] - cv[0])) * ihc;
-  a[7] = (((cv[7] - cv[6]) - (cv[5] - cv[4])) - ((cv[3] - cv[2]) - (cv[1] - cv[0]))) * ihc;
 }
 
 template <class R>
@@ -1969,6 +2071,466 @@ __global__ void __launch_bounds__(256) cell_coop_kernel(const __grid_constant__ 
   if (lane == 0 && any_to && P.timeout_flag) atomicExch(P.timeout_flag, 1);
 }
 
+// ------------------------------------------------------------ lengths-only cell-wise tracer
+// The cell-wise Dormand-Prince tracer for lengths only (refinement passes and
+// lengths-only maps), one lane per line. Only the position is integrated, so
+// inside a cell the right-hand side is three trilinear polynomials in the
+// in-cell coordinates (normalise-first fields; raw fields normalise the three
+// at the point), whose 24 coefficients stay in registers from the cell entry
+// on: a stage is the polynomials' four independent first-level FMAs and three
+// dependent ones per component, plus one FMA of the stage combination on its
+// dependent chain (the earlier terms of each combination are summed while the
+// previous stages run). No shuffles and no shared memory. While a step is
+// integrated, the 8 corners of the cell the line is expected to enter next
+// (across the first plane along the step's initial direction) are loaded, so
+// a cell entry usually finds its corners in registers instead of waiting for
+// the memory system.
+template <class V>
+__device__ __forceinline__ float vcomp(const V& q, int c) {
+  return c == 0 ? q.x : (c == 1 ? q.y : q.z);
+}
+
+template <class R, class V>
+__device__ __forceinline__ void len_coeffs(const V* q, bool raw, const R* ih, R (*a)[8]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R cv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) cv[k] = R(c == 0 ? q[k].x : (c == 1 ? q[k].y : q[k].z));
+    trilinear_coeffs<R>(cv, raw ? R(1) : ih[c], a[c]);
+  }
+}
+
+// Stage derivative in cell units: ih_c b_c(u, v, w).
+template <class R>
+__device__ __forceinline__ void len_rhs(const R (*a)[8], bool raw, const R* ih, const R* t, R* k) {
+  const R u = t[0], v = t[1], w = t[2];
+  R val[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R p0 = fma(a[c][1], u, a[c][0]), p1 = fma(a[c][4], u, a[c][2]), p2 = fma(a[c][5], u, a[c][3]),
+            p3 = fma(a[c][7], u, a[c][6]);
+    val[c] = fma(fma(p3, v, p2), w, fma(p1, v, p0));
+  }
+  if (raw) {
+    // interpolate B, normalise at the point
+    const R m2 = val[0] * val[0] + val[1] * val[1] + val[2] * val[2];
+    const R rm = m2 > R(0) ? rsqrt(m2) : R(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) k[c] = val[c] * rm * ih[c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) k[c] = val[c];
+  }
+}
+
+// Earliest crossing fraction t in (0, 1] of plane `target` by the axis
+// component of the step's dense output, offset t P(t) with the cubic
+// P(t) = dya + (1 - t)(bspl + t (c3 + (1 - t) c4)); sg = +1 for an upper plane.
+// The same bracket (t = 1/4, 1/2, 3/4) and safeguarded Newton iteration as the
+// other cell-wise kernels; a step that starts on the plane (r = 0) solves P = 0
+// (the trivial root t = 0 divided out).
+template <class R>
+__device__ __forceinline__ R len_crossing(R r, R dya, R bspl, R c3, R c4, R sg) {
+  const bool defl = (r == R(0));
+  R ta = R(0), tb = R(1);
+#pragma unroll
+  for (int q = 1; q < 4; ++q) {
+    R tq = R(0.25) * R(q);
+    R s1 = R(1) - tq;
+    R pq = dya + s1 * (bspl + tq * (c3 + s1 * c4));
+    R f = defl ? pq : tq * pq - r;
+    if (sg * f > R(0) && tb == R(1)) tb = tq;
+    else if (tb == R(1)) ta = tq;
+  }
+  R t = ta + (tb - ta) * R(0.5);
+  if (!defl) {
+    R tl = qdiv(r, dya);
+    if (tl > ta && tl < tb) t = tl;
+  }
+  for (int it = 0; it < 30; ++it) {
+    R s1 = R(1) - t;
+    R inner = c3 + s1 * c4;
+    R mid = bspl + t * inner;
+    R pv = dya + s1 * mid;
+    R f = defl ? pv : t * pv - r;
+    if (fabs(f) <= R(4) * eps_of<R>() * (fabs(r) + fabs(dya)) || !(tb - ta > R(2) * eps_of<R>())) break;
+    if (sg * f > R(0)) tb = t;
+    else ta = t;
+    R dmid = inner - t * c4;
+    R dp = s1 * dmid - mid;
+    R df = defl ? dp : pv + t * dp;
+    R tn = t - qdiv(f, df);
+    t = (tn > ta && tn < tb) ? tn : R(0.5) * (ta + tb);
+  }
+  return t;
+}
+
+// One line direction of the lengths-only tracer, start to end, by one lane.
+// The item's constants are copied into registers once (nothing in the step
+// loop reads memory but the corners at a cell entry), the planes and the
+// error-norm offsets of the current cell are formed at its entry, and the
+// cell's vertex address moves by one stride per face crossed.
+template <class R>
+__device__ __forceinline__ void len_line(const TraceParams<R>& P, int64_t unit, unsigned long long* c_stage,
+                                         unsigned long long* c_acc, unsigned long long* c_rej,
+                                         unsigned long long* c_land, bool* timed_out,
+                                         unsigned long long t_start) {
+  typedef typename V4<R>::type V;
+  constexpr bool PREFETCH = sizeof(R) == 4;  // FP64 corners would double the registers held
+  int64_t g;
+  double xd[3];
+  const Item<R>* E = resolve_seed(P, unit >> 1, &g, xd);
+  const R sgn = (unit & 1) ? R(-1) : R(1);
+  // the item's constants, in registers
+  const V* const fv = E->F.v;
+  const bool raw = E->F.raw != 0;
+  const int n0 = E->F.n[0], n1 = E->F.n[1], n2 = E->F.n[2];
+  const int64_t sy = n0, sz = (int64_t)n0 * n1;
+  const R ih[3] = {R(E->F.inv_h[0]), R(E->F.inv_h[1]), R(E->F.inv_h[2])};
+  const R hh3[3] = {R(1) / ih[0], R(1) / ih[1], R(1) / ih[2]};
+  const R org[3] = {R(E->F.org[0]), R(E->F.org[1]), R(E->F.org[2])};
+  const R dlo[3] = {E->lo[0], E->lo[1], E->lo[2]}, dhi[3] = {E->hi[0], E->hi[1], E->hi[2]};
+  const R max_len = E->max_len, h_max = E->h_max, h_min = E->h_min;
+  const R tiny = R(1e-4) * h_max;
+  const R band = R(16) * eps_of<R>();  // tolerance band of internal cell faces (cell units)
+  const R tol_abs = P.tol_abs, tol_rel = P.tol_rel;
+  const long long max_steps = P.max_steps;
+  int ic[3];
+  R y[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    double fa = (xd[ax] - E->org_d[ax]) * E->inv_h_d[ax];
+    double fl = floor(fmin(fmax(fa, 0.0), (double)(E->F.n[ax] - 2)));
+    ic[ax] = (int)fl;
+    y[ax] = (R)(fa - fl);
+  }
+  int status = ST_RUNNING, lface = NO_FACE;
+  {
+    bool outside = false;
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+      if (face_g<R, true>(E->lo, E->hi, ic, f, y, (const R*)nullptr) > R(0)) outside = true;
+    if (outside || !isfinite(xd[0]) || !isfinite(xd[1]) || !isfinite(xd[2])) {
+      status = QSL_LINE_OUTSIDE;
+    } else {
+      Interp<R> I0;
+      interp<R, R, false, false, true, false>(E->F, y[0], y[1], y[2], I0, ic);
+      R m0 = sqrt(I0.b[0] * I0.b[0] + I0.b[1] * I0.b[1] + I0.b[2] * I0.b[2]);
+      if (!(m0 > R(0))) {
+        status = QSL_LINE_NULL;
+      } else {
+        // a seed on a face whose field points out of the domain ends this side
+        // at once with zero length
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          if (status == ST_RUNNING && face_g<R, true>(E->lo, E->hi, ic, f, y, (const R*)nullptr) == R(0)) {
+            R bn = I0.b[f >> 1] * sgn;
+            R outw = (f & 1) ? bn : -bn;
+            if (outw > R(0)) {
+              status = QSL_LINE_OK;
+              lface = f;
+            }
+          }
+        }
+      }
+    }
+  }
+  if (status != ST_RUNNING) {
+    write_end<R, 3, true>(P, E, unit, y, ic, R(0), lface, status, 0);
+    return;
+  }
+  R mu = 0, muc = 0, h = E->h_init;
+  int steps = 0, zc = 0;
+  bool kvalid = false, pf_valid = false;
+  int64_t cell = (int64_t)ic[2] * sz + (int64_t)ic[1] * sy + ic[0];  // vertex index of the cell's corner 000
+  int64_t pf_cell = -1;
+  R a[3][8], k1[3];
+  R lo_pl[3], hi_pl[3], base[3];
+  bool lo_dom[3], hi_dom[3];
+  V pq[8];
+  for (;;) {
+    if (P.timeout_ns && ((steps & 63) == 63)) {
+      if (globaltimer() - t_start > P.timeout_ns) *timed_out = true;
+    }
+    if (*timed_out) status = QSL_LINE_TIMEOUT;
+    else if (steps >= max_steps) status = QSL_LINE_MAXSTEPS;
+    const R room = max_len - mu;
+    if (status == ST_RUNNING && !(room > R(0))) status = QSL_LINE_MAXLEN;
+    if (status != ST_RUNNING) break;
+    if (!kvalid) {
+      // the cell's corners (prefetched when predicted) to its polynomials;
+      // its planes (cell faces, or domain faces where they come first)
+      V q[8];
+      if (PREFETCH && pf_valid && pf_cell == cell) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q[k] = pq[k];
+      } else {
+        const V* p = fv + cell;
+        q[0] = ldg4(p);
+        q[1] = ldg4(p + 1);
+        q[2] = ldg4(p + sy);
+        q[3] = ldg4(p + sy + 1);
+        q[4] = ldg4(p + sz);
+        q[5] = ldg4(p + sz + 1);
+        q[6] = ldg4(p + sz + sy);
+        q[7] = ldg4(p + sz + sy + 1);
+      }
+      pf_valid = false;
+      len_coeffs<R, V>(q, raw, ih, a);
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        const R lr = dlo[ax] - R(ic[ax]), hr = dhi[ax] - R(ic[ax]);
+        lo_dom[ax] = lr >= R(0);
+        hi_dom[ax] = hr <= R(1);
+        lo_pl[ax] = lo_dom[ax] ? lr : R(0);
+        hi_pl[ax] = hi_dom[ax] ? hr : R(1);
+        base[ax] = org[ax] + R(ic[ax]) * hh3[ax];
+      }
+      len_rhs<R>(a, raw, ih, y, k1);
+      *c_stage += 1;
+      kvalid = true;
+    }
+    // step: controller size, capped a little beyond the first plane along k1
+    R tface = R(1e30);
+    int pax = -1, pup = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      const R vel = sgn * k1[ax];
+      R tt = R(1e30);
+      if (vel > R(0)) tt = qdiv(hi_pl[ax] - y[ax], vel);
+      else if (vel < R(0)) tt = qdiv(lo_pl[ax] - y[ax], vel);
+      if (tt < tface) {
+        tface = tt;
+        pax = ax;
+        pup = vel > R(0);
+      }
+    }
+    if (PREFETCH && pax >= 0) {
+      // load the corners of the cell across that plane while the step runs
+      const bool pdom = pup ? sel3(pax, hi_dom[0], hi_dom[1], hi_dom[2]) : sel3(pax, lo_dom[0], lo_dom[1], lo_dom[2]);
+      const int na = sel3(pax, ic[0], ic[1], ic[2]) + (pup ? 1 : -1);
+      const int nmax = sel3(pax, n0, n1, n2) - 2;
+      const int64_t st = pax == 0 ? 1 : (pax == 1 ? sy : sz);
+      const int64_t nc = cell + (pup ? st : -st);
+      if (!pdom && na >= 0 && na <= nmax && !(pf_valid && pf_cell == nc)) {
+        const V* p = fv + nc;
+        pq[0] = ldg4(p);
+        pq[1] = ldg4(p + 1);
+        pq[2] = ldg4(p + sy);
+        pq[3] = ldg4(p + sy + 1);
+        pq[4] = ldg4(p + sz);
+        pq[5] = ldg4(p + sz + 1);
+        pq[6] = ldg4(p + sz + sy);
+        pq[7] = ldg4(p + sz + sy + 1);
+        pf_cell = nc;
+        pf_valid = true;
+      }
+    }
+    R hs = fmin(fmin(h, h_max), room);
+    bool capped = room <= fmin(h, h_max);
+    const R hf = R(1.25) * fmax(tface, R(0)) + tiny;
+    if (hf < hs) {
+      hs = hf;
+      capped = false;
+    }
+    const R hh = sgn * hs;
+    // stage combinations with the step folded into the coefficients; each
+    // stage's newest term is the last FMA
+    const R c21 = hh * R(DA21), c31 = hh * R(DA31), c32 = hh * R(DA32), c41 = hh * R(DA41), c42 = hh * R(DA42),
+            c43 = hh * R(DA43), c51 = hh * R(DA51), c52 = hh * R(DA52), c53 = hh * R(DA53), c54 = hh * R(DA54),
+            c61 = hh * R(DA61), c62 = hh * R(DA62), c63 = hh * R(DA63), c64 = hh * R(DA64), c65 = hh * R(DA65);
+    const R b1 = hh * R(DB1), b3 = hh * R(DB3), b4 = hh * R(DB4), b5 = hh * R(DB5), b6 = hh * R(DB6);
+    R k2[3], k3[3], k4[3], k5[3], k6[3], k7[3], t[3], dy[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t[i] = fma(c21, k1[i], y[i]);
+    len_rhs<R>(a, raw, ih, t, k2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t[i] = fma(c32, k2[i], fma(c31, k1[i], y[i]));
+    len_rhs<R>(a, raw, ih, t, k3);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t[i] = fma(c43, k3[i], fma(c42, k2[i], fma(c41, k1[i], y[i])));
+    len_rhs<R>(a, raw, ih, t, k4);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t[i] = fma(c54, k4[i], fma(c53, k3[i], fma(c52, k2[i], fma(c51, k1[i], y[i]))));
+    len_rhs<R>(a, raw, ih, t, k5);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      t[i] = fma(c65, k5[i], fma(c64, k4[i], fma(c63, k3[i], fma(c62, k2[i], fma(c61, k1[i], y[i])))));
+    len_rhs<R>(a, raw, ih, t, k6);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      dy[i] = fma(b6, k6[i], fma(b5, k5[i], fma(b4, k4[i], fma(b3, k3[i], b1 * k1[i]))));
+      t[i] = y[i] + dy[i];
+    }
+    len_rhs<R>(a, raw, ih, t, k7);
+    *c_stage += 6;
+    steps += 1;
+    R err = 0;
+    bool finite = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const R e = fabs(hh * (R(DE1) * k1[i] + R(DE3) * k3[i] + R(DE4) * k4[i] + R(DE5) * k5[i] + R(DE6) * k6[i] +
+                             R(DE7) * k7[i])) * hh3[i];
+      if (!isfinite(t[i])) finite = false;
+      const R ya = fabs(base[i] + y[i] * hh3[i]), yb = fabs(base[i] + t[i] * hh3[i]);
+      err = fmax(err, cdiv(e, tol_abs + tol_rel * fmax(ya, yb)));
+    }
+    if (!finite) {
+      status = QSL_LINE_NONFINITE;
+      break;
+    }
+    if (err > R(1)) {
+      *c_rej += 1;
+      h = hs * fmax(R(0.2), R(0.9) * cpow(err, R(-0.25)));
+      if (h < h_min) {
+        status = QSL_LINE_STALL;
+        break;
+      }
+      continue;
+    }
+    *c_acc += 1;
+    const R hnext = hs * ((err == R(0)) ? R(5) : fmin(R(5), R(0.9) * cpow(err, R(-0.2))));
+    // first plane crossed within the step on the dense output (4th-order
+    // continuous extension); the earliest crossing wins, lower plane id on ties
+    R th = R(2);
+    int ax_c = -1, up_c = 0;
+    unsigned cmask = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      if ((lo_pl[ax] - y[ax]) - dy[ax] > (lo_dom[ax] ? R(0) : band)) cmask |= 1u << (2 * ax);
+      if (dy[ax] - (hi_pl[ax] - y[ax]) > (hi_dom[ax] ? R(0) : band)) cmask |= 2u << (2 * ax);
+    }
+#pragma unroll 1
+    while (cmask) {
+      const int pl = __ffs(cmask) - 1;
+      cmask &= cmask - 1;
+      const int ax = pl >> 1, up = pl & 1;
+      const R ya = sel3(ax, y[0], y[1], y[2]);
+      const R dya = sel3(ax, dy[0], dy[1], dy[2]);
+      const R target = up ? sel3(ax, hi_pl[0], hi_pl[1], hi_pl[2]) : sel3(ax, lo_pl[0], lo_pl[1], lo_pl[2]);
+      const R k1a = sel3(ax, k1[0], k1[1], k1[2]);
+      const R k7a = sel3(ax, k7[0], k7[1], k7[2]);
+      const R c4 = hh * (R(DD1) * k1a + R(DD3) * sel3(ax, k3[0], k3[1], k3[2]) + R(DD4) * sel3(ax, k4[0], k4[1], k4[2]) +
+                         R(DD5) * sel3(ax, k5[0], k5[1], k5[2]) + R(DD6) * sel3(ax, k6[0], k6[1], k6[2]) + R(DD7) * k7a);
+      const R bspl = hh * k1a - dya;
+      const R c3 = dya - hh * k7a - bspl;
+      const R tc = len_crossing<R>(target - ya, dya, bspl, c3, c4, up ? R(1) : R(-1));
+      if (tc < th) {
+        th = tc;
+        ax_c = ax;
+        up_c = up;
+      }
+    }
+    if (ax_c < 0) {
+      // the step stays in the cell: accept it; k7 is the next k1
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        y[i] += dy[i];
+        k1[i] = k7[i];
+      }
+      R t1 = hs - muc, t2 = mu + t1;
+      muc = (t2 - mu) - t1;
+      mu = t2;
+      h = hnext;
+      zc = 0;
+      if (capped) {
+        status = QSL_LINE_MAXLEN;
+        break;
+      }
+      continue;
+    }
+    // advance to the plane on the dense output and snap onto it
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      y[i] += y_at<R>(th, dy[i], hh * k1[i], hh * k7[i],
+                      hh * (R(DD1) * k1[i] + R(DD3) * k3[i] + R(DD4) * k4[i] + R(DD5) * k5[i] + R(DD6) * k6[i] +
+                            R(DD7) * k7[i]));
+    const bool dom = up_c ? sel3(ax_c, hi_dom[0], hi_dom[1], hi_dom[2]) : sel3(ax_c, lo_dom[0], lo_dom[1], lo_dom[2]);
+    const R target = up_c ? sel3(ax_c, hi_pl[0], hi_pl[1], hi_pl[2]) : sel3(ax_c, lo_pl[0], lo_pl[1], lo_pl[2]);
+    if (ax_c == 0) y[0] = target;
+    else if (ax_c == 1) y[1] = target;
+    else y[2] = target;
+    const R dl = th * hs;
+    R t1 = dl - muc, t2 = mu + t1;
+    muc = (t2 - mu) - t1;
+    mu = t2;
+    *c_land += 1;
+    if (dom) {
+      status = QSL_LINE_OK;
+      lface = 2 * ax_c + up_c;
+      break;
+    }
+    // enter the neighbouring cell
+    zc = (dl < tiny) ? zc + 1 : 0;
+    const int na = sel3(ax_c, ic[0], ic[1], ic[2]) + (up_c ? 1 : -1);
+    if (zc > 3 || na < 0 || na > sel3(ax_c, n0, n1, n2) - 2) {
+      // grazing a face back and forth: stay in this cell for one step (the
+      // cell's polynomial continued across the face)
+      zc = 0;
+    } else {
+      const int64_t st = ax_c == 0 ? 1 : (ax_c == 1 ? sy : sz);
+      cell += up_c ? st : -st;
+      if (ax_c == 0) {
+        ic[0] = na;
+        y[0] = up_c ? R(0) : R(1);
+      } else if (ax_c == 1) {
+        ic[1] = na;
+        y[1] = up_c ? R(0) : R(1);
+      } else {
+        ic[2] = na;
+        y[2] = up_c ? R(0) : R(1);
+      }
+      kvalid = false;
+    }
+    h = fmax(hnext, hs);
+  }
+  write_end<R, 3, true>(P, E, unit, y, ic, mu, lface, status, steps);
+}
+
+// The lengths-only kernel: lane l of global warp w traces units w + l W,
+// w + (l + 32) W, ... (W warps in the grid), so the units of a launch spread
+// over all warps before a warp takes a second one, and a lane runs its line
+// to the end with no warp-wide operation in between.
+template <class R>
+__global__ void __launch_bounds__(256) cell_len_kernel(const __grid_constant__ TraceParams<R> P) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int64_t total = P.n_units;
+  if (P.n_seeds_dev) {
+    int64_t c = 2 * (*P.n_seeds_dev);
+    total = c < total ? c : total;
+  }
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  unsigned long long c_stage = 0, c_acc = 0, c_rej = 0, c_land = 0, c_lines = 0;
+  bool timed_out = false;
+  const unsigned long long t_start = P.timeout_ns ? globaltimer() : 0ull;
+  for (int64_t unit = w + (int64_t)lane * W; unit < total; unit += 32 * W) {
+    c_lines += (unit & 1) == 0;
+    len_line<R>(P, unit, &c_stage, &c_acc, &c_rej, &c_land, &timed_out, t_start);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c_stage += __shfl_down_sync(FULL, c_stage, o);
+    c_acc += __shfl_down_sync(FULL, c_acc, o);
+    c_rej += __shfl_down_sync(FULL, c_rej, o);
+    c_land += __shfl_down_sync(FULL, c_land, o);
+    c_lines += __shfl_down_sync(FULL, c_lines, o);
+  }
+  unsigned any_to = __ballot_sync(FULL, timed_out);
+  if (lane == 0 && P.stats) {
+    atomicAdd(&P.stats->stage_evals, c_stage);
+    atomicAdd(&P.stats->accepted, c_acc);
+    atomicAdd(&P.stats->rejected, c_rej);
+    atomicAdd(&P.stats->landing, c_land);
+    atomicAdd(&P.stats->lines, c_lines);
+    if (any_to) atomicAdd(&P.stats->timeouts, 1ull);
+  }
+  if (lane == 0 && any_to && P.timeout_flag) atomicExch(P.timeout_flag, 1);
+}
+
 // ------------------------------------------------------------ assembly (FP64)
 __device__ __forceinline__ double dot3(const double* a, const double* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
@@ -2243,8 +2805,19 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
   int threads = 32 * shape.warps_per_block;
   // persistent kernel: never launch more blocks than can be resident at once
   const bool use_cell = loc && cfg.integrator == QSL_DOPRI5_CELL;
+  // lengths only, unless three lanes per line are asked for: the one-lane
+  // polynomial kernel when every lane of the resident grid takes at most one
+  // line direction (refinement passes; launches bound by their longest line)
+  bool len_kernel = false;
+  if (use_cell && NC == 3 && shape.line_lanes != 3) {
+    int res_len = 0;
+    QSL_CHECK_CUDA(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res_len, cell_len_kernel<R>, 32 * shape.warps_per_block, 0));
+    const int bps_len = shape.blocks_per_sm < res_len ? shape.blocks_per_sm : res_len;
+    len_kernel = 2 * n_seeds <= (int64_t)32 * shape.warps_per_block * (bps_len > 0 ? bps_len : 1) * sms;
+  }
   bool coop = false;
-  if (use_cell) {
+  if (use_cell && !len_kernel) {
     if (shape.line_lanes == 3) {
       coop = true;
     } else if (shape.line_lanes == 0) {
@@ -2255,9 +2828,11 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
       coop = n_seeds_dev != nullptr || 2 * n_seeds <= (int64_t)512 * sms;
     }
   }
-  size_t smem = (use_cell && !coop) ? (size_t)24 * threads * sizeof(R) : 0;
+  size_t smem = (use_cell && !coop && !len_kernel) ? (size_t)24 * threads * sizeof(R) : 0;
   int resident = 0;
-  if (coop)
+  if (len_kernel)
+    QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_len_kernel<R>, threads, 0));
+  else if (coop)
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_coop_kernel<R, NC>, threads, 0));
   else if (use_cell)
     QSL_CHECK_CUDA(
@@ -2286,7 +2861,10 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
   if (blocks < 1) blocks = 1;
   if (ev) QSL_CHECK_CUDA(cudaEventRecord(ev[0], stream));
   if (n_seeds > 0) {
-    if (coop) {
+    if (len_kernel) {
+      cell_len_kernel<R><<<blocks, threads, 0, stream>>>(P);
+      qsl::count_launch();
+    } else if (coop) {
       cell_coop_kernel<R, NC><<<blocks, threads, 0, stream>>>(P);
       qsl::count_launch();
     } else if (use_cell) {

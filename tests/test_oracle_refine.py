@@ -218,3 +218,22 @@ def test_replay_q_threshold_band(oracle_mod):
     assert np.array_equal(rep["key"], noisy["key"])
     narrow = oracle_mod.refine_replay(exact, sp, noisy["key"], noisy["origin"], band_rel=0.1 * eps)
     assert not np.array_equal(narrow["key"], noisy["key"])
+
+
+def test_replay_unsure_samples_follow_the_other_run(oracle_mod):
+    """A pair with a sample the evaluator marks as undetermined is decided by
+    the other run: values that differ arbitrarily at such samples (a line on a
+    separatrix, whose length depends on the integration) still replay."""
+    kw = dict(ndim=2, coarse_order=3, max_order=7, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), tau=0.05)
+    sp = oracle_mod.refine_spec(**kw)
+    odd = lambda k: np.array([(int(v) * 7919) % 13 == 0 for v in k])
+
+    def jumpy(x, k):
+        q, L = ramp_map(x)
+        return q, np.where(odd(k), L + 0.3, L)
+
+    other = oracle_mod.refine_replay(jumpy, sp)
+    plain = oracle_mod.refine_replay(lambda x, k: ramp_map(x), sp)
+    assert not np.array_equal(other["key"], plain["key"])
+    rep = oracle_mod.refine_replay(lambda x, k: ramp_map(x) + (odd(k),), sp, other["key"], other["origin"])
+    assert np.array_equal(rep["key"], other["key"]) and np.array_equal(rep["origin"], other["origin"])

@@ -51,13 +51,18 @@ def test_noalloc_leaves_device_memory_unchanged():
     """Free device memory (cudaMemGetInfo) is the same before and after two
     calls, once the first call has looked up the array's address and loaded
     the kernels; the same check catches qsl_trace_seeds, whose scratch comes
-    from the library's stream-ordered pool (kept cached after the call)."""
+    from the library's stream-ordered pool (kept cached after the call), on a
+    launch whose scratch (112 MB) is larger than any free space the pool's
+    blocks can hold after a trim."""
     from paper_1609_00724_gb300 import qsl
     F = _field(qsl)
     o = qsl.qsl_opts_default(tol_abs=1e-7, tol_rel=1e-7, integrator=2, retrace_q=0.0)
     n = 5000
     sd = torch.as_tensor(inputs.random_seeds(n, 33)).cuda()
     out = torch.empty(n * qsl.QSL_LINE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    n2 = 1 << 20
+    sd2 = torch.as_tensor(inputs.random_seeds(n2, 34)).cuda()
+    out2 = torch.empty(n2 * qsl.QSL_LINE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     qsl.qsl_trace_seeds_noalloc(F, sd, o, out)  # first call on this device
     torch.cuda.synchronize()
     qsl.qsl_trim_pool()
@@ -68,7 +73,7 @@ def test_noalloc_leaves_device_memory_unchanged():
     torch.cuda.synchronize()
     free1 = torch.cuda.mem_get_info()[0]
     assert free1 == free0, (free0, free1)
-    qsl.qsl_trace_seeds(F, sd, o, out=out)
+    qsl.qsl_trace_seeds(F, sd2, o, out=out2)
     torch.cuda.synchronize()
     free2 = torch.cuda.mem_get_info()[0]
     assert free2 < free1
