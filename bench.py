@@ -44,20 +44,51 @@ FIELD_SEED = 2
 # stage's share of the combinations (414 per step) and error norm (144 per
 # step) over 6.5 evaluations per step (85).
 # DRAM bytes per launch of the two tracer phases of the default workload
-# (4-charge field on 256^3, 1024^2 map refined to 4096^2): dram__bytes_read.sum
-# + dram__bytes_write.sum from one ncu capture (the coarse pass; the mean over
-# the 27 refinement passes). None where the kernel has changed since its
-# capture: the passes' three-lane kernel now evaluates its stages on the cell's
-# trilinear polynomial coefficients.
-TRAFFIC_COARSE_BYTES = 564.2e6
+# (4-charge field on 256^3, 1024^2 map refined to 4096^2):
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the
+# current kernels (summaries under profiles/); None until captured.
+TRAFFIC_COARSE_BYTES = None
 TRAFFIC_PASS_BYTES = None
 FLOP_PER_STAGE = {"ck": 246.0, "cell": 227.0}
 # length-only stage evaluation of the cell-wise kernels (trilinear values of 3
 # components 63, position scaling 3, the 3-component share of the stage
 # combinations and error norm 29)
 FLOP_PER_STAGE_LEN = 95.0
-# FP32 peak of the FMA pipe: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 FMA pipe from unit counts (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz):
+# context only; the roofline divides by the rate measured in the same run
+# (measure_peaks).
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# the tolerance the autotuner picks on this workload (used where no GPU runs
+# the tuner: the reference arm)
+TUNED_TOL = 1e-5
+# algorithmic gather of the cell-wise tracers: the 8 corner vertices of a cell
+# (8 x 16 B) once per cell entered
+GATHER_BYTES_PER_ENTRY = 128.0
+
+
+def measure_peaks(local):
+    """FP32 FMA and L2 read rates of this GPU from the package's own
+    microbenchmarks (CUDA events, fastest of several launches), with the SM
+    clock sampled meanwhile; no clock or power setting is read or changed."""
+    import ctypes as C
+
+    from paper_1609_00724_gb300 import build as _b
+    lib = C.CDLL(_b.PEAKS_LIB)
+    tf, ms_f, gb, ms_l = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    with ClockSampler(local) as clk:
+        rc1 = lib.qslpk_fp32_fma(C.c_int(2048), C.c_int(5), None, C.byref(tf), C.byref(ms_f))
+        rc2 = lib.qslpk_l2_read(C.c_int64(48 << 20), C.c_int(40), C.c_int(5), None, C.byref(gb), C.byref(ms_l))
+        time.sleep(0.3)
+    if rc1 or rc2:
+        raise RuntimeError("peak microbenchmarks failed")
+    c = clk.summary()
+    out = {"fp32_tflops": tf.value, "fp32_ms": ms_f.value, "l2_read_gbs": gb.value, "l2_ms": ms_l.value,
+           "l2_buffer_mb": 48, "clocks": c,
+           "how": "libqslpeaks.so: 8 independent FMA chains per thread, 152x8 blocks of 256; float4 __ldcg sweeps "
+                  "of a 48 MB buffer resident in L2, 152x4 blocks of 512; fastest of 5 launches (CUDA events)"}
+    if c.get("sm_mhz"):
+        out["fp32_flop_per_sm_cycle"] = tf.value * 1e12 / (c["sm_mhz"] * 1e6) / 152
+    return out
 
 
 def parse():
@@ -166,6 +197,8 @@ def make_field(seed, device, n):
 
 
 INTEGRATOR = {"cell": 2, "ck": 0}
+PEAK = {"fp32": FP32_NOMINAL_TFLOPS, "l2": None, "note": "nominal (not measured)"}
+PEAKS_RUN = None
 RUN = {"integrator": "cell", "tol": TOL}
 
 
@@ -213,21 +246,20 @@ def alloc(torch, coarse, device):
             "sg": torch.empty((eff, eff), dtype=torch.float32, device=device), "eff": eff}
 
 
-def oracle_sample_rate(gf_cpu, coarse, budget_s=15.0, seed=99):
-    """The FP64 oracle, as it stands, on a seeded subsample of the coarse map's
-    seeds at the bench tolerance, on all host cores. Returns (Q-points/s,
-    seeds, cores, seconds)."""
+def oracle_sample_rate(gf_cpu, seeds, tol, budget_s=15.0, seed=99):
+    """The FP64 oracle, as it stands, on seeded subsamples of `seeds` (S x 3)
+    at tolerance `tol`, on all host cores, until about budget_s seconds of
+    tracing. Returns (Q-points/s, seeds traced, cores, seconds)."""
     import oracle
     from paper_1609_00724_gb300 import inputs
     g = inputs.to_numpy64(gf_cpu)
     F = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
-    seeds = oracle.plane_seeds([0, 0, 0], [2, 0, 0], [0, 2, 0], coarse, coarse)
     cores = os.cpu_count() or 1
-    o = oracle.default_opts(tol_abs=TOL, tol_rel=TOL, nthreads=cores)
+    o = oracle.default_opts(tol_abs=tol, tol_rel=tol, nthreads=cores)
     done, t_used, m = 0, 0.0, 64 * cores
     rng_seed = seed
     while t_used < budget_s and done < len(seeds):
-        idx = inputs.subsample(len(seeds), m, rng_seed)
+        idx = inputs.subsample(len(seeds), min(m, len(seeds)), rng_seed)
         t0 = time.perf_counter()
         oracle.trace_seeds(F, seeds[idx], o)
         t_used += time.perf_counter() - t0
@@ -235,6 +267,15 @@ def oracle_sample_rate(gf_cpu, coarse, budget_s=15.0, seed=99):
         rng_seed += 1
         m = min(4 * m, max(64, int(m * budget_s / max(t_used, 1e-3))))
     return done / t_used, done, cores, t_used
+
+
+def sample_positions(qsl, keys, coarse):
+    """z = 0 plane positions of refinement sample keys (effective lattice)."""
+    eff = coarse << (P - P0)
+    p = int(np.log2(eff))
+    c = np.zeros((len(keys), 2), dtype=np.uint32)
+    qsl.qsl_hilbert_decode(np.ascontiguousarray(keys), 2, p, c)
+    return np.column_stack([(c[:, 0] + 0.5) / eff * 2 - 1, (c[:, 1] + 0.5) / eff * 2 - 1, np.zeros(len(keys))])
 
 
 def parity_sample(qsl, gf, gf_cpu, coarse, n=200):
@@ -322,7 +363,7 @@ def run_reference(args, rank, world):
     F = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
     seeds = oracle.plane_seeds([0, 0, 0], [2, 0, 0], [0, 2, 0], args.coarse, args.coarse)
     cores = os.cpu_count() or 1
-    o = oracle.default_opts(tol_abs=TOL, tol_rel=TOL, nthreads=cores)
+    o = oracle.default_opts(tol_abs=TUNED_TOL, tol_rel=TUNED_TOL, nthreads=cores)
     per_step = 256 * cores  # 4 of the oracle's 64-seed work chunks per thread
     for w in range(args.warmup):
         oracle.trace_seeds(F, seeds[inputs.subsample(len(seeds), per_step, 1000 + w)], o)
@@ -333,7 +374,8 @@ def run_reference(args, rank, world):
         oracle.trace_seeds(F, seeds[idx], o)
         t += time.perf_counter() - t0
     value = per_step * args.steps / t
-    sample = "%d seeded coarse-map seeds per step of the 1024^2 z=0 map, tol %g" % (per_step, TOL)
+    sample = ("%d seeded coarse-map seeds per step of the 1024^2 z=0 map, tol %g (the tolerance the GPU arm's "
+              "autotuner picks on this workload)" % (per_step, TUNED_TOL))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -390,13 +432,13 @@ def run_volume(args, qsl, torch, dev, rank, world, local):
                        "tol": RUN["tol"], "integrator": RUN["integrator"], "retraced_last_step": st["retraced"],
                        "l2": "inputs larger than L2 (906 MB packed field)"},
             "clocks": clk.summary(), "gpu_launches": qsl.qsl_kernel_launches() - l0,
-            "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": PEAK["fp32"], "unit": "TFLOP/s",
+                         "frac": ach / PEAK["fp32"], "traffic": None,
                          "kernel": "%s (512x512x256 volume, one launch)" % (
                              "cell_kernel_f32<9>" if RUN["integrator"] == "cell" else "trace_kernel<float,9>"),
                          "kernel_ms": st["kernel_ms"], "stage_evals": st["stage_evals"],
                          "flop_per_stage": fps,
-                         "peak_note": "FP32 FMA pipe at 2.07 GHz (derived from unit counts)"}}
+                         "peak_note": "of measured: %s" % PEAK["note"]}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -663,6 +705,11 @@ def main():
     dev = torch.device("cuda", local)
     from paper_1609_00724_gb300 import qsl
     qsl.lib()
+    global PEAKS_RUN
+    PEAKS_RUN = measure_peaks(local)
+    PEAK.update(fp32=PEAKS_RUN["fp32_tflops"], l2=PEAKS_RUN["l2_read_gbs"],
+                note="%.1f TFLOP/s FP32, %.0f GB/s L2 read at a median %s MHz SM clock" % (
+                    PEAKS_RUN["fp32_tflops"], PEAKS_RUN["l2_read_gbs"], PEAKS_RUN["clocks"].get("sm_mhz")))
     if args.shape:
         RUN["shape"] = tuple(int(v) for v in args.shape.split(","))
     if args.hmax:
@@ -753,13 +800,25 @@ def main():
     achieved_tflops = st["stage_evals"] * flop_per_stage / (kms / 1000.0) / 1e12
     kname = "cell_kernel_f32<9>" if RUN["integrator"] == "cell" else "trace_kernel<float,9>"
     default_workload = args.grid == 256 and args.coarse == 1024 and RUN["integrator"] == "cell"
-    roof_coarse = {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                   "frac": achieved_tflops / FP32_PEAK_TFLOPS,
+    peak_note = "of measured: %s in this run (%s)" % ("FP32 FMA microbenchmark" if PEAK["l2"] else "nominal",
+                                                    PEAK["note"])
+
+    def gather(entries, ms):
+        """Algorithmic gather rate (8 corner vertices per cell entered) against the measured L2 read peak."""
+        if not PEAK["l2"] or ms <= 0:
+            return None
+        a = entries * GATHER_BYTES_PER_ENTRY / (ms / 1000.0) / 1e9
+        return {"bound": "l2", "achieved": a, "peak": PEAK["l2"], "unit": "GB/s", "frac": a / PEAK["l2"],
+                "bytes_per_entry": GATHER_BYTES_PER_ENTRY, "entries": int(entries),
+                "peak_note": "of measured: L2 read microbenchmark in this run"}
+
+    roof_coarse = {"bound": "alu", "achieved": achieved_tflops, "peak": PEAK["fp32"], "unit": "TFLOP/s",
+                   "frac": achieved_tflops / PEAK["fp32"],
                    "traffic": TRAFFIC_COARSE_BYTES if default_workload else None,
                    "kernel": kname + " (%d^2 coarse map, one launch)" % args.coarse, "kernel_ms": kms,
                    "stage_evals": st["stage_evals"], "accepted": st["accepted"], "rejected": st["rejected"],
-                   "landings": st["landing"], "flop_per_stage": flop_per_stage,
-                   "peak_note": "FP32 FMA pipe at 2.07 GHz (derived from unit counts)"}
+                   "landings": st["landing"], "flop_per_stage": flop_per_stage, "peak_note": peak_note,
+                   "gather": gather(st["landing"] + 2 * N, kms)}
     # refinement passes: few lines per launch, each launch as long as its
     # longest line (latency-bound); average over the step's passes, which
     # trace lengths only with the FLL-jump criterion
@@ -768,27 +827,30 @@ def main():
     pass_flop = FLOP_PER_STAGE_LEN if (len_only and RUN["integrator"] == "cell") else flop_per_stage
     pass_tflops = (rs["pass_stage_evals"] * pass_flop / (rs["passes_ms"] / 1000.0) / 1e12
                    if rs["passes_ms"] > 0 else 0.0)
-    roof_passes = {"bound": "alu", "achieved": pass_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                   "frac": pass_tflops / FP32_PEAK_TFLOPS,
+    roof_passes = {"bound": "alu", "achieved": pass_tflops, "peak": PEAK["fp32"], "unit": "TFLOP/s",
+                   "frac": pass_tflops / PEAK["fp32"],
                    "traffic": TRAFFIC_PASS_BYTES if default_workload else None,
-                   "kernel": (("cell_coop_kernel<float,%d>" % (3 if len_only else 9)) if RUN["integrator"] == "cell"
-                              else kname) + " (%srefinement passes, %d per step)"
+                   "kernel": (("cell_len_kernel<float>" if len_only else "cell_coop_kernel<float,9>")
+                              if RUN["integrator"] == "cell" else kname) + " (%srefinement passes, %d per step)"
                    % ("length-only " if len_only else "", rs["passes"]), "kernel_ms": pass_ms,
                    "stage_evals": rs["pass_stage_evals"] // max(rs["passes"], 1), "flop_per_stage": pass_flop,
-                   "peak_note": "FP32 FMA pipe at 2.07 GHz (derived from unit counts); launches are bound by "
-                                "the latency of their longest line, not by the pipe"}
+                   "peak_note": peak_note + "; launches are bound by the latency of their longest line, not by the "
+                                            "pipe",
+                   "gather": gather((rs["pass_landings"] + 2 * rs["pass_lines"]) / max(rs["passes"], 1), pass_ms)}
     passes_dominate = rs["passes_ms"] > rs["coarse_ms"]
     step_breakdown = {"device_ms": rs["total_ms"], "coarse_trace_ms": rs["coarse_ms"],
                       "pass_trace_ms": rs["passes_ms"], "deferred_trace_ms": rs["deferred_ms"],
                       "passes": rs["passes"], "iters": rs["iters"], "pass_lines": rs["pass_lines"],
                       "other_ms": rs["total_ms"] - rs["coarse_ms"] - rs["passes_ms"] - rs["deferred_ms"]}
 
-    # --- end to end through the C ABI with host buffers (pinned), copies inside
+    # --- end to end through the C ABI with host buffers (pinned), copies inside:
+    # field load, refinement with conversion, and the FLEDGE of the converted
+    # length grid, as in the timed step; median of three runs
     eff = args.coarse << (P - P0)
     host = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in bufs.items() if k != "eff"}
     hb = [a.cpu().pin_memory() for a in (gf.bx, gf.by, gf.bz)]
     e2e_t = []
-    for it in range(2):
+    for it in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Fh = qsl.qsl_load_field(hb[0].numpy(), hb[1].numpy(), hb[2].numpy(), gf.xc, gf.yc, gf.zc,
@@ -796,37 +858,44 @@ def main():
         n_h, _, traced_h, _ = qsl.qsl_refine(Fh, spec(qsl, args.coarse), opts(qsl), host["key"].numpy(),
                                              host["q"].numpy(), host["L"].numpy(), host["faces"].numpy(),
                                              host["st"].numpy(), 0, host["qg"].numpy(), host["lg"].numpy())
+        qsl.qsl_fledge(host["lg"].numpy().reshape(eff, eff), host["sg"].numpy())
         e2e_t.append(time.perf_counter() - t0)
         del Fh
-    e2e_value = traced_h / min(e2e_t)
-    h2d = sum(a.numel() * a.element_size() for a in hb)
-    d2h = n_h * (8 + 4 + 4 + 2 + 1) + 2 * eff * eff * 4
+    e2e_value = traced_h / float(np.median(e2e_t))
+    h2d = sum(a.numel() * a.element_size() for a in hb) + eff * eff * 4  # the field; the length grid to FLEDGE
+    d2h = n_h * (8 + 4 + 4 + 2 + 1) + 3 * eff * eff * 4  # samples; Q, L and FLEDGE grids
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "4-charge potential field %d^3 FP32, %d^2 z=0 Q map refined to %d^2 effective"
                                    % (args.grid, args.coarse, eff),
-                       "tol": RUN["tol"], "integrator": RUN["integrator"], "tau": TAU, "coarse_order": int(np.log2(args.coarse)), "max_order":
-                           int(np.log2(eff)), "interp": "paper (normalise first)", "precision": "FP32 trace, FP64 Q",
+                       "tol": RUN["tol"], "integrator": RUN["integrator"], "tau": TAU,
+                       "coarse_order": int(np.log2(args.coarse)), "max_order": int(np.log2(eff)),
+                       "interp": "paper (normalise first)", "precision": "FP32 trace, FP64 Q",
                        "l2": "inputs larger than L2 (268 MB packed field)", "parallelism": "replicas x%d" % world,
                        "autotune": tune_rep,
                        "samples_per_step": info.get("samples"), "refine_iters": info.get("iters"),
                        "q_points_per_step": traced_total // max(args.steps, 1)},
             "clocks": clk.summary(),
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "runs_s": e2e_t},
             "gpu_launches": launches,
             "roofline": roof_passes if passes_dominate else roof_coarse,
             "roofline_other": roof_coarse if passes_dominate else roof_passes,
+            "peaks": PEAKS_RUN,
             "step_breakdown": step_breakdown}
     if rank == 0 and not args.no_cpu_baseline:
         gf_cpu = make_field(field_seed, "cpu", args.grid)
-        rate, nseeds, cores, secs = oracle_sample_rate(gf_cpu, args.coarse)
+        n_s = int(info.get("samples") or 0)
+        seeds_all = sample_positions(qsl, bufs["key"][:n_s].cpu().numpy().view(np.uint64), args.coarse)
+        rate, nseeds, cores, secs = oracle_sample_rate(gf_cpu, seeds_all, RUN["tol"])
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "%d seeded seeds of the %d^2 coarse map, tol %g, %.1f s"
-                                          % (nseeds, args.coarse, TOL, secs)}
+                                "sample": "%d seeded samples of the GPU step's %d refined-map samples (coarse and "
+                                          "refined in proportion), tol %g (the autotuned GPU tolerance), %.1f s"
+                                          % (nseeds, n_s, RUN["tol"], secs)}
         line["parity"] = parity_sample(qsl, gf, gf_cpu, args.coarse)
-        line["parity_refined"] = refined_parity(bufs, int(info.get("samples") or 0), gf_cpu, args.coarse)
+        line["parity_refined"] = refined_parity(bufs, n_s, gf_cpu, args.coarse)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -280,7 +280,9 @@ typedef struct qsl_refine_stats {
   int64_t coarse_stage_evals, pass_stage_evals, deferred_stage_evals; /* FP32 tracer
                                        stage evaluations (the first 512 trace calls)     */
   int32_t passes, iters;            /* refinement pass trace calls, iterations           */
-} qsl_refine_stats; /* 80 bytes */
+  int64_t coarse_landings, pass_landings, deferred_landings; /* plane crossings of the
+                                       cell-wise tracers (cell entries and ends), same calls */
+} qsl_refine_stats; /* 104 bytes */
 int qsl_last_refine_stats(qsl_refine_stats* out);
 
 /* ---- batches of fields and cuts: one persistent launch, captured plans ---------
@@ -347,9 +349,11 @@ int qsl_cnn_nparams(void);
  * workload:
  *  - the loosest tolerance in {1e-5, 1e-6, 1e-7} (FP32 tracing; FP64:
  *    {1e-6, ..., 1e-9}) whose Q (relative error <= 2e-4 for Q < 1e6), lengths
- *    (|dL| <= 2e-6 max(L, smallest spacing)) and end faces (<= 0.1 % of lines
- *    differ) agree with an FP64 trace of the same seeds at tol 1e-10 (a fifth
- *    of the 1e-3 / 1e-5 accuracy bar). Candidates run the caller's precision
+ *    (|dL| <= 2e-6 L for lines of at least the smallest spacing h) and end
+ *    faces (<= 0.1 % of lines differ) agree with an FP64 trace of the same
+ *    seeds at tol 1e-10 (a fifth of the 1e-3 / 1e-5 accuracy bar); lines
+ *    shorter than h, whose length error is set by the FP32 field samples and
+ *    not by the tolerance, are held to |dL| <= 1e-5 h. Candidates run the caller's precision
  *    policy, FP64 retrace above retrace_q included. When none passes, the
  *    tightest is taken and report->passed is 0;
  *  - the step cap: the requested h_max, or 4 smallest spacings when that also
@@ -377,6 +381,8 @@ typedef struct qsl_tune_report {
   int32_t passed;        /* 1: the chosen tolerance met the bounds; 0: none of
                             the candidates did and the tightest was taken      */
   int32_t shape_reps;    /* copies of the sample in each shape timing         */
+  double l_err_subcell;  /* worst length error of lines shorter than one cell,
+                            in cells (held to the full bar, 1e-5)              */
 } qsl_tune_report;
 int qsl_autotune(const qsl_field* field, const double* seeds, int64_t S, qsl_opts* opts, qsl_tune_report* report,
                  void* stream);

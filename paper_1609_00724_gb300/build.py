@@ -35,6 +35,21 @@ def _stale(lib, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+PEAKS_SRC = os.path.join(CSRC, "peaks", "peaks.cu")
+PEAKS_LIB = os.path.join(HERE, "libqslpeaks.so")
+
+
+def build_peaks(force=False):
+    """The benchmark's peak-rate microbenchmarks (FP32 FMA, L2 read), a
+    separate small library: measurement utilities, not part of the method."""
+    if not force and not _stale(PEAKS_LIB, [PEAKS_SRC, __file__]):
+        return PEAKS_LIB
+    subprocess.check_call([nvcc(), *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", PEAKS_SRC,
+                           "-o", PEAKS_LIB + ".tmp"])
+    os.replace(PEAKS_LIB + ".tmp", PEAKS_LIB)
+    return PEAKS_LIB
+
+
 def build(force=False, verbose=False, extra=()):
     os.makedirs(OUT, exist_ok=True)
     srcs = sources()

@@ -1058,9 +1058,16 @@ int qsl_last_refine_stats(qsl_refine_stats* out) {
   std::vector<DeviceStats> h(ns);
   if (ns) QSL_CHECK_CUDA(cudaMemcpy(h.data(), rk.snap, sizeof(DeviceStats) * ns, cudaMemcpyDeviceToHost));
   for (size_t i = 0; i < ns; ++i) {
-    if (rk.kind[i] == 0) out->coarse_stage_evals += (int64_t)h[i].stage_evals;
-    else if (rk.kind[i] == 1) out->pass_stage_evals += (int64_t)h[i].stage_evals;
-    else out->deferred_stage_evals += (int64_t)h[i].stage_evals;
+    if (rk.kind[i] == 0) {
+      out->coarse_stage_evals += (int64_t)h[i].stage_evals;
+      out->coarse_landings += (int64_t)h[i].landing;
+    } else if (rk.kind[i] == 1) {
+      out->pass_stage_evals += (int64_t)h[i].stage_evals;
+      out->pass_landings += (int64_t)h[i].landing;
+    } else {
+      out->deferred_stage_evals += (int64_t)h[i].stage_evals;
+      out->deferred_landings += (int64_t)h[i].landing;
+    }
   }
   out->iters = rk.iters;
   return QSL_OK;

@@ -50,12 +50,14 @@ int time_trace(const qsl_field* f, const double* seeds, int64_t S, const qsl_opt
 }
 
 // Worst relative errors of `got` against `ref` (Q below 1e6 and both ends on
-// the same faces). Length errors are taken relative to max(L, cell): a line
-// shorter than a cell that leaves at a grazing angle has a length set by a
-// cancellation in the field samples, so it is held to an absolute bound.
+// the same faces). Lengths: *el over lines of at least one cell (relative);
+// *es over shorter lines, in units of one cell: a line shorter than a cell that
+// leaves at a grazing angle has a length set by a cancellation in the FP32
+// field samples, whatever the step tolerance, so it is held to the absolute
+// bound of the parity bar and does not decide the tolerance.
 void errors(const std::vector<qsl_line>& got, const std::vector<qsl_line>& ref, int q_form, double cell, double* eq,
-            double* el, double* face_mismatch) {
-  double wq = 0, wl = 0;
+            double* el, double* es, double* face_mismatch) {
+  double wq = 0, wl = 0, ws = 0;
   int64_t fm = 0;
   for (size_t i = 0; i < ref.size(); ++i) {
     const qsl_line& a = got[i];
@@ -67,11 +69,15 @@ void errors(const std::vector<qsl_line>& got, const std::vector<qsl_line>& ref, 
     double qa = q_form == QSL_Q_FOOT ? a.q_foot : (q_form == QSL_Q_DET ? a.q_det : a.q_perp);
     double qb = q_form == QSL_Q_FOOT ? b.q_foot : (q_form == QSL_Q_DET ? b.q_det : b.q_perp);
     if (std::isfinite(qb) && qb < 1e6) wq = fmax(wq, fabs(qa / qb - 1.0));
-    if (std::isfinite(b.length))
-      wl = fmax(wl, fabs((double)a.length - (double)b.length) / fmax((double)b.length, cell));
+    if (std::isfinite(b.length)) {
+      const double d = fabs((double)a.length - (double)b.length);
+      if ((double)b.length >= cell) wl = fmax(wl, d / (double)b.length);
+      else ws = fmax(ws, d / cell);
+    }
   }
   *eq = wq;
   *el = wl;
+  *es = ws;
   *face_mismatch = ref.empty() ? 0.0 : (double)fm / (double)ref.size();
 }
 
@@ -125,15 +131,15 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
   const double* tols = fp64 ? tols64 : tols32;
   const int n_tols = fp64 ? 4 : 3;
   qsl_opts base = *opts;
-  double chosen_tol = tols[n_tols - 1], eq = 0, el = 0, fm = 0;
+  double chosen_tol = tols[n_tols - 1], eq = 0, el = 0, es = 0, fm = 0;
   int passed = 0;
   for (int k = 0; k < n_tols; ++k) {
     qsl_opts c = base;
     c.tol_abs = c.tol_rel = tols[k];
     if ((rc = time_trace(f, seeds, S, &c, d.p, s, &ms))) return rc;
     QSL_CHECK_CUDA(cudaMemcpy(got.data(), d.p, sizeof(qsl_line) * S, cudaMemcpyDeviceToHost));
-    errors(got, ref, opts->q_form, f->cell, &eq, &el, &fm);
-    if (eq <= 2e-4 && el <= 2e-6 && fm <= 1e-3) {
+    errors(got, ref, opts->q_form, f->cell, &eq, &el, &es, &fm);
+    if (eq <= 2e-4 && el <= 2e-6 && es <= 1e-5 && fm <= 1e-3) {
       chosen_tol = tols[k];
       passed = 1;
       break;
@@ -146,11 +152,11 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
     qsl_opts c = base;
     c.tol_abs = c.tol_rel = chosen_tol;
     c.h_max = 4.0;
-    double eq4 = 0, el4 = 0, fm4 = 0;
+    double eq4 = 0, el4 = 0, es4 = 0, fm4 = 0;
     if ((rc = time_trace(f, seeds, S, &c, d.p, s, &ms))) return rc;
     QSL_CHECK_CUDA(cudaMemcpy(got.data(), d.p, sizeof(qsl_line) * S, cudaMemcpyDeviceToHost));
-    errors(got, ref, opts->q_form, f->cell, &eq4, &el4, &fm4);
-    if (eq4 <= 2e-4 && el4 <= 2e-6 && fm4 <= 1e-3) hmaxes[n_hmax++] = 4.0;
+    errors(got, ref, opts->q_form, f->cell, &eq4, &el4, &es4, &fm4);
+    if (eq4 <= 2e-4 && el4 <= 2e-6 && es4 <= 1e-5 && fm4 <= 1e-3) hmaxes[n_hmax++] = 4.0;
   }
   // launch shape and step cap: fastest of the candidates at the chosen
   // tolerance (best of 2), on the sample repeated to at least 16 waves of
@@ -215,6 +221,7 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
   rep.tol = chosen_tol;
   rep.q_err = eq;
   rep.l_err = el;
+  rep.l_err_subcell = es;
   rep.face_mismatch = fm;
   rep.sample_ms = best;
   rep.sample_seeds = S;

@@ -61,7 +61,8 @@ class qsl_refine_stats(C.Structure):
     _fields_ = [("total_ms", C.c_double), ("coarse_ms", C.c_double), ("passes_ms", C.c_double),
                 ("deferred_ms", C.c_double), ("coarse_lines", C.c_int64), ("pass_lines", C.c_int64),
                 ("coarse_stage_evals", C.c_int64), ("pass_stage_evals", C.c_int64),
-                ("deferred_stage_evals", C.c_int64), ("passes", C.c_int32), ("iters", C.c_int32)]
+                ("deferred_stage_evals", C.c_int64), ("passes", C.c_int32), ("iters", C.c_int32),
+                ("coarse_landings", C.c_int64), ("pass_landings", C.c_int64), ("deferred_landings", C.c_int64)]
 
 
 class qsl_refine_spec(C.Structure):
@@ -92,7 +93,8 @@ class qsl_tune_report(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_min", C.c_int32),
                 ("cached", C.c_int32), ("tol", C.c_double), ("q_err", C.c_double), ("l_err", C.c_double),
                 ("face_mismatch", C.c_double), ("sample_ms", C.c_double), ("sample_seeds", C.c_int64),
-                ("h_max", C.c_double), ("passed", C.c_int32), ("shape_reps", C.c_int32)]
+                ("h_max", C.c_double), ("passed", C.c_int32), ("shape_reps", C.c_int32),
+                ("l_err_subcell", C.c_double)]
 
 
 _lib = None

@@ -34,6 +34,16 @@ def test_opts_default_and_struct_sizes():
     o = qsl.qsl_opts_default()
     assert o.integrator == qsl.QSL_RKCK54 and o.tol_abs == 1e-2 and o.retrace_q == 1e6
     assert C.sizeof(qsl.qsl_opts) == 176
-    assert C.sizeof(qsl.qsl_refine_stats) == 80
+    assert C.sizeof(qsl.qsl_refine_stats) == 104
+    assert C.sizeof(qsl.qsl_samples) == 72
     assert qsl.QSL_LINE_DTYPE.itemsize == 112
     assert qsl.lib().qsl_last_error() == b""
+
+
+def test_peak_microbenchmarks_library_exports():
+    """The benchmark's peak-rate microbenchmarks build into their own library."""
+    from paper_1609_00724_gb300 import build
+    path = build.build_peaks()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (qslpk_\w+)", out))
+    assert {"qslpk_fp32_fma", "qslpk_l2_read"} <= exported, exported

@@ -95,7 +95,7 @@ def test_autotune_picks_valid_shape_and_tolerance(qsl):
     rep = qsl.qsl_autotune(items[1][0], seeds, o)
     assert rep["tol"] in (1e-5, 1e-6, 1e-7)
     assert rep["passed"] == 1
-    assert rep["q_err"] <= 2e-4 and rep["l_err"] <= 2e-6 and rep["cached"] == 0
+    assert rep["q_err"] <= 2e-4 and rep["l_err"] <= 2e-6 and rep["l_err_subcell"] <= 1e-5 and rep["cached"] == 0
     assert o.tol_rel == rep["tol"] and o.warps_per_block == rep["warps_per_block"]
     assert rep["h_max"] in (2.0, 4.0) and o.h_max == rep["h_max"]
     # shapes are timed on the sample repeated to at least 16 x 384 line
