@@ -450,12 +450,11 @@ def run_batch(args, qsl, torch, dev, rank, world, local):
     (plan), with the launch shape and tolerance picked by the autotuner on a
     sample of the first cut."""
     from paper_1609_00724_gb300 import inputs
-    rng = np.random.Generator(np.random.PCG64(replica_seed(4, rank)))
     items, fields = [], []
-    for i in range(64):
-        n = int(rng.integers(64, 257))
-        m = int(rng.integers(256, 1025))
-        gf = inputs.charge_field(inputs.random_charges(4, replica_seed(4000 + i, rank)), n, dtype=torch.float32,
+    for i, (n, m, fseed) in enumerate(inputs.batch64_specs()):
+        if rank:  # replica r: its own draw of sizes and fields
+            n, m, _ = inputs.batch64_specs(replica_seed(4, rank))[i]
+        gf = inputs.charge_field(inputs.random_charges(4, replica_seed(fseed, rank)), n, dtype=torch.float32,
                                  device=dev, slab=64)
         F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
         del gf

@@ -1051,23 +1051,30 @@ __device__ __forceinline__ void trilinear_coeffs(const R* cv, R ihc, R* a) {
 // Right-hand side inside one cell from the coefficients of the cell's
 // trilinear polynomials (8 per component c, corner form turned into
 // a0 + a1 u + a2 v + a3 w + a4 uv + a5 uw + a6 vw + a7 uvw once per cell entry),
-// held in shared memory with a stride of one block. Deviations are carried in
+// held in shared memory as two 4-vectors per component with a stride of one
+// block (six vector loads per stage, consecutive lanes on consecutive
+// 16-byte words). Deviations are carried in
 // cell units (du_j = dx_j / h_j). Normalise-first fields: the coefficients of
 // component c are pre-scaled by 1/h_c, so the polynomial's value is the
 // position derivative in cell units and its gradient in (u, v, w), applied to
 // the deviations, their derivative in cell units; no scaling per stage. Raw
 // fields (unscaled coefficients of B): b = B/|B| and its gradient
 // (I - b b^T) grad B / |B| at the point, then the 1/h_c row scaling.
+// Vector of 4 coefficients in shared memory (one 16-byte load per float4).
+template <class R>
+struct C4 {
+  typedef typename V4<R>::type type;
+};
+
 template <class R, int NC>
-__device__ __forceinline__ void cell_rhs_poly(const R* __restrict__ cs, int st, bool raw, const R* ih, const R* y,
-                                              R* k) {
+__device__ __forceinline__ void cell_rhs_poly(const typename C4<R>::type* __restrict__ cs, int st, bool raw,
+                                              const R* ih, const R* y, R* k) {
   const R u = y[0], v = y[1], w = y[2];
   R val[3], d[3][3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const R* a = cs + (8 * c) * st;
-    const R a0 = a[0], a1 = a[st], a2 = a[2 * st], a3 = a[3 * st], a4 = a[4 * st], a5 = a[5 * st], a6 = a[6 * st],
-            a7 = a[7 * st];
+    const typename C4<R>::type lo = cs[(2 * c) * st], hi = cs[(2 * c + 1) * st];
+    const R a0 = lo.x, a1 = lo.y, a2 = lo.z, a3 = lo.w, a4 = hi.x, a5 = hi.y, a6 = hi.z, a7 = hi.w;
     const R p0 = fma(a1, u, a0), p1 = fma(a4, u, a2), p2 = fma(a5, u, a3), p3 = fma(a7, u, a6);
     const R q1 = fma(p3, v, p2);
     val[c] = fma(q1, w, fma(p1, v, p0));
@@ -1128,9 +1135,10 @@ __device__ __forceinline__ void dev_to_domain(R* y, const R* hh3) {
 
 template <class R, int NC>
 __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  typedef typename C4<R>::type CV;
   const int st = blockDim.x;
-  R* cs = reinterpret_cast<R*>(smem_raw) + threadIdx.x;
+  CV* cs = reinterpret_cast<CV*>(smem_raw) + threadIdx.x;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -1303,8 +1311,17 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) cv[j] = R(c == 0 ? q[j].x : (c == 1 ? q[j].y : q[j].z));
           trilinear_coeffs<R>(cv, E->F.raw ? R(1) : ih[c], co);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) cs[(8 * c + j) * st] = co[j];
+          CV lo, hi;
+          lo.x = co[0];
+          lo.y = co[1];
+          lo.z = co[2];
+          lo.w = co[3];
+          hi.x = co[4];
+          hi.y = co[5];
+          hi.z = co[6];
+          hi.w = co[7];
+          cs[(2 * c) * st] = lo;
+          cs[(2 * c + 1) * st] = hi;
         }
         cell_rhs_poly<R, NC>(cs, st, E->F.raw, ih, y, k1);
         c_stage += 1;
@@ -1369,12 +1386,16 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
       cell_rhs_poly<R, NC>(cs, st, E->F.raw, ih, t, k7);
       c_stage += 6;
       steps += 1;
+      // the error estimate's and the continuous extension's weights, scaled by the step
+      const R e1 = hh * R(DE1), e3 = hh * R(DE3), e4 = hh * R(DE4), e5 = hh * R(DE5), e6 = hh * R(DE6),
+              e7 = hh * R(DE7);
+      const R w1 = hh * R(DD1), w3 = hh * R(DD3), w4 = hh * R(DD4), w5 = hh * R(DD5), w6 = hh * R(DD6),
+              w7 = hh * R(DD7);
       R err = 0;
       bool finite = true;
 #pragma unroll
       for (int i = 0; i < NC; ++i) {
-        R e = fabs(hh * (R(DE1) * k1[i] + R(DE3) * k3[i] + R(DE4) * k4[i] + R(DE5) * k5[i] + R(DE6) * k6[i] +
-                         R(DE7) * k7[i]));
+        R e = fabs(fma(e7, k7[i], fma(e6, k6[i], fma(e5, k5[i], fma(e4, k4[i], fma(e3, k3[i], e1 * k1[i]))))));
         if (!isfinite(t[i])) finite = false;
         R ya, yb;
         if (i < 3) {
@@ -1426,10 +1447,8 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
           R sg = up ? R(1) : R(-1);  // sg * f > 0 beyond the plane
           R k1a = a == 0 ? k1[0] : (a == 1 ? k1[1] : k1[2]);
           R k7a = a == 0 ? k7[0] : (a == 1 ? k7[1] : k7[2]);
-          R c4 = hh * (R(DD1) * k1a + R(DD3) * (a == 0 ? k3[0] : (a == 1 ? k3[1] : k3[2])) +
-                       R(DD4) * (a == 0 ? k4[0] : (a == 1 ? k4[1] : k4[2])) +
-                       R(DD5) * (a == 0 ? k5[0] : (a == 1 ? k5[1] : k5[2])) +
-                       R(DD6) * (a == 0 ? k6[0] : (a == 1 ? k6[1] : k6[2])) + R(DD7) * k7a);
+          R c4 = fma(w7, k7a, fma(w6, sel3(a, k6[0], k6[1], k6[2]), fma(w5, sel3(a, k5[0], k5[1], k5[2]),
+                 fma(w4, sel3(a, k4[0], k4[1], k4[2]), fma(w3, sel3(a, k3[0], k3[1], k3[2]), w1 * k1a)))));
           R bspl = hh * k1a - dya;
           R c3 = dya - hh * k7a - bspl;
           // The offset along the axis is t * P(t) with the cubic
@@ -1494,8 +1513,7 @@ __device__ __forceinline__ void cell_trace(const TraceParams<R>& P) {
 #pragma unroll
           for (int i = 0; i < NC; ++i)
             y[i] += y_at<R>(th, dy[i], hh * k1[i], hh * k7[i],
-                            hh * (R(DD1) * k1[i] + R(DD3) * k3[i] + R(DD4) * k4[i] + R(DD5) * k5[i] +
-                                  R(DD6) * k6[i] + R(DD7) * k7[i]));
+                            fma(w7, k7[i], fma(w6, k6[i], fma(w5, k5[i], fma(w4, k4[i], fma(w3, k3[i], w1 * k1[i]))))));
           bool dom = up_c ? sel3(ax_c, hi_dom[0], hi_dom[1], hi_dom[2]) : sel3(ax_c, lo_dom[0], lo_dom[1], lo_dom[2]);
           R target = up_c ? sel3(ax_c, hi_pl[0], hi_pl[1], hi_pl[2]) : sel3(ax_c, lo_pl[0], lo_pl[1], lo_pl[2]);
           if (ax_c == 0) y[0] = target;
@@ -2554,7 +2572,8 @@ __device__ void end_terms(const FieldView<S>& F, const double* x, const double* 
   interp<double, S, false, true>(F, x[0], x[1], x[2], I);
   r.bmag = I.m;
   double m = sqrt(dot3(I.b, I.b));
-  double u[3] = {I.b[0] / m, I.b[1] / m, I.b[2] / m};
+  const double rm = 1.0 / m;  // one FP64 division per end
+  double u[3] = {I.b[0] * rm, I.b[1] * rm, I.b[2] * rm};
   // Sec. "Squashing factor calculation": dx_perp = dx - b (b.dx), b normalised
   double ud1 = dot3(u, d1), ud2 = dot3(u, d2);
   double ap[3], bp[3];
@@ -2573,9 +2592,11 @@ __device__ void end_terms(const FieldView<S>& F, const double* x, const double* 
     int a = face >> 1;
     if (u[a] != 0.0) {
       double af[3], bf[3];
+      const double ru = 1.0 / u[a];
+      const double s1 = d1[a] * ru, s2 = d2[a] * ru;
       for (int i = 0; i < 3; ++i) {
-        af[i] = d1[i] - u[i] * (d1[a] / u[a]);
-        bf[i] = d2[i] - u[i] * (d2[a] / u[a]);
+        af[i] = d1[i] - u[i] * s1;
+        bf[i] = d2[i] - u[i] * s2;
       }
       r.Af = dot3(af, af);
       r.Bf = dot3(bf, bf);
@@ -2633,13 +2654,14 @@ __global__ void __launch_bounds__(128) assemble_kernel(const __grid_constant__ A
       bf = tf.bmag;
       bb = tb.bmag;
       double br = tf.A * tb.B + tb.A * tf.B - 2.0 * tb.C * tf.C;
-      q_perp = bf * bb / (b0 * b0) * br;  // Eq. finalQ
+      const double rb0 = 1.0 / b0, rb02 = rb0 * rb0;
+      q_perp = bf * bb * rb02 * br;  // Eq. finalQ
       q_det = br / sqrt((tf.A * tf.B - tf.C * tf.C) * (tb.A * tb.B - tb.C * tb.C));
-      ff = bf / b0 * tf.cross - 1.0;
-      fb = bb / b0 * tb.cross - 1.0;
+      ff = bf * rb0 * tf.cross - 1.0;
+      fb = bb * rb0 * tb.cross - 1.0;
       if (tf.foot_ok && tb.foot_ok) {
         double brf = tf.Af * tb.Bf + tb.Af * tf.Bf - 2.0 * tb.Cf * tf.Cf;
-        q_foot = tf.bn * tb.bn / (b0 * b0) * brf;
+        q_foot = tf.bn * tb.bn * rb02 * brf;
       }
       if (P.out.skip_open && open) q_perp = q_foot = q_det = NaN;
     }

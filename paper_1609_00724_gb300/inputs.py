@@ -120,3 +120,16 @@ def subsample(n, count, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     count = min(count, n)
     return np.sort(rng.choice(n, size=count, replace=False))
+
+
+def batch64_specs(seed=4, count=64):
+    """The 64-field batch workload: (grid edge n, cut edge m, field seed) per
+    field, n ~ U{64..256} and m ~ U{256..1024} drawn in turn from one PCG64
+    stream with `seed`; field i's charges use seed 1000 * seed + i."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        n = int(rng.integers(64, 257))
+        m = int(rng.integers(256, 1025))
+        out.append((n, m, 1000 * seed + i))
+    return out

@@ -105,3 +105,52 @@ def test_autotune_picks_valid_shape_and_tolerance(qsl):
     o2 = qsl.qsl_opts_default(integrator=qsl.QSL_DOPRI5_CELL)
     rep2 = qsl.qsl_autotune(items[1][0], seeds, o2)
     assert rep2["cached"] == 1 and o2.refill_min == rep["refill_min"] and o2.h_max == rep["h_max"]
+
+
+def test_config4_batch64_full_size_sampled(qsl, oracle_mod):
+    """The 64-field batch at full size, as the bench runs it: 64 independently
+    seeded 4-charge fields with grid edges n ~ U{64..256} and z = 0 cuts of
+    m x m seeds, m ~ U{256..1024} (about 34 M seeds), autotuned on a sample of
+    the first cut, in one persistent launch recorded into a CUDA graph and
+    replayed twice; ten seeded pixels of every field against the FP64 oracle."""
+    specs = inputs.batch64_specs()
+    items, gfs = [], []
+    for n, m, fseed in specs:
+        gf = inputs.charge_field(inputs.random_charges(4, fseed), n, dtype=torch.float32, device="cuda", slab=64)
+        F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
+        items.append((F, (0, 0, 0), (2, 0, 0), (0, 2, 0), m, m))
+        gfs.append(gf)
+    N = sum(m * m for _, m, _ in specs)
+    assert N > 30_000_000
+    o = qsl.qsl_opts_default(integrator=qsl.QSL_DOPRI5_CELL, tol_abs=1e-7, tol_rel=1e-7)
+    m0 = specs[0][1]
+    pick = inputs.subsample(m0 * m0, 131072, 17)
+    ii, jj = pick % m0, pick // m0
+    sd = np.column_stack([-1 + (ii + 0.5) * 2 / m0, -1 + (jj + 0.5) * 2 / m0, np.zeros(len(pick))])
+    rep = qsl.qsl_autotune(items[0][0], torch.as_tensor(sd).cuda(), o)
+    print("autotune on the first cut (n = %d, m = %d):" % specs[0][:2], rep)
+    assert rep["tol"] in (1e-5, 1e-6, 1e-7)
+    q, L = torch.empty(N, device="cuda"), torch.empty(N, device="cuda")
+    fc = torch.empty(2 * N, dtype=torch.uint8, device="cuda")
+    plan = qsl.Plan(items, o, q=q, length=L, faces=fc)
+    for _ in range(2):
+        q.fill_(-1.0)
+        plan.launch()
+    torch.cuda.synchronize()
+    assert plan.stats()["lines"] == N
+    off = 0
+    checked = 0
+    for k, ((n, m, fseed), gf) in enumerate(zip(specs, gfs)):
+        idx = inputs.subsample(m * m, 10, 500 + k)
+        g = inputs.to_numpy64(gf)
+        Fo = oracle_mod.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
+        seeds = oracle_mod.plane_seeds((0, 0, 0), (2, 0, 0), (0, 2, 0), m, m)[idx]
+        ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
+        del Fo, g
+        gd = {"q_perp": q[off + idx].cpu().numpy(), "L": L[off + idx].cpu().numpy(),
+              "face_f": fc.view(-1, 2)[off + idx, 0].cpu().numpy(), "face_b": fc.view(-1, 2)[off + idx, 1].cpu().numpy()}
+        rep_k = compare_lines(gd, ref, 1.0 / (n - 1), (-1, -1, 0), (1, 1, 1))
+        checked += rep_k["q_checked"]
+        off += m * m
+    assert checked > 500
+    del plan

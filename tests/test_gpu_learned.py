@@ -44,3 +44,58 @@ def test_learned_proposal_end_to_end():
     # sample keys stay unique and sorted
     k = lrn.key[:n_l].cpu().numpy()
     assert np.all(np.diff(k) > 0)
+
+
+def test_config5_learned_volume_full_size_sampled(oracle_mod):
+    """The learned-proposal workload at full size: an 8-charge field on 512^3,
+    a 256 x 256 x 128 coarse cell-centre volume refined two orders (1024 x 1024
+    x 512 effective) after a CNN proposal on its z-slices, with the plain
+    criterion as fallback. The network here is a quick one (40 small training
+    maps): what is checked is the tracer on this volume, on seeded samples of
+    each kind (coarse, proposed, refinement passes) against the FP64 oracle."""
+    from gpu_helpers import compare_lines
+    from paper_1609_00724_gb300 import learned, qsl
+    o = qsl.qsl_opts_default(tol_abs=1e-6, tol_rel=1e-6, integrator=qsl.QSL_DOPRI5_CELL)
+    X, Y, _ = learned.make_training_set(40, grid=64, coarse=64, levels=2, tau=0.05, seed0=6100, opts=o)
+    net, hist, pw = learned.train(X[:32], Y[:32], epochs=20, batch=8, lr=3e-3)
+    thr, _ = learned.calibrate(net, X[32:], Y[32:], recall=0.99)
+    gf = inputs.charge_field(inputs.random_charges(8, 5), 512, dtype=torch.float32, device="cuda", slab=16)
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
+    coarse = (256, 256, 128)
+    cap = 96 * 1024 * 1024
+    smp = learned.Samples(cap)
+    org = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    spec0 = learned.volume_spec(coarse, 2, 0.05, max_iters=0)
+    n0, _, _, rc = qsl.qsl_refine(F, spec0, o, smp.key, smp.q, smp.L, smp.faces, smp.status, 0, origin=org)
+    assert rc == qsl.QSL_OK and n0 == 256 * 256 * 128
+    smp.count = n0
+    Lc, Qc, _ = learned.coarse_grids(smp, 3, spec0.max_order, 2, coarse[::-1])
+    budget = int(0.8 * (cap - n0) / 64)
+    mask = learned.propose(net, learned.features_slices(Lc, Qc), thr, budget=budget).contiguous()
+    assert 0 < int(mask.sum().item()) <= budget
+    spec = learned.volume_spec(coarse, 2, 0.05, proposal=mask)
+    n, iters, traced, rc = qsl.qsl_refine(F, spec, o, smp.key, smp.q, smp.L, smp.faces, smp.status, n0, origin=org)
+    assert rc == qsl.QSL_OK and n > n0 and iters > 0
+    keys = smp.key[:n].cpu().numpy().view(np.uint64)
+    assert np.all(np.diff(keys.astype(np.int64)) > 0)
+    og = org[:n].cpu().numpy()
+    c = np.zeros((n, 3), dtype=np.uint32)
+    qsl.qsl_hilbert_decode(keys, 3, spec.max_order, c)
+    on_coarse = np.all((c % 4) == 2, axis=1)
+    kinds = {"coarse": np.where(on_coarse)[0], "proposed": np.where(~on_coarse & (og == 0))[0],
+             "passes": np.where(og > 0)[0]}
+    idx = np.concatenate([v[inputs.subsample(len(v), min(60, len(v)), 40 + j)] for j, v in enumerate(kinds.values())])
+    assert len(kinds["proposed"]) > 0 and len(kinds["passes"]) > 0
+    ext = np.array([1024, 1024, 512])
+    lo, hi = np.array([-1.0, -1.0, 0.0]), np.array([1.0, 1.0, 1.0])
+    pos = lo[None] + (c[idx] + 0.5) / ext[None] * (hi - lo)[None]
+    g = inputs.to_numpy64(gf)
+    del gf
+    Fo = oracle_mod.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
+    del g
+    ref = oracle_mod.trace_seeds(Fo, pos, oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11))
+    fa = smp.faces[:2 * n].view(-1, 2).cpu().numpy()
+    gd = {"q_perp": smp.q[:n].cpu().numpy()[idx], "L": smp.L[:n].cpu().numpy()[idx], "face_f": fa[idx, 0],
+          "face_b": fa[idx, 1]}
+    rep = compare_lines(gd, ref, 1.0 / 511, tuple(lo), tuple(hi))
+    assert rep["q_checked"] > 100

@@ -319,9 +319,10 @@ def test_higher_order_euler_and_argument_checks(qsl, oracle_mod):
 @pytest.mark.parametrize("mode,lanes", [(0, 1), (0, 3), (1, 1), (1, 3)])
 def test_length_only_matches_oracle(qsl, oracle_mod, mode, lanes):
     """Lengths only (qsl_opts.length_only, the mode of the refinement passes)
-    on the cell-wise kernels: one lane per line and the three-lane kernel, whose
-    normalise-first stages evaluate the cell's trilinear polynomial. Lengths
-    and end faces against the oracle's lengths-only trace; Q outputs are NaN."""
+    on the cell-wise kernels, which evaluate the cell's trilinear polynomial:
+    one lane per line (for a launch this small the kernel of the refinement
+    passes) and the queue-refilled three-lane kernel. Lengths and end faces
+    against the oracle's lengths-only trace; Q outputs are NaN."""
     ch = inputs.random_charges(4, 2)
     gf = inputs.charge_field(ch, 64, dtype=torch.float32)
     F = _gpu_field(qsl, gf, mode)
