@@ -105,7 +105,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (fixed tolerance and shape)")
     ap.add_argument("--config", default="refine2d",
-                    choices=["refine2d", "volume", "batch64", "learned", "qcrit", "euler"],
+                    choices=["refine2d", "hyperbolic", "volume", "batch64", "learned", "qcrit", "euler"],
                     help="refine2d: 1024^2 map refined to 4096^2 (default); volume: 512x512x256 Q/FLL/FLEDGE volume "
                          "of an 8-charge field on 384^3")
     ap.add_argument("--shape", default=None,
@@ -387,6 +387,61 @@ def run_reference(args, rank, world):
     del torch
 
 
+def run_hyperbolic(args, qsl, torch, dev, rank, world, local):
+    """Config 1: the linear hyperbolic field B = (3x, -3y, 1) sampled in FP64 on
+    64^3 over [-1, 1]^2 x [0, 1]; one step = the 256 x 256 z = 0 Q/FLL map
+    (raw mode, exact for a linear field); the maps against the closed forms
+    of the golden fixture (Q_foot = k^2 + k^-2 for top exits and the side-exit
+    form, lengths by quadrature)."""
+    from paper_1609_00724_gb300 import inputs
+    gf = inputs.hyperbolic_field(64)
+    t = [torch.as_tensor(a).to(dev) for a in (gf.bx, gf.by, gf.bz)]
+    F = qsl.qsl_load_field(*t, gf.xc, gf.yc, gf.zc, interp_mode=qsl.QSL_RAW_B)
+    n = 256
+    N = n * n
+    q = torch.empty(N, device=dev)
+    L = torch.empty(N, device=dev)
+    fc = torch.empty(2 * N, dtype=torch.uint8, device=dev)
+    o = qsl.qsl_opts_default(tol_abs=RUN["tol"], tol_rel=RUN["tol"], q_form=qsl.QSL_Q_FOOT,
+                             integrator=INTEGRATOR[RUN["integrator"]])
+
+    def step():
+        qsl.qsl_q_map_2d(F, (0, 0, 0), (2, 0, 0), (0, 2, 0), n, n, o, q=q, length=L, faces=fc)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    l0 = qsl.qsl_kernel_launches()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(args.steps, 20)
+    with ClockSampler(local) as clk:
+        start.record()
+        for _ in range(reps):
+            step()
+        end.record()
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    st = qsl.qsl_last_stats()
+    ms_max, units = reduce_timing(torch, ms, N * reps, world, dev)
+    g = np.loadtxt(os.path.join(ROOT, "tests", "golden", "hyperbolic_closed_forms.txt"))
+    idx = g[:, 1].astype(int) * n + g[:, 0].astype(int)
+    qh, Lh, fh = q.cpu().numpy()[idx], L.cpu().numpy()[idx], fc.cpu().numpy().reshape(-1, 2)[idx]
+    line = {"metric": "Q-points/s (256^2 hyperbolic-field map, Q_foot against its closed form)",
+            "value": units / (ms_max / 1000.0), "unit": UNIT, "n_gpus": world, "steps": reps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_max / reps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "hyperbolic field (3x, -3y, 1) on 64^3 (FP64 samples), 256^2 z=0 map, raw mode",
+                       "tol": RUN["tol"], "integrator": RUN["integrator"]},
+            "clocks": clk.summary(), "gpu_launches": qsl.qsl_kernel_launches() - l0, "kernel_ms": st["kernel_ms"],
+            "closed_form": {"pixels": int(len(idx)), "faces_equal": float(np.mean(fh[:, 0] == g[:, 7].astype(int))),
+                            "q_foot_max_rel": float(np.max(np.abs(qh / g[:, 4] - 1))),
+                            "l_max_rel": float(np.max(np.abs(Lh / g[:, 6] - 1)))}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_volume(args, qsl, torch, dev, rank, world, local):
     """Config 3: 8 charges on 384^3 (FP32); one step = Q/FLL at 512x512x256
     cell-centre seeds (FP32 trace, FP64 assembly, FP64 retrace above 1e6) and
@@ -603,87 +658,114 @@ def run_qcrit(args, qsl, torch, dev, rank, world, local):
 
 
 def run_learned(args, qsl, torch, dev, rank, world, local):
-    """Config 5: the learned refinement proposal. Training: 2000 tracer-generated
-    maps (random 4-12-charge fields on 128^3, coarse 128^2 z=0 cuts refined two
-    orders by the plain criterion). Evaluation: an 8-charge field on 512^3, a
-    coarse 256 x 256 x 128 cell-centre volume refined two orders (1024 x 1024 x
-    512 effective). Compared: wall time of the plain criterion with FP64
-    everywhere against the learned proposal (CNN on the coarse z-slices) with
-    FP32 tracing and the plain criterion as fallback; recall of the plain
-    run's samples."""
+    """Config 5: the learned refinement proposal. Training: z-slices of
+    tracer-generated volumes (random 4-12-charge fields on 128^3, coarse
+    64 x 64 x 32 cell-centre volumes refined two orders by the plain
+    criterion). Evaluation: an 8-charge field on 512^3, a coarse 256 x 256 x
+    128 volume refined two orders (1024 x 1024 x 512 effective). Compared:
+    wall time of the plain criterion with FP64 everywhere (and with FP32
+    tracing) against the learned proposal (CNN on the coarse z-slices, mask
+    dilated by one cell, every effective cell of a proposed coarse cell traced
+    in one launch) with FP32 tracing and the plain criterion as fallback, run
+    for a few iterations and to convergence; recall of the plain FP64 run's
+    QSL pixels."""
     from paper_1609_00724_gb300 import inputs, learned
-    n_train = int(os.environ.get("QSL_LEARNED_MAPS", "2000"))
+    n_vol = int(os.environ.get("QSL_LEARNED_VOLUMES", "160"))
+    fb_iters = int(os.environ.get("QSL_LEARNED_FALLBACK_ITERS", "2"))
     o32 = opts(qsl)
     o64 = qsl.qsl_opts_default(tol_abs=RUN["tol"], tol_rel=RUN["tol"], integrator=INTEGRATOR[RUN["integrator"]],
                                precision=qsl.QSL_FP64)
     ot = qsl.qsl_opts_default(tol_abs=1e-6, tol_rel=1e-6, integrator=INTEGRATOR[RUN["integrator"]])
-    X, Y, t_data = learned.make_training_set(n_train, grid=128, coarse=128, levels=2, tau=TAU, seed0=5000, opts=ot,
-                                             device=dev)
-    n_fit = int(0.9 * n_train)
+    tr_coarse = (64, 64, 32)
+    X, Y, W, t_data = learned.make_training_volumes(n_vol, grid=128, coarse=tr_coarse, levels=2, tau=TAU,
+                                                    seed0=5000, opts=ot, device=dev)
+    nz_tr = tr_coarse[2]
+    n_fit = int(0.9 * n_vol) * nz_tr
     t0 = time.perf_counter()
     net, hist, pw = learned.train(X[:n_fit], Y[:n_fit], epochs=12, batch=32, lr=2e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    thr, frac = learned.calibrate(net, X[n_fit:], Y[n_fit:], recall=0.995)
-    del X, Y
+    thr, frac, rec_cal = learned.calibrate_qsl(net, X[n_fit:], W[n_fit:], nz_tr, recall=0.995, dilate=True)
+    del X, Y, W
     gf = inputs.charge_field(inputs.random_charges(8, 5), 512, dtype=torch.float32, device=dev, slab=16)
     F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
     del gf
     coarse = tuple(int(v) for v in os.environ.get("QSL_LEARNED_COARSE", "256,256,128").split(","))  # x, y, z
-    cap = int(os.environ.get("QSL_LEARNED_CAPACITY", str(96 * 1024 * 1024)))
+    cap = int(os.environ.get("QSL_LEARNED_CAPACITY", str(128 * 1024 * 1024)))
     spec = learned.volume_spec(coarse, 2, TAU)
-    res = {}
-    # plain criterion, FP64 everywhere
-    smp = learned.Samples(cap, dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    n_p, it_p, tr_p, rc_p = smp.refine(F, spec, o64)
-    torch.cuda.synchronize()
-    res["plain_fp64"] = {"seconds": time.perf_counter() - t0, "samples": n_p, "iters": it_p, "rc": rc_p}
-    plain_keys = smp.key[:n_p].clone()
     ext = [c * 4 for c in coarse]
     out_order = spec.max_order - 1
+    res = {}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, r
+
+    # plain criterion, FP64 everywhere (the reference of recall)
+    smp = learned.Samples(cap, dev)
+    dt, (n_p, it_p, tr_p, rc_p) = timed(lambda: smp.refine(F, spec, o64))
+    res["plain_fp64"] = {"seconds": dt, "samples": n_p, "iters": it_p, "rc": rc_p}
+    plain_keys = smp.key[:n_p].clone()
     qp = learned.converted_q(smp, 3, spec.max_order, ext, out_order)
-    del smp
+    # QSL pixels: output cells holding a plain FP64 sample with Q >= 100
+    hot = torch.nan_to_num(smp.q[:n_p], nan=0.0) >= 100.0
+    cc = smp.coords(3, spec.max_order)[hot] >> 1
+    eo = [e >> 1 for e in ext]
+    qsl_cells = torch.unique(cc[:, 0] + eo[0] * (cc[:, 1] + eo[1] * cc[:, 2]))
+    del smp, cc, hot
     # plain criterion with FP32 tracing (what the network is compared with)
     smp = learned.Samples(cap, dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    n_3, it_3, _, rc_3 = smp.refine(F, spec, o32)
-    torch.cuda.synchronize()
-    res["plain_fp32"] = {"seconds": time.perf_counter() - t0, "samples": n_3, "iters": it_3, "rc": rc_3}
+    dt, (n_3, it_3, _, rc_3) = timed(lambda: smp.refine(F, spec, o32))
+    res["plain_fp32"] = {"seconds": dt, "samples": n_3, "iters": it_3, "rc": rc_3}
     del smp
-    # learned proposal + FP32, plain criterion as fallback
-    smp = learned.Samples(cap, dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    smp.refine(F, learned.volume_spec(coarse, 2, TAU, max_iters=0), o32)
-    L, Q, _ = learned.coarse_grids(smp, 3, spec.max_order, 2, coarse[::-1])
-    budget = max(0, int(0.8 * (cap - smp.count) / 64))
-    mask = learned.propose(net, learned.features_slices(L, Q), thr, budget=budget).contiguous()
-    n_l, it_l, tr_l, rc_l = smp.refine(F, learned.volume_spec(coarse, 2, TAU, proposal=mask), o32)
-    torch.cuda.synchronize()
-    res["learned_fp32"] = {"seconds": time.perf_counter() - t0, "samples": n_l, "iters": it_l, "rc": rc_l,
-                           "proposed_cells": int(mask.sum().item())}
-    lk = smp.key[:n_l]
-    pos = torch.searchsorted(lk, plain_keys)
-    pos = pos.clamp(max=n_l - 1)
-    hit = (lk[pos] == plain_keys)
-    recall = float(hit.float().mean().item())
-    ql = learned.converted_q(smp, 3, spec.max_order, ext, out_order)
-    qsl_pix = torch.nan_to_num(qp, nan=0.0) >= 100.0
-    qsl_recall = float(((torch.nan_to_num(ql, nan=0.0) >= 100.0) & qsl_pix).sum().item() /
-                       max(1, int(qsl_pix.sum().item())))
-    line = {"metric": "refined-map wall time: learned proposal + FP32 vs plain FP64 (recall of plain samples)",
-            "value": res["plain_fp64"]["seconds"] / res["learned_fp32"]["seconds"], "unit": "x speed-up",
+
+    def learned_run(max_iters):
+        s2 = learned.Samples(cap, dev)
+
+        def go():
+            s2.refine(F, learned.volume_spec(coarse, 2, TAU, max_iters=0), o32)
+            L, Q, _ = learned.coarse_grids(s2, 3, spec.max_order, 2, coarse[::-1])
+            budget = max(0, int(0.9 * (cap - s2.count) / 64))
+            mask = learned.propose(net, learned.features_slices(L, Q), thr, dilate=True)
+            if int(mask.sum().item()) > budget:
+                mask = learned.propose(net, learned.features_slices(L, Q), thr, budget=budget // 27, dilate=True)
+            r = s2.refine(F, learned.volume_spec(coarse, 2, TAU, proposal=mask, max_iters=max_iters), o32)
+            return r, int(mask.sum().item())
+
+        dt, ((n_l, it_l, tr_l, rc_l), ncells) = timed(go)
+        lk = s2.key[:n_l]
+        pos = torch.searchsorted(lk, plain_keys).clamp(max=n_l - 1)
+        sample_recall = float((lk[pos] == plain_keys).float().mean().item())
+        ql = learned.converted_q(s2, 3, spec.max_order, ext, out_order)
+        qsl_pix = torch.nan_to_num(ql.reshape(-1)[qsl_cells], nan=0.0) >= 100.0
+        old_pix = torch.nan_to_num(qp, nan=0.0) >= 100.0
+        old_recall = float(((torch.nan_to_num(ql, nan=0.0) >= 100.0) & old_pix).sum().item() /
+                           max(1, int(old_pix.sum().item())))
+        return {"seconds": dt, "samples": n_l, "iters": it_l, "rc": rc_l, "proposed_cells": ncells,
+                "proposed_frac": ncells / float(np.prod(coarse)), "fallback_max_iters": max_iters,
+                "qsl_pixel_recall": float(qsl_pix.float().mean().item()), "sample_recall": sample_recall,
+                "converted_qsl_recall": old_recall}
+
+    res["learned_fp32_bounded"] = learned_run(fb_iters)
+    res["learned_fp32_full"] = learned_run(64)
+    meets = [k for k in ("learned_fp32_bounded", "learned_fp32_full") if res[k]["qsl_pixel_recall"] >= 0.99]
+    best = min(meets, key=lambda k: res[k]["seconds"]) if meets else "learned_fp32_full"
+    line = {"metric": "refined-map wall time: learned proposal + FP32 vs plain FP64 at >= 99% QSL-pixel recall",
+            "value": res["plain_fp64"]["seconds"] / res[best]["seconds"], "unit": "x speed-up",
             "n_gpus": world, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "8-charge field 512^3, coarse 256x256x128 -> 1024x1024x512 effective",
-                       "training": {"maps": n_train, "data_s": t_data, "train_s": t_train, "final_loss": hist[-1],
-                                    "pos_weight": pw, "threshold": thr, "proposed_frac_heldout": frac},
-                       "tau": TAU, "tol": RUN["tol"]},
-            "results": res, "sample_recall": recall, "qsl_pixel_recall": qsl_recall,
-            "qsl_pixels": int(qsl_pix.sum().item()), "recall_grid": [e >> 1 for e in ext]}
+                       "training": {"volumes": n_vol, "slices": n_vol * nz_tr, "data_s": t_data, "train_s": t_train,
+                                    "final_loss": hist[-1], "pos_weight": pw, "threshold": thr,
+                                    "proposed_frac_heldout": frac, "qsl_recall_heldout": rec_cal},
+                       "tau": TAU, "tol": RUN["tol"], "qsl_pixel": "output cell (512x512x256) holding a plain FP64 "
+                                                                   "sample with Q >= 100"},
+            "headline": best, "recall_target_met": bool(meets),
+            "vs_plain_fp32": res["plain_fp32"]["seconds"] / res[best]["seconds"],
+            "qsl_pixels": int(qsl_cells.numel()), "results": res}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -713,9 +795,9 @@ def main():
         RUN["shape"] = tuple(int(v) for v in args.shape.split(","))
     if args.hmax:
         RUN["h_max"] = args.hmax
-    if args.config in ("volume", "batch64", "learned", "qcrit", "euler"):
-        {"volume": run_volume, "batch64": run_batch, "learned": run_learned, "qcrit": run_qcrit,
-         "euler": run_euler}[args.config](
+    if args.config in ("hyperbolic", "volume", "batch64", "learned", "qcrit", "euler"):
+        {"hyperbolic": run_hyperbolic, "volume": run_volume, "batch64": run_batch, "learned": run_learned,
+         "qcrit": run_qcrit, "euler": run_euler}[args.config](
             args, qsl, torch, dev, rank, world, local)
         if world > 1:
             torch.distributed.destroy_process_group()

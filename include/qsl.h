@@ -343,6 +343,16 @@ int qsl_cnn_loss_grad(qsl_cnn* cnn, const float* x, const float* y, int n, int h
 int qsl_cnn_adam_step(qsl_cnn* cnn, const float* grad, float lr, float beta1, float beta2, float eps, void* stream);
 void qsl_cnn_free(qsl_cnn* cnn);
 int qsl_cnn_nparams(void);
+/* Network input (device, NCHW X[nz][2][ny][nx]) of the nz z-slices of a
+ * coarse map or volume from its FLEDGE map S (qsl_fledge of the coarse
+ * lengths) and Q (both [nz][ny][nx], device): channel 0 S over the largest
+ * finite S of its slice (non-finite entries 0), channel 1 (log10 Q - 2) / 2
+ * clamped to [-2, 3] (NaN Q counts as Q = 2). */
+int qsl_cnn_features(const float* S, const float* Q, int nz, int ny, int nx, float* X, void* stream);
+/* Proposal mask dilation (device bytes [nz][ny][nx]): out = 1 where any cell
+ * of the 3 x 3 x 3 neighbourhood of `in`, clipped to the volume, is nonzero.
+ * in and out must not alias. */
+int qsl_mask_dilate(const uint8_t* in, int nz, int ny, int nx, uint8_t* out, void* stream);
 
 /* ---- autotuner -----------------------------------------------------------------
  * Picks, on a sample of S seeds (device memory, S >= 1) of the caller's

@@ -233,9 +233,95 @@ int forward(qsl_cnn* c, const float* x, int n, int H, int W, cudaStream_t s, flo
 
 bool dims_ok(int n, int H, int W) { return n >= 1 && H >= 1 && W >= 1 && (int64_t)n * H * W <= (1ll << 31); }
 
+// Network input of each z-slice of a coarse volume (one block per slice):
+// channel 0 the FLEDGE map over its largest finite value in the slice
+// (non-finite entries 0), channel 1 (log10 Q - 2) / 2 clamped to [-2, 3], a
+// missing Q (NaN) counted as the floor Q = 2 and an infinite one as the top
+// of the range.
+__global__ void __launch_bounds__(256) features_kernel(const float* __restrict__ S, const float* __restrict__ Q,
+                                                       int64_t plane, float* __restrict__ X) {
+  __shared__ float red[256];
+  const int z = blockIdx.x;
+  const float* s = S + (size_t)z * plane;
+  const float* q = Q + (size_t)z * plane;
+  float m = 0.0f;
+  for (int64_t i = threadIdx.x; i < plane; i += blockDim.x) {
+    const float v = s[i];
+    if (isfinite(v) && v > m) m = v;
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const float smax = fmaxf(red[0], 1e-12f);
+  float* x0 = X + (size_t)z * 2 * plane;
+  float* x1 = x0 + plane;
+  for (int64_t i = threadIdx.x; i < plane; i += blockDim.x) {
+    const float v = s[i] / smax;
+    x0[i] = isfinite(v) ? v : 0.0f;
+    float qv = q[i];
+    if (isnan(qv) || (isinf(qv) && qv < 0)) qv = 2.0f;  // no Q: the floor Q = 2
+    x1[i] = isinf(qv) ? 3.0f : fminf(fmaxf((log10f(fmaxf(qv, 2.0f)) - 2.0f) * 0.5f, -2.0f), 3.0f);
+  }
+}
+
+// out = 1 where any cell of the 3 x 3 x 3 neighbourhood (clipped to the
+// volume; 3 x 3 for one slice) of `in` is nonzero.
+__global__ void dilate_kernel(const uint8_t* __restrict__ in, int nz, int ny, int nx, uint8_t* __restrict__ out) {
+  const int64_t n = (int64_t)nz * ny * nx;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+    uint8_t v = 0;
+    for (int dz = -1; dz <= 1 && !v; ++dz) {
+      const int zz = z + dz;
+      if (zz < 0 || zz >= nz) continue;
+      for (int dy = -1; dy <= 1 && !v; ++dy) {
+        const int yy = y + dy;
+        if (yy < 0 || yy >= ny) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int xx = x + dx;
+          if (xx < 0 || xx >= nx) continue;
+          if (in[((int64_t)zz * ny + yy) * nx + xx]) {
+            v = 1;
+            break;
+          }
+        }
+      }
+    }
+    out[i] = v;
+  }
+}
+
 }  // namespace
 
 extern "C" {
+
+int qsl_cnn_features(const float* S, const float* Q, int nz, int ny, int nx, float* X, void* stream_) {
+  if (!S || !Q || !X || nz < 1 || ny < 1 || nx < 1) {
+    qsl::set_error("qsl_cnn_features: bad arguments");
+    return QSL_EINVAL;
+  }
+  features_kernel<<<nz, 256, 0, (cudaStream_t)stream_>>>(S, Q, (int64_t)ny * nx, X);
+  qsl::count_launch();
+  QSL_CHECK_CUDA(cudaGetLastError());
+  return QSL_OK;
+}
+
+int qsl_mask_dilate(const uint8_t* in, int nz, int ny, int nx, uint8_t* out, void* stream_) {
+  if (!in || !out || in == out || nz < 1 || ny < 1 || nx < 1) {
+    qsl::set_error("qsl_mask_dilate: bad arguments (in and out must differ)");
+    return QSL_EINVAL;
+  }
+  const int64_t n = (int64_t)nz * ny * nx;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  dilate_kernel<<<blocks, 256, 0, (cudaStream_t)stream_>>>(in, nz, ny, nx, out);
+  qsl::count_launch();
+  QSL_CHECK_CUDA(cudaGetLastError());
+  return QSL_OK;
+}
 
 int qsl_cnn_create(const float* params, qsl_cnn** out) {
   if (!params || !out) {

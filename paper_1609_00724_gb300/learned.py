@@ -3,15 +3,18 @@ which coarse cells the FLL-jump refinement (Sec. "Adaptive refinements") will
 sample, so that those cells are traced in one launch before the plain
 criterion runs as the fallback.
 
-Pipeline (every computation runs in libqsl.so kernels; torch only holds device
+Pipeline (every computation runs in libqsl.so kernels; torch holds device
 memory and does index bookkeeping):
-* training data: random 4-12-charge fields; the coarse z = 0 cut of each is
-  refined by the plain criterion; the CNN input is the coarse pair
-  (FLEDGE / max FLEDGE, (log10 Q - 2) / 2), the label marks the coarse cells
-  that received refined samples;
+* training data: coarse cell-centre volumes of random 4-12-charge fields,
+  refined by the plain criterion; each z-slice is one example, with input
+  (FLEDGE / max FLEDGE of the slice, (log10 Q - 2) / 2) of the coarse volume,
+  label = coarse cells that received refined samples, and weight = the number
+  of samples with Q >= 100 (QSL samples) of the plain run in each cell;
 * training: mean BCE with a positive-class weight, Adam, BF16 weights;
-* inference: coarse map -> CNN -> probability per coarse cell -> threshold
-  (calibrated for label recall on held-out maps) -> proposal mask.
+* inference: coarse volume -> per-slice CNN -> probability per coarse cell ->
+  threshold -> 3 x 3 x 3 dilation -> proposal mask; the threshold is the
+  largest whose dilated mask holds the required fraction of the held-out
+  QSL samples.
 """
 import math
 import time
@@ -105,11 +108,9 @@ def features(L2d, Q2d):
     """CNN input [2, H, W] from coarse L and Q maps (device tensors)."""
     S = torch.empty_like(L2d)
     qsl.qsl_fledge(L2d.contiguous(), S)
-    smax = torch.nan_to_num(S, nan=0.0).max().clamp_min(1e-12)
-    f0 = torch.nan_to_num(S / smax, nan=0.0)
-    lq = torch.log10(torch.nan_to_num(Q2d, nan=2.0).clamp_min(2.0))
-    f1 = ((lq - 2.0) / 2.0).clamp(-2.0, 3.0)
-    return torch.stack([f0, f1])
+    X = torch.empty((1, 2) + tuple(L2d.shape), device=L2d.device)
+    qsl.qsl_cnn_features(S, Q2d.contiguous(), X)
+    return X[0]
 
 
 def features_slices(L3, Q3):
@@ -117,11 +118,62 @@ def features_slices(L3, Q3):
     sliced, log10 Q)."""
     S = torch.empty_like(L3)
     qsl.qsl_fledge(L3.contiguous(), S)
-    smax = torch.nan_to_num(S, nan=0.0).amax(dim=(1, 2), keepdim=True).clamp_min(1e-12)
-    f0 = torch.nan_to_num(S / smax, nan=0.0)
-    lq = torch.log10(torch.nan_to_num(Q3, nan=2.0).clamp_min(2.0))
-    f1 = ((lq - 2.0) / 2.0).clamp(-2.0, 3.0)
-    return torch.stack([f0, f1], dim=1).contiguous()
+    X = torch.empty((L3.shape[0], 2) + tuple(L3.shape[1:]), device=L3.device)
+    qsl.qsl_cnn_features(S, Q3.contiguous(), X)
+    return X
+
+
+def qsl_counts(smp, ndim, max_order, levels, coarse_shape, q_qsl=100.0):
+    """Number of samples with Q >= q_qsl (QSL samples) in each coarse cell."""
+    R = 1 << levels
+    c = smp.coords(ndim, max_order)
+    cc = c // R
+    flat = cc[:, 0]
+    mult = 1
+    shape_xyz = list(coarse_shape)[::-1]
+    for a in range(1, ndim):
+        mult *= shape_xyz[a - 1]
+        flat = flat + cc[:, a] * mult
+    hot = torch.nan_to_num(smp.q[:smp.count], nan=0.0) >= q_qsl
+    W = torch.zeros(int(np.prod(coarse_shape)), dtype=torch.float32, device=c.device)
+    W.index_add_(0, flat[hot], torch.ones(int(hot.sum().item()), device=c.device))
+    return W.view(coarse_shape)
+
+
+def make_training_volumes(n_vol, grid=128, coarse=(64, 64, 32), levels=2, tau=0.05, seed0=5000, opts=None,
+                          device="cuda", charges=(4, 12), log_every=0):
+    """Tracer-generated training slices: volume i is the coarse cell-centre
+    lattice `coarse` (x, y, z) of a field with k ~ U{charges} charges (seed
+    seed0 + i) on grid^3, refined `levels` orders by the plain criterion.
+    Returns X [n_vol * nz, 2, ny, nx], Y [.., ny, nx] (refined cells), W [..]
+    (QSL samples per cell), all device tensors, and the time spent."""
+    if opts is None:
+        opts = qsl.qsl_opts_default(tol_abs=1e-6, tol_rel=1e-6, integrator=qsl.QSL_DOPRI5_CELL)
+    nx, ny, nz = coarse
+    X = torch.empty((n_vol * nz, 2, ny, nx), device=device)
+    Y = torch.empty((n_vol * nz, ny, nx), device=device)
+    W = torch.empty((n_vol * nz, ny, nx), device=device)
+    R = 1 << levels
+    smp = Samples(nx * ny * nz * R ** 3, device)
+    spec = volume_spec(coarse, levels, tau)
+    t0 = time.perf_counter()
+    for i in range(n_vol):
+        rng = np.random.Generator(np.random.PCG64(seed0 + i))
+        k = int(rng.integers(charges[0], charges[1] + 1))
+        gf = inputs.charge_field(inputs.random_charges(k, seed0 + i), grid, dtype=torch.float32, device=device)
+        F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
+        del gf
+        smp.count = 0
+        smp.refine(F, spec, opts)
+        L, Q, refined = coarse_grids(smp, 3, spec.max_order, levels, (nz, ny, nx))
+        X[i * nz:(i + 1) * nz] = features_slices(L, Q)
+        Y[i * nz:(i + 1) * nz] = refined
+        W[i * nz:(i + 1) * nz] = qsl_counts(smp, 3, spec.max_order, levels, (nz, ny, nx))
+        del F
+        if log_every and (i + 1) % log_every == 0:
+            print("training volumes: %d / %d" % (i + 1, n_vol), flush=True)
+    torch.cuda.synchronize()
+    return X, Y, W, time.perf_counter() - t0
 
 
 def make_training_set(n_maps, grid=128, coarse=128, levels=2, tau=0.05, seed0=5000, opts=None, device="cuda",
@@ -205,9 +257,11 @@ def calibrate(net, X, Y, recall=0.995):
     return thr, frac
 
 
-def propose(net, X, thr, budget=None):
-    """uint8 mask (same layout as X's spatial dims) of cells with p >= thr;
-    with a budget, only the `budget` most probable of them."""
+def propose(net, X, thr, budget=None, dilate=False):
+    """uint8 mask (same layout as X's spatial dims: one volume [nz, ny, nx]
+    or one map [ny, nx]) of cells with p >= thr, dilated by one cell in every
+    direction if asked; with a budget, only the `budget` most probable of them
+    (before dilation)."""
     P = predict(net, X)
     mask = P >= thr
     if budget is not None and int(mask.sum().item()) > budget:
@@ -216,7 +270,45 @@ def propose(net, X, thr, budget=None):
         mask = torch.zeros_like(flat, dtype=torch.bool)
         mask[top] = True
         mask = mask.view(P.shape)
-    return mask.to(torch.uint8).contiguous()
+    mask = mask.to(torch.uint8).contiguous()
+    if dilate:
+        out = torch.empty_like(mask)
+        qsl.qsl_mask_dilate(mask, out)
+        mask = out
+    return mask
+
+
+def calibrate_qsl(net, X, W, nz, recall=0.995, dilate=True, steps=30):
+    """Largest probability threshold whose mask (dilated per volume of nz
+    slices, if asked) holds `recall` of the QSL samples W of held-out
+    volumes; also returns the fraction of cells it proposes and the recall."""
+    P = predict(net, X)
+    nv = X.shape[0] // nz
+    Pv = P.view(nv, nz, *P.shape[1:])
+    Wv = W.view(nv, nz, *W.shape[1:])
+    total = float(Wv.sum().item())
+    if total == 0:
+        return 0.5, 0.0, 1.0
+
+    def at(thr):
+        m = (Pv >= thr).to(torch.uint8).contiguous()
+        if dilate:
+            d = torch.empty_like(m)
+            for v in range(nv):
+                qsl.qsl_mask_dilate(m[v], d[v])
+            m = d
+        return float((Wv * m.float()).sum().item()) / total, float(m.float().mean().item())
+
+    lo, hi = 0.0, 1.0  # recall(lo) = 1
+    for _ in range(steps):
+        mid = 0.5 * (lo + hi)
+        r, _ = at(mid)
+        if r >= recall:
+            lo = mid
+        else:
+            hi = mid
+    r, frac = at(lo)
+    return max(lo, 1e-6), frac, r
 
 
 def converted_q(smp, ndim, max_order, extent, out_order):

@@ -137,6 +137,8 @@ def lib():
     L.qsl_cnn_loss_grad.argtypes = [vp, vp, vp, i32, i32, i32, C.c_float, vp, vp, vp]
     L.qsl_cnn_adam_step.argtypes = [vp, vp, C.c_float, C.c_float, C.c_float, C.c_float, vp]
     L.qsl_cnn_free.argtypes = [vp]
+    L.qsl_cnn_features.argtypes = [vp, vp, i32, i32, i32, vp, vp]
+    L.qsl_mask_dilate.argtypes = [vp, i32, i32, i32, vp, vp]
     L.qsl_autotune.argtypes = [vp, vp, i64, C.POINTER(qsl_opts), C.POINTER(qsl_tune_report), vp]
     L.qsl_trace_seeds_noalloc.argtypes = [vp, vp, i64, C.POINTER(qsl_opts), vp, vp]
     _lib = L
@@ -294,6 +296,20 @@ def qsl_autotune(field, seeds, opts, stream=None):
 
 
 QSL_CNN_NPARAMS = 32 * 2 * 9 + 32 + 32 * 32 * 9 + 32 + 32 * 9 + 1
+
+
+def qsl_cnn_features(S, Q, X, stream=None):
+    """CNN input X [nz, 2, ny, nx] from FLEDGE S and Q ([nz, ny, nx] or [ny, nx]), device tensors."""
+    nz, ny, nx = (1,) + tuple(S.shape) if S.dim() == 2 else tuple(S.shape)
+    _check(lib().qsl_cnn_features(_ptr(S), _ptr(Q), nz, ny, nx, _ptr(X), _stream(stream)))
+    return X
+
+
+def qsl_mask_dilate(mask, out, stream=None):
+    """3 x 3 x 3 dilation of a uint8 device mask ([nz, ny, nx] or [ny, nx])."""
+    nz, ny, nx = (1,) + tuple(mask.shape) if mask.dim() == 2 else tuple(mask.shape)
+    _check(lib().qsl_mask_dilate(_ptr(mask), nz, ny, nx, _ptr(out), _stream(stream)))
+    return out
 
 
 class Cnn:
