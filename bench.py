@@ -46,8 +46,9 @@ FIELD_SEED = 2
 # DRAM bytes per launch of the two tracer phases of the default workload
 # (4-charge field on 256^3, 1024^2 map refined to 4096^2):
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the
-# current kernels (summaries under profiles/); None until captured.
-TRAFFIC_COARSE_BYTES = None
+# current kernels (summaries under profiles/); None until captured. Coarse:
+# one full-size launch, 435.2 MB read + 105.9 MB written.
+TRAFFIC_COARSE_BYTES = 541.0e6
 TRAFFIC_PASS_BYTES = None
 FLOP_PER_STAGE = {"ck": 246.0, "cell": 227.0}
 # length-only stage evaluation of the cell-wise kernels (trilinear values of 3
@@ -115,6 +116,13 @@ def parse():
                     help="one qsl_refine of the bench workload and its time accounting (for ncu captures)")
     ap.add_argument("--profile-map", action="store_true",
                     help="only run the coarse Q map (the tracer kernel) --steps times, for ncu captures")
+    ap.add_argument("--profile-pass", type=int, default=0,
+                    help="one refinement of the bench workload, then the samples that pass N added traced again "
+                         "in lengths-only mode as one launch --steps times (the refinement-pass kernel), for ncu "
+                         "captures")
+    ap.add_argument("--pass-seeds", default=None,
+                    help="with --profile-pass: file of that pass's seed positions; written by a run that finds it "
+                         "missing, read (no refinement in the process) by one that finds it")
     return ap.parse_args()
 
 
@@ -267,6 +275,28 @@ def oracle_sample_rate(gf_cpu, seeds, tol, budget_s=15.0, seed=99):
         rng_seed += 1
         m = min(4 * m, max(64, int(m * budget_s / max(t_used, 1e-3))))
     return done / t_used, done, cores, t_used
+
+
+def oracle_rate_on(gf, seeds, tol, mode=0, budget_s=10.0, seed=99):
+    """cpu_baseline of a bench mode: the FP64 oracle on seeded subsamples of
+    `seeds` of the field gf (GridField, any device) at tolerance `tol`."""
+    from paper_1609_00724_gb300 import inputs
+    import oracle
+    g = inputs.to_numpy64(gf)
+    F = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=mode)
+    cores = os.cpu_count() or 1
+    o = oracle.default_opts(tol_abs=tol, tol_rel=tol, nthreads=cores)
+    done, t_used, m, k = 0, 0.0, 64 * cores, seed
+    while t_used < budget_s and done < len(seeds):
+        idx = inputs.subsample(len(seeds), min(m, len(seeds)), k)
+        t0 = time.perf_counter()
+        oracle.trace_seeds(F, seeds[idx], o)
+        t_used += time.perf_counter() - t0
+        done += len(idx)
+        k += 1
+        m = min(4 * m, max(64, int(m * budget_s / max(t_used, 1e-3))))
+    return {"value": done / t_used, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d seeded seeds of the workload, tol %g, %.1f s" % (done, tol, t_used)}
 
 
 def sample_positions(qsl, keys, coarse):
@@ -438,6 +468,10 @@ def run_hyperbolic(args, qsl, torch, dev, rank, world, local):
             "closed_form": {"pixels": int(len(idx)), "faces_equal": float(np.mean(fh[:, 0] == g[:, 7].astype(int))),
                             "q_foot_max_rel": float(np.max(np.abs(qh / g[:, 4] - 1))),
                             "l_max_rel": float(np.max(np.abs(Lh / g[:, 6] - 1)))}}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        line["cpu_baseline"] = oracle_rate_on(gf, oracle.plane_seeds((0, 0, 0), (2, 0, 0), (0, 2, 0), n, n), RUN["tol"],
+                                              mode=1)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -494,6 +528,12 @@ def run_volume(args, qsl, torch, dev, rank, world, local):
                          "kernel_ms": st["kernel_ms"], "stage_evals": st["stage_evals"],
                          "flop_per_stage": fps,
                          "peak_note": "of measured: %s" % PEAK["note"]}}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        sub = inputs.subsample(N, 2_000_000, 5)
+        ijk = np.column_stack([sub % nx, (sub // nx) % ny, sub // (nx * ny)]).astype(np.float64)
+        sd = np.array(lo)[None] + (ijk + 0.5) / np.array([nx, ny, nz])[None] * (np.array(hi) - np.array(lo))[None]
+        line["cpu_baseline"] = oracle_rate_on(gf, sd, RUN["tol"])
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -512,6 +552,8 @@ def run_batch(args, qsl, torch, dev, rank, world, local):
         gf = inputs.charge_field(inputs.random_charges(4, replica_seed(fseed, rank)), n, dtype=torch.float32,
                                  device=dev, slab=64)
         F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc)
+        if i == 0:
+            gf0 = gf
         del gf
         fields.append(F)
         items.append((F, (0, 0, 0), (2, 0, 0), (0, 2, 0), m, m))
@@ -551,6 +593,12 @@ def run_batch(args, qsl, torch, dev, rank, world, local):
                        "l2": "inputs larger than L2 (%d packed fields)" % len(items)},
             "clocks": clk.summary(), "gpu_launches": qsl.qsl_kernel_launches() - l0,
             "stats_last_replay": st}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        m0 = items[0][4]
+        line["cpu_baseline"] = oracle_rate_on(gf0, oracle.plane_seeds((0, 0, 0), (2, 0, 0), (0, 2, 0), m0, m0),
+                                              o.tol_rel)
+        line["cpu_baseline"]["sample"] += " (the first field's cut)"
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -722,6 +770,8 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
     res["plain_fp32"] = {"seconds": dt, "samples": n_3, "iters": it_3, "rc": rc_3}
     del smp
 
+    ql_keep = {}
+
     def learned_run(max_iters):
         s2 = learned.Samples(cap, dev)
 
@@ -740,6 +790,7 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
         pos = torch.searchsorted(lk, plain_keys).clamp(max=n_l - 1)
         sample_recall = float((lk[pos] == plain_keys).float().mean().item())
         ql = learned.converted_q(s2, 3, spec.max_order, ext, out_order)
+        ql_keep["b" if max_iters == fb_iters else "f"] = ql
         qsl_pix = torch.nan_to_num(ql.reshape(-1)[qsl_cells], nan=0.0) >= 100.0
         old_pix = torch.nan_to_num(qp, nan=0.0) >= 100.0
         old_recall = float(((torch.nan_to_num(ql, nan=0.0) >= 100.0) & old_pix).sum().item() /
@@ -751,6 +802,22 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
 
     res["learned_fp32_bounded"] = learned_run(fb_iters)
     res["learned_fp32_full"] = learned_run(64)
+    dense = None
+    if os.environ.get("QSL_LEARNED_DENSE") == "1":
+        # a dense map of every effective cell (FP32), max-pooled to the output
+        # lattice: which map shows the QSL cells of the dense truth
+        torch.cuda.empty_cache()
+        nx, ny, nz = ext
+        qd = torch.empty(nx * ny * nz, device=dev)
+        dt_d, _ = timed(lambda: qsl.qsl_q_volume_3d(F, (-1, -1, 0), (1, 1, 1), nx, ny, nz, o32, q=qd))
+        qd = torch.nan_to_num(qd, nan=0.0).view(1, 1, nz, ny, nx)
+        truth = torch.nn.functional.max_pool3d(qd, 2).reshape(-1) >= 100.0
+        del qd
+        dense = {"seconds": dt_d, "qsl_cells": int(truth.sum().item())}
+        for k, qmap in (("plain_fp64", qp), ("learned_fp32_bounded", ql_keep["b"]), ("learned_fp32_full", ql_keep["f"])):
+            got = torch.nan_to_num(qmap, nan=0.0).reshape(-1) >= 100.0
+            tp = int((got & truth).sum().item())
+            dense[k] = {"recall": tp / max(1, dense["qsl_cells"]), "precision": tp / max(1, int(got.sum().item()))}
     meets = [k for k in ("learned_fp32_bounded", "learned_fp32_full") if res[k]["qsl_pixel_recall"] >= 0.99]
     best = min(meets, key=lambda k: res[k]["seconds"]) if meets else "learned_fp32_full"
     line = {"metric": "refined-map wall time: learned proposal + FP32 vs plain FP64 at >= 99% QSL-pixel recall",
@@ -765,7 +832,7 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
                                                                    "sample with Q >= 100"},
             "headline": best, "recall_target_met": bool(meets),
             "vs_plain_fp32": res["plain_fp32"]["seconds"] / res[best]["seconds"],
-            "qsl_pixels": int(qsl_cells.numel()), "results": res}
+            "qsl_pixels": int(qsl_cells.numel()), "results": res, "dense_truth": dense}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -811,6 +878,32 @@ def main():
         rs = qsl.qsl_last_refine_stats()
         print(json.dumps({"profile_refine": True, "grid": args.grid, "coarse": args.coarse, "tol": RUN["tol"],
                           "shape": RUN.get("shape"), "h_max": RUN.get("h_max"), "q_points": tr, **info, **rs}))
+        return
+    if args.profile_pass:
+        F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
+        it = None
+        if args.pass_seeds and os.path.exists(args.pass_seeds):
+            pos = np.load(args.pass_seeds)
+        else:
+            bufs = alloc(torch, args.coarse, dev)
+            org = torch.full((bufs["key"].shape[0],), -1, dtype=torch.int32, device=dev)
+            n, it, _, _ = qsl.qsl_refine(F, spec(qsl, args.coarse), opts(qsl), bufs["key"], bufs["q"], bufs["L"],
+                                         bufs["faces"], bufs["st"], origin=org)
+            sel = org[:n] == args.profile_pass
+            pos = sample_positions(qsl, bufs["key"][:n][sel].cpu().numpy().view(np.uint64), args.coarse)
+            del bufs, org
+            torch.cuda.synchronize()
+            qsl.qsl_trim_pool()
+            if args.pass_seeds:
+                np.save(args.pass_seeds, pos)
+        sd = torch.as_tensor(pos).to(dev)
+        ol = opts(qsl)
+        ol.length_only = 1
+        for _ in range(args.steps):
+            qsl.qsl_trace_seeds(F, sd, ol)
+        st = qsl.qsl_last_stats()
+        print(json.dumps({"profile_pass": args.profile_pass, "seeds": int(sd.shape[0]), "kernel_ms": st["kernel_ms"],
+                          "stage_evals": st["stage_evals"], "landings": st["landing"], "iters": it}))
         return
     if args.profile_map:
         F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
