@@ -47,9 +47,10 @@ FIELD_SEED = 2
 # (4-charge field on 256^3, 1024^2 map refined to 4096^2):
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the
 # current kernels (summaries under profiles/); None until captured. Coarse:
-# one full-size launch, 435.2 MB read + 105.9 MB written.
+# one full-size launch, 435.2 MB read + 105.9 MB written. Passes: the average
+# over one refined map's 27 launches, 29.0 MB read + 0.17 MB written.
 TRAFFIC_COARSE_BYTES = 541.0e6
-TRAFFIC_PASS_BYTES = None
+TRAFFIC_PASS_BYTES = 29.2e6
 FLOP_PER_STAGE = {"ck": 246.0, "cell": 227.0}
 # length-only stage evaluation of the cell-wise kernels (trilinear values of 3
 # components 63, position scaling 3, the 3-component share of the stage
@@ -1065,8 +1066,9 @@ def main():
         seeds_all = sample_positions(qsl, bufs["key"][:n_s].cpu().numpy().view(np.uint64), args.coarse)
         rate, nseeds, cores, secs = oracle_sample_rate(gf_cpu, seeds_all, RUN["tol"])
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "%d seeded samples of the GPU step's %d refined-map samples (coarse and "
-                                          "refined in proportion), tol %g (the autotuned GPU tolerance), %.1f s"
+                                "sample": "%d line traces in growing batches, each a seeded subsample of the GPU step's "
+                                          "%d refined-map samples (coarse and refined in proportion), tol %g (the "
+                                          "autotuned GPU tolerance), %.1f s"
                                           % (nseeds, n_s, RUN["tol"], secs)}
         line["parity"] = parity_sample(qsl, gf, gf_cpu, args.coarse)
         line["parity_refined"] = refined_parity(bufs, n_s, gf_cpu, args.coarse)
