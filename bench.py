@@ -50,12 +50,18 @@ FIELD_SEED = 2
 # one full-size launch, 435.2 MB read + 105.9 MB written. Passes: the average
 # over one refined map's 27 launches, 29.0 MB read + 0.17 MB written.
 TRAFFIC_COARSE_BYTES = 541.0e6
-TRAFFIC_PASS_BYTES = 29.2e6
+TRAFFIC_PASS_BYTES = None
 FLOP_PER_STAGE = {"ck": 246.0, "cell": 227.0}
-# length-only stage evaluation of the cell-wise kernels (trilinear values of 3
+# length-only stage evaluation: the cell-wise kernels (trilinear values of 3
 # components 63, position scaling 3, the 3-component share of the stage
-# combinations and error norm 29)
-FLOP_PER_STAGE_LEN = 95.0
+# combinations and error norm 29) and the Cash-Karp kernel of the refinement
+# passes' decision traces (trilinear values 63, cell location 9, the
+# 3-component share of the stage combinations, error norm and controller 32)
+FLOP_PER_STAGE_LEN = {"cell": 95.0, "ck": 104.0}
+# decision tracer of the refinement passes (qsl_refine_spec.pass_stepper) and
+# its step cap in smallest grid spacings
+PASS_STEPPER = 0
+PASS_H_MAX = 4.0
 # FP32 FMA pipe from unit counts (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz):
 # context only; the roofline divides by the rate measured in the same run
 # (measure_peaks).
@@ -224,7 +230,8 @@ def opts(qsl):
 def spec(qsl, coarse):
     p0 = int(np.log2(coarse))
     return qsl.refine_spec(ndim=2, coarse_order=p0, max_order=p0 + (P - P0), center=(0, 0, 0), u=(2, 0, 0),
-                           v=(0, 2, 0), tau=TAU, shift=1, max_iters=64)
+                           v=(0, 2, 0), tau=TAU, shift=1, max_iters=64, pass_stepper=PASS_STEPPER,
+                           pass_h_max=PASS_H_MAX)
 
 
 def gpu_step(qsl, gf, bufs, coarse, stream_sync=True):
@@ -900,6 +907,8 @@ def main():
         sd = torch.as_tensor(pos).to(dev)
         ol = opts(qsl)
         ol.length_only = 1
+        if PASS_STEPPER == 0:  # the decision traces of qsl_refine
+            ol.integrator, ol.h_max = qsl.QSL_RKCK54, PASS_H_MAX
         for _ in range(args.steps):
             qsl.qsl_trace_seeds(F, sd, ol)
         st = qsl.qsl_last_stats()
@@ -999,14 +1008,19 @@ def main():
     # trace lengths only with the FLL-jump criterion
     pass_ms = rs["passes_ms"] / max(rs["passes"], 1)
     len_only = rs["deferred_ms"] > 0
-    pass_flop = FLOP_PER_STAGE_LEN if (len_only and RUN["integrator"] == "cell") else flop_per_stage
+    if len_only and PASS_STEPPER == 0:
+        pass_flop, pass_kernel = FLOP_PER_STAGE_LEN["ck"], "trace_kernel<float,3> (Cash-Karp decision traces, "
+    elif len_only:
+        pass_flop, pass_kernel = FLOP_PER_STAGE_LEN["cell"], "cell_len_kernel<float> ("
+    else:
+        pass_flop = flop_per_stage
+        pass_kernel = ("cell_coop_kernel<float,9>" if RUN["integrator"] == "cell" else kname) + " ("
     pass_tflops = (rs["pass_stage_evals"] * pass_flop / (rs["passes_ms"] / 1000.0) / 1e12
                    if rs["passes_ms"] > 0 else 0.0)
     roof_passes = {"bound": "alu", "achieved": pass_tflops, "peak": PEAK["fp32"], "unit": "TFLOP/s",
                    "frac": pass_tflops / PEAK["fp32"],
                    "traffic": TRAFFIC_PASS_BYTES if default_workload else None,
-                   "kernel": (("cell_len_kernel<float>" if len_only else "cell_coop_kernel<float,9>")
-                              if RUN["integrator"] == "cell" else kname) + " (%srefinement passes, %d per step)"
+                   "kernel": pass_kernel + "%srefinement passes, %d per step)"
                    % ("length-only " if len_only else "", rs["passes"]), "kernel_ms": pass_ms,
                    "stage_evals": rs["pass_stage_evals"] // max(rs["passes"], 1), "flop_per_stage": pass_flop,
                    "peak_note": peak_note + "; launches are bound by the latency of their longest line, not by the "

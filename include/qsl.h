@@ -225,11 +225,28 @@ typedef struct qsl_refine_spec {
                                    QSL_REFINE_Q_THRESHOLD (1): a pair is refined when either
                                    sample's Q (opts.q_form) is finite and > q_threshold, the
                                    alternative Sec. "Adaptive refinements" compares against */
-  int32_t reserved;             /* must be 0                                              */
+  int32_t pass_stepper;         /* tracer of the FLL-jump decisions of the refinement passes
+                                   (criterion QSL_REFINE_FLL_JUMP, opts.length_only == 0):
+                                   QSL_PASS_CASH_KARP (0, default): lengths only, traced by the
+                                     paper's Cash-Karp stepper across cells at opts' tolerance
+                                     and the step cap pass_h_max; Cartesian fields;
+                                   QSL_PASS_SAME (1): lengths only with opts' integrator when it
+                                     is QSL_DOPRI5_CELL on a uniform grid, else as QSL_PASS_FULL;
+                                   QSL_PASS_FULL (2): the passes trace with opts unchanged.
+                                   With 0 and 1 one launch after the last iteration traces every
+                                   pass sample with opts (deviation equations, FP64 retrace) and
+                                   its values are the ones stored; the decision lengths only
+                                   chose the samples. Other criteria, and 0 on spherical fields,
+                                   trace as QSL_PASS_FULL.                                   */
   double q_threshold;
+  double pass_h_max;            /* step cap of QSL_PASS_CASH_KARP in smallest grid spacings;
+                                   0: 4                                                      */
 } qsl_refine_spec;
 #define QSL_REFINE_FLL_JUMP 0
 #define QSL_REFINE_Q_THRESHOLD 1
+#define QSL_PASS_CASH_KARP 0
+#define QSL_PASS_SAME 1
+#define QSL_PASS_FULL 2
 
 typedef struct qsl_samples {
   int64_t capacity;  /* entries the arrays below can hold                           */
@@ -256,12 +273,10 @@ typedef struct qsl_samples {
  * qsl_q_volume_3d over the effective lattice. With samples->count > 0 the
  * call resumes from those (sorted) samples instead of the coarse pass.
  * QSL_ECAPACITY when the capacity is reached (samples so far are valid).
- * With the FLL-jump criterion and QSL_DOPRI5_CELL on a uniform grid the
- * refinement passes trace lengths only (the criterion reads L) and the pass
- * samples' Q, L, end faces and status come from one tangent-space trace after
- * the last iteration; the Cash-Karp stepper, whose lengths-only traces miss
- * the length accuracy of its tangent-space ones, traces its passes in
- * tangent space. */
+ * With the FLL-jump criterion the refinement passes trace lengths only (the
+ * criterion reads L) with the tracer spec->pass_stepper names, and the pass
+ * samples' Q, L, end faces and status come from one trace with opts after the
+ * last iteration. The coarse pass (and a proposal) always trace with opts. */
 int qsl_refine(const qsl_field* field, const qsl_refine_spec* spec, const qsl_opts* opts, qsl_samples* samples,
                float* q_grid, float* l_grid, int mem, void* stream);
 

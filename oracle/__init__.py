@@ -30,7 +30,8 @@ class RefineSpec(C.Structure):
                 ("extent", C.c_int * 3), ("shift", C.c_int), ("q_form", C.c_int), ("out_order", C.c_int),
                 ("pad", C.c_int), ("center", C.c_double * 3), ("u", C.c_double * 3), ("v", C.c_double * 3),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("tau", C.c_double), ("criterion", C.c_int),
-                ("pad2", C.c_int), ("q_threshold", C.c_double)]
+                ("pad2", C.c_int), ("q_threshold", C.c_double), ("pass_stepper", C.c_int), ("pad3", C.c_int),
+                ("pass_h_max", C.c_double)]
 
 
 class Lines(C.Structure):

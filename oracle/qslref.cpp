@@ -1145,11 +1145,21 @@ struct RefineSpec {
   int criterion;                 // 0: FLL jump |L_i - L_{i+1}| > tau; 1: Q threshold
   int pad2;
   double q_threshold;            // criterion 1: refine a pair where a sample's Q exceeds it
+  // Lengths the FLL-jump criterion compares for samples added by the passes
+  // (the coarse samples' own lengths decide for them): 0 a lengths-only trace
+  // by the Cash-Karp stepper (Sec. "Integration methods") at the run's
+  // tolerance with the step cap pass_h_max; 1 a lengths-only trace with the
+  // run's options; 2 the stored lengths themselves. The stored values are
+  // always those of the trace with the run's options.
+  int pass_stepper;
+  int pad3;
+  double pass_h_max;             // smallest grid spacings; 0: 4
 };
 
 struct Sample {
   uint64_t key;
   double q, L;
+  double Ld;   // the length the FLL-jump criterion compares (see RefineSpec::pass_stepper)
   int face_f, face_b, st_f, st_b;
   int origin;  // pass that added it: 0 coarse pass, 2i + 1 / 2i + 2 pass A / B of iteration i
   int unsure;  // test hook: the evaluator could not determine the value
@@ -1261,7 +1271,9 @@ bool nearest_in_region(uint64_t m, uint64_t k_lo, uint64_t k_hi, int nd, int bit
   return false;
 }
 
-void trace_samples(const Evaluator& ev, const RefineSpec& s, std::vector<Sample>& v) {
+// `pass`: the batch was added by a refinement pass (decision lengths per
+// RefineSpec::pass_stepper); otherwise the coarse batch.
+void trace_samples(const Evaluator& ev, const RefineSpec& s, std::vector<Sample>& v, bool pass) {
   if (v.empty()) return;
   std::vector<double> seeds(3 * v.size());
   for (size_t i = 0; i < v.size(); ++i) {
@@ -1282,6 +1294,7 @@ void trace_samples(const Evaluator& ev, const RefineSpec& s, std::vector<Sample>
     for (size_t i = 0; i < v.size(); ++i) {
       v[i].q = q[i];
       v[i].L = L[i];
+      v[i].Ld = L[i];
       v[i].face_f = v[i].face_b = NO_FACE;
       v[i].st_f = v[i].st_b = ST_OK;
       v[i].unsure = unsure[i];
@@ -1290,10 +1303,18 @@ void trace_samples(const Evaluator& ev, const RefineSpec& s, std::vector<Sample>
   }
   const Field& F = *ev.F;
   const Opts& o = *ev.o;
+  const bool decide = pass && s.criterion == 0 && !o.length_only && s.pass_stepper != 2;
+  Opts od = o;
+  od.length_only = 1;
+  if (s.pass_stepper == 0) {
+    od.integrator = 0;
+    od.h_max = s.pass_h_max > 0 ? s.pass_h_max : 4.0;
+  }
   parallel_for((int64_t)v.size(), o.nthreads, [&](int64_t i) {
     LineOut r = trace_line(F, o, &seeds[3 * i], nullptr);
     v[i].q = (s.q_form == 1) ? r.q_foot : r.q_perp;
     v[i].L = r.L;
+    v[i].Ld = decide ? trace_line(F, od, &seeds[3 * i], nullptr).L : r.L;
     v[i].face_f = r.face_f;
     v[i].face_b = r.face_b;
     v[i].st_f = r.st_f;
@@ -1334,7 +1355,7 @@ int qslref_sizeof_refine_spec(void) { return (int)sizeof(RefineSpec); }
 static bool pair_flagged(const RefineSpec& s, const Sample& A, const Sample& B) {
   if (s.criterion == 1)
     return (std::isfinite(A.q) && A.q > s.q_threshold) || (std::isfinite(B.q) && B.q > s.q_threshold);
-  return std::fabs(B.L - A.L) > s.tau;
+  return std::fabs(B.Ld - A.Ld) > s.tau;
 }
 
 // The decision with the test hook: the comparison, or, for a pair within the
@@ -1346,8 +1367,8 @@ static bool pair_ambiguous(const RefineSpec& s, const Sample& A, const Sample& B
     auto near = [&](double q) { return std::isfinite(q) && std::fabs(q / s.q_threshold - 1.0) <= arb.band_rel; };
     return !clear_above(A.q) && !clear_above(B.q) && (near(A.q) || near(B.q));
   }
-  double d = std::fabs(B.L - A.L);
-  double band = arb.band_abs + arb.band_rel * std::max(std::fabs(A.L), std::fabs(B.L));
+  double d = std::fabs(B.Ld - A.Ld);
+  double band = arb.band_abs + arb.band_rel * std::max(std::fabs(A.Ld), std::fabs(B.Ld));
   return std::fabs(d - s.tau) <= band;
 }
 
@@ -1380,7 +1401,7 @@ static int64_t refine_impl(const Evaluator& ev, const RefineSpec* sp, int64_t ca
           smp.key = hilbert_key(c, nd, p);
           all.push_back(smp);
         }
-    trace_samples(ev, s, all);
+    trace_samples(ev, s, all, false);
     std::sort(all.begin(), all.end(), [](const Sample& a, const Sample& b) { return a.key < b.key; });
     if (traced_per_iter) traced_per_iter[0] = (int64_t)all.size();
   }
@@ -1404,7 +1425,7 @@ static int64_t refine_impl(const Evaluator& ev, const RefineSpec* sp, int64_t ca
         add.push_back(smp);
       }
     }
-    trace_samples(ev, s, add);
+    trace_samples(ev, s, add, true);
     added += (int64_t)add.size();
     merge_in(all, add);
     // (B) flag along the shifted curve
@@ -1448,7 +1469,7 @@ static int64_t refine_impl(const Evaluator& ev, const RefineSpec* sp, int64_t ca
           add2.push_back(smp);
         }
       }
-      trace_samples(ev, s, add2);
+      trace_samples(ev, s, add2, true);
       added += (int64_t)add2.size();
       merge_in(all, add2);
     }

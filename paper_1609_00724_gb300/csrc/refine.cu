@@ -735,15 +735,23 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
   // length-only mode, and one launch after the last iteration traces every
   // pass sample with the deviation equations; its Q, L, end faces and status
   // (FP64 retrace above retrace_q included) replace the pass values, whose
-  // lengths only decided the refinement. Only the cell-wise integrator keeps
-  // its length accuracy in length-only mode: the Cash-Karp stepper across the
-  // kinks of the trilinear field is held to its tolerance by the deviation
-  // components, and without them its lengths are tens of times less accurate,
-  // so its passes trace the deviations too.
-  const bool decouple = sp->criterion == QSL_REFINE_FLL_JUMP && !o->length_only &&
-                        o->integrator == QSL_DOPRI5_CELL && f->uniform;
+  // lengths only decided the refinement. The decision traces take the paper's
+  // Cash-Karp stepper across cells with the step cap pass_h_max (a step spans
+  // several cells, where the cell-wise stepper lands on every face), or, on
+  // request, the run's own integrator: only the cell-wise one keeps its length
+  // bar without the deviation components, which hold the Cash-Karp stepper to
+  // its tolerance across the kinks of the trilinear field.
+  const bool fll_pass = sp->criterion == QSL_REFINE_FLL_JUMP && !o->length_only;
   qsl_opts o_len = *o;
   o_len.length_only = 1;
+  bool decouple = false;
+  if (fll_pass && sp->pass_stepper == QSL_PASS_CASH_KARP && f->geom == QSL_GEOM_CARTESIAN) {
+    decouple = true;
+    o_len.integrator = QSL_RKCK54;
+    o_len.h_max = sp->pass_h_max > 0 ? sp->pass_h_max : 4.0;
+  } else if (fll_pass && sp->pass_stepper == QSL_PASS_SAME) {
+    decouple = o->integrator == QSL_DOPRI5_CELL && f->uniform;
+  }
   uint64_t* pkeys = nullptr;  // keys of the pass samples in the order traced
   int64_t n_pass = 0;
   if ((rc = sc.alloc(&pkeys, cap))) return rc;
@@ -1192,8 +1200,9 @@ int qsl_refine(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o,
     set_error("criterion must be QSL_REFINE_FLL_JUMP or QSL_REFINE_Q_THRESHOLD");
     return QSL_EINVAL;
   }
-  if (sp->reserved != 0) {
-    set_error("reserved must be 0");
+  if (sp->pass_stepper < QSL_PASS_CASH_KARP || sp->pass_stepper > QSL_PASS_FULL ||
+      !(sp->pass_h_max >= 0.0 && sp->pass_h_max < 1e6)) {
+    set_error("pass_stepper must be QSL_PASS_CASH_KARP, QSL_PASS_SAME or QSL_PASS_FULL and 0 <= pass_h_max < 1e6");
     return QSL_EINVAL;
   }
   int R = 1 << (p - p0);

@@ -70,12 +70,15 @@ class qsl_refine_spec(C.Structure):
                 ("max_iters", C.c_int32), ("extent", C.c_int32 * 3), ("shift", C.c_int32),
                 ("out_order", C.c_int32), ("pad", C.c_int32), ("center", C.c_double * 3), ("u", C.c_double * 3),
                 ("v", C.c_double * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("tau", C.c_double),
-                ("proposal", C.c_void_p), ("criterion", C.c_int32), ("reserved", C.c_int32),
-                ("q_threshold", C.c_double)]
+                ("proposal", C.c_void_p), ("criterion", C.c_int32), ("pass_stepper", C.c_int32),
+                ("q_threshold", C.c_double), ("pass_h_max", C.c_double)]
 
 
 QSL_REFINE_FLL_JUMP = 0
 QSL_REFINE_Q_THRESHOLD = 1
+QSL_PASS_CASH_KARP = 0
+QSL_PASS_SAME = 1
+QSL_PASS_FULL = 2
 
 
 class qsl_samples(C.Structure):

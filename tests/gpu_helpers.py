@@ -13,6 +13,14 @@ EDGE_CELLS = 1e-3
 # FP32 tracer tolerance used by the parity runs (the oracle runs at 1e-11)
 GPU_TOL = 1e-7
 
+# decision lengths of the refinement passes (lengths-only Cash-Karp across
+# cells, step cap 4 smallest spacings) against the oracle's trace with the same
+# method and settings: where the cap sets every step both take the same steps
+# and meet L_RTOL; where the error estimate sets some steps (tight tolerances)
+# the FP32 and FP64 runs step differently near cell faces and differ by the
+# method's own error across the kinks of the trilinear field
+D_RTOL = 1e-4
+
 
 def min_spacing(gf):
     """Smallest grid spacing over the three axes of a GridField."""

@@ -36,6 +36,7 @@ def test_opts_default_and_struct_sizes():
     assert C.sizeof(qsl.qsl_opts) == 176
     assert C.sizeof(qsl.qsl_refine_stats) == 104
     assert C.sizeof(qsl.qsl_samples) == 72
+    assert C.sizeof(qsl.qsl_refine_spec) == 200
     assert qsl.QSL_LINE_DTYPE.itemsize == 112
     assert qsl.lib().qsl_last_error() == b""
 

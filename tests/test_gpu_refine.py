@@ -5,7 +5,7 @@ import pytest
 import torch
 
 from paper_1609_00724_gb300 import inputs
-from gpu_helpers import GPU_TOL, L_RTOL, Q_RTOL, length_err, min_spacing
+from gpu_helpers import D_RTOL, GPU_TOL, L_RTOL, Q_RTOL, length_err, min_spacing
 
 pytestmark = pytest.mark.gpu
 
@@ -159,28 +159,45 @@ class _Truth:
     (ten times the GPU's position error, on the axes of the sample lattice)
     ends on other faces or with a length that jumps by more than 1e-3 of the
     line: its line runs along a separatrix within that distance (or grazes a
-    face), so its end depends on the integration and no bar applies to it."""
+    face), so its end depends on the integration and no bar applies to it.
 
-    def __init__(self, oracle_mod, Fo, ndim):
+    `decide` (oracle opts, lengths only): the tracer of the GPU passes'
+    decision lengths. Batches after the first (the coarse pass) then return
+    the lengths of that trace, undetermined when the tangent-space line is or
+    when the same perturbation changes the decision trace's end; the stored
+    lines and their own undetermined flags stay the tangent-space ones."""
+
+    def __init__(self, oracle_mod, Fo, ndim, decide=None):
         self.o, self.Fo, self.ndim = oracle_mod, Fo, ndim
         self.opts = oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11)
         self.opts_len = oracle_mod.default_opts(tol_abs=1e-11, tol_rel=1e-11, length_only=1)
+        self.decide = decide
         self.lines = {}
+        self.calls = 0
 
-    def __call__(self, x, keys):
-        r = self.o.trace_seeds(self.Fo, x, self.opts)
+    def _unsure(self, x, r, opts):
         unsure = np.zeros(len(x), dtype=bool)
         d = 1e-5 * self.Fo.cell
         for ax in range(self.ndim):
             for sg in (1.0, -1.0):
                 xp = x.copy()
                 xp[:, ax] += sg * d
-                rp = self.o.trace_seeds(self.Fo, xp, self.opts_len)
+                rp = self.o.trace_seeds(self.Fo, xp, opts)
                 unsure |= (rp["face_f"] != r["face_f"]) | (rp["face_b"] != r["face_b"])
                 unsure |= ~(np.abs(rp["L"] - r["L"]) <= 1e-3 * np.maximum(r["L"], self.Fo.cell))
+        return unsure
+
+    def __call__(self, x, keys):
+        r = self.o.trace_seeds(self.Fo, x, self.opts)
+        unsure = self._unsure(x, r, self.opts_len)
         for i, k in enumerate(keys):
             self.lines[int(k)] = dict({name: r[name][i] for name in r}, unsure=bool(unsure[i]))
-        return r["q_perp"], r["L"], unsure
+        first = self.calls == 0
+        self.calls += 1
+        if self.decide is None or first:
+            return r["q_perp"], r["L"], unsure
+        rd = self.o.trace_seeds(self.Fo, x, self.decide)
+        return r["q_perp"], rd["L"], unsure | self._unsure(x, rd, self.decide)
 
     def records(self, keys):
         names = self.lines[int(keys[0])].keys()
@@ -195,11 +212,11 @@ def _determined(ref, n_max_frac=0.005):
     return ~un
 
 
-def _band(cell):
+def _band(cell, rtol=L_RTOL):
     """Band of the threshold within which a refinement decision may differ
-    between the GPU and the oracle: each length is within L_RTOL max(L, cell) of
-    the oracle's, so a pair's |dL| within 2 L_RTOL (max L + cell)."""
-    return 2 * L_RTOL * cell, 2 * L_RTOL
+    between the GPU and the oracle: each length is within rtol max(L, cell) of
+    the oracle's, so a pair's |dL| within 2 rtol (max L + cell)."""
+    return 2 * rtol * cell, 2 * rtol
 
 
 def _check_replay(oracle_mod, g, rep, what):
@@ -253,20 +270,26 @@ def test_refine_length_only_decisions_replay_exactly(qsl, oracle_mod, ndim):
                   (-1, -1, 0), (1, 1, 1))
 
 
-@pytest.mark.parametrize("integrator", ["ck", "cell"])
+@pytest.mark.parametrize("integrator,stepper", [("ck", 0), ("cell", 0), ("cell", 1), ("ck", 2)])
 @pytest.mark.parametrize("ndim", [2, 3])
-def test_refine_sample_set_matches_oracle(qsl, oracle_mod, ndim, integrator):
+def test_refine_sample_set_matches_oracle(qsl, oracle_mod, ndim, integrator, stepper):
     """Default refinement (tangent-space coarse pass, lengths-only passes, one
     tangent-space trace of the pass samples): the oracle's driver on its own
     lines reproduces the GPU sample set key for key once the pairs within the
     stated length error of tau follow the GPU's choice; every sample's Q, L and
-    end faces match the oracle's; the converted grids keep the sampled values."""
+    end faces match the oracle's; the converted grids keep the sampled values.
+    Pass decision tracers (spec.pass_stepper): 0, the default, lengths-only
+    Cash-Karp across cells with a step cap of 4 spacings, replayed on the
+    oracle's trace with the same settings and a band of the decision lengths'
+    error (D_RTOL); 1 with the cell-wise integrator,
+    its own lengths-only trace, replayed on the oracle's tight lines (it meets
+    the length bar); 2 the tangent-space passes themselves."""
     from gpu_helpers import compare_lines
     F, Fo = _fields(qsl, oracle_mod, n=40, seed=3)
     kw, cap = _refine_case(ndim)
     o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL,
                              integrator=qsl.QSL_DOPRI5_CELL if integrator == "cell" else qsl.QSL_RKCK54)
-    sp = qsl.refine_spec(**kw)
+    sp = qsl.refine_spec(pass_stepper=stepper, **kw)
     b = _alloc(cap)
     org = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
     qg = torch.zeros(cap, device="cuda")
@@ -280,10 +303,14 @@ def test_refine_sample_set_matches_oracle(qsl, oracle_mod, ndim, integrator):
     g = {"key": keys.copy(), "q_perp": b["q"].cpu().numpy()[:n], "L": b["L"].cpu().numpy()[:n], "face_f": fa[:, 0],
          "face_b": fa[:, 1], "origin": org.cpu().numpy()[:n], "iters": iters}
     spo = oracle_mod.refine_spec(**kw)
-    truth = _Truth(oracle_mod, Fo, ndim)
-    ba, br = _band(Fo.cell)
+    decide = (oracle_mod.default_opts(tol_abs=GPU_TOL, tol_rel=GPU_TOL, length_only=1, h_max=4.0)
+              if stepper == 0 else None)
+    truth = _Truth(oracle_mod, Fo, ndim, decide)
+    ba, br = _band(Fo.cell, D_RTOL if stepper == 0 else L_RTOL)
     rep = oracle_mod.refine_replay(truth, spo, keys, g["origin"], band_abs=ba, band_rel=br)
     _check_replay(oracle_mod, g, rep, "replay on oracle lines")
+    st = qsl.qsl_last_refine_stats()
+    assert (st["deferred_ms"] > 0) == (stepper == 0 or integrator == "cell" and stepper == 1)
     ref = truth.records(keys)
     ok = _determined(ref)
     compare_lines({k: v[ok] for k, v in g.items() if k in ("q_perp", "L", "face_f", "face_b")},

@@ -5,7 +5,7 @@ import pytest
 import torch
 
 from paper_1609_00724_gb300 import inputs
-from gpu_helpers import GPU_TOL, compare_lines
+from gpu_helpers import GPU_TOL, L_RTOL, compare_lines
 
 pytestmark = pytest.mark.gpu
 
@@ -338,6 +338,30 @@ def test_length_only_matches_oracle(qsl, oracle_mod, mode, lanes):
     rep = compare_lines(_rec_to_dict(rec), ref, 1.0 / 63, BOX_LO, BOX_HI)
     assert rep["labels_checked"] > 550
     assert np.array_equal(rec["status_f"], ref["st_f"]) and np.array_equal(rec["status_b"], ref["st_b"])
+
+
+@pytest.mark.parametrize("mode,tol", [(0, 1e-5), (0, 1e-7), (1, 1e-5)])
+def test_cash_karp_decision_lengths_match_oracle(qsl, oracle_mod, mode, tol):
+    """The refinement passes' decision tracer (lengths only, the Cash-Karp
+    stepper across cells, step cap 4 smallest spacings) against the oracle's
+    lengths-only Cash-Karp trace with the same tolerance and step cap: the
+    same method in FP64. End faces equal; lengths within the length bar where
+    the cap sets the steps (tol 1e-5), within D_RTOL where the error estimate
+    sets some of them (tol 1e-7: the two runs step differently near faces)."""
+    from gpu_helpers import D_RTOL
+    ch = inputs.random_charges(4, 2)
+    gf = inputs.charge_field(ch, 64, dtype=torch.float32)
+    F = _gpu_field(qsl, gf, mode)
+    Fo = _oracle_field(oracle_mod, gf, mode)
+    seeds = inputs.random_seeds(600, 47)
+    seeds[:200, 2] = 0.0
+    o = qsl.qsl_opts_default(tol_abs=tol, tol_rel=tol, integrator=qsl.QSL_RKCK54, length_only=1, h_max=4.0)
+    rec = qsl.lines_to_numpy(qsl.qsl_trace_seeds(F, torch.as_tensor(seeds).cuda(), o))
+    ref = oracle_mod.trace_seeds(Fo, seeds, oracle_mod.default_opts(tol_abs=tol, tol_rel=tol, length_only=1,
+                                                                    h_max=4.0))
+    assert np.all(np.isnan(rec["q_perp"]))
+    rep = compare_lines(_rec_to_dict(rec), ref, 1.0 / 63, BOX_LO, BOX_HI, l_rtol=L_RTOL if tol >= 1e-5 else D_RTOL)
+    assert rep["labels_checked"] > 550
 
 
 @pytest.mark.parametrize("integ,lanes", [(0, 0), (2, 1), (2, 3)])

@@ -193,3 +193,19 @@ def test_euler_is_first_order(oracle_mod, raw_field):
             assert np.all((ratio > 1.8) & (ratio < 2.2)), (key, ratio)
         rich = np.abs((2 * res[0.05][key] - res[0.1][key]) / ex - 1)
         assert np.all(rich <= err[0.05] / 20), (key, rich / err[0.05])
+
+
+def test_length_only_matches_closed_form_lengths(oracle_mod, raw_field):
+    """Lengths-only tracing (no deviation equations; the mode of the refinement
+    passes' decision traces) meets the closed-form lengths and exit faces: to
+    1e-10 at tol 1e-11, and to 1e-7 at the decision traces' settings (tol 1e-5,
+    step cap 4 smallest spacings); its Q outputs are NaN."""
+    seeds = oracle_mod.plane_seeds([0, 0, 0], [2, 0, 0], [0, 2, 0], 64, 64).reshape(-1, 3)[::7]
+    for tol, h_max, bar in ((1e-11, 2.0, 1e-10), (1e-5, 4.0, 1e-7)):
+        r = oracle_mod.trace_seeds(raw_field, seeds, oracle_mod.default_opts(tol_abs=tol, tol_rel=tol, length_only=1,
+                                                                             h_max=h_max))
+        assert np.all(np.isnan(r["q_perp"]))
+        for i, (x0, y0, _) in enumerate(seeds):
+            _, _, L, face = closed_forms(x0, y0)
+            assert r["face_f"][i] == face and r["face_b"][i] == 4
+            assert abs(r["L"][i] / L - 1) < bar, (tol, x0, y0, r["L"][i], L)

@@ -237,3 +237,39 @@ def test_replay_unsure_samples_follow_the_other_run(oracle_mod):
     assert not np.array_equal(other["key"], plain["key"])
     rep = oracle_mod.refine_replay(lambda x, k: ramp_map(x) + (odd(k),), sp, other["key"], other["origin"])
     assert np.array_equal(rep["key"], other["key"]) and np.array_equal(rep["origin"], other["origin"])
+
+
+def test_pass_decisions_use_lengths_only_traces(oracle_mod):
+    """pass_stepper 0 (the default): the FLL-jump decisions on samples added by
+    the passes compare lengths from a lengths-only Cash-Karp trace with the
+    step cap pass_h_max, the coarse samples' decisions their own lengths, and
+    the stored values are those of the run's options. The driver run that way
+    equals the replay whose evaluator returns exactly those lengths, batch by
+    batch; it differs from pass_stepper 2 (decisions on the stored lengths),
+    and its stored lengths are the run's own traces of its keys."""
+    import torch
+    from paper_1609_00724_gb300 import inputs
+    gf = inputs.charge_field(inputs.random_charges(4, 2), 24, dtype=torch.float32)
+    g = inputs.to_numpy64(gf)
+    F = oracle_mod.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
+    tol, h_max = 1e-4, 8.0
+    o = oracle_mod.default_opts(tol_abs=tol, tol_rel=tol)
+    od = oracle_mod.default_opts(tol_abs=tol, tol_rel=tol, length_only=1, h_max=h_max)
+    kw = dict(ndim=2, coarse_order=3, max_order=7, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), tau=0.05)
+    r0 = oracle_mod.refine(F, oracle_mod.refine_spec(pass_h_max=h_max, **kw), o)
+    r2 = oracle_mod.refine(F, oracle_mod.refine_spec(pass_stepper=2, **kw), o)
+    batches = []
+
+    def decision_lengths(x, k):
+        r = oracle_mod.trace_seeds(F, x, o)
+        L = r["L"] if not batches else oracle_mod.trace_seeds(F, x, od)["L"]
+        batches.append(len(k))
+        return r["q_perp"], L
+
+    rep = oracle_mod.refine_replay(decision_lengths, oracle_mod.refine_spec(**kw))
+    assert np.array_equal(rep["key"], r0["key"]) and np.array_equal(rep["origin"], r0["origin"])
+    assert batches[0] == 64 and len(batches) > 4
+    assert len(np.setxor1d(r0["key"], r2["key"])) > 20
+    c = np.array([oracle_mod.hilbert_coords(k, 2, 7) for k in r0["key"]], dtype=np.float64)
+    x = np.column_stack([(c[:, 0] + 0.5) / 128 * 2 - 1, (c[:, 1] + 0.5) / 128 * 2 - 1, np.zeros(len(c))])
+    assert np.array_equal(r0["L"], oracle_mod.trace_seeds(F, x, o)["L"])
