@@ -2549,6 +2549,401 @@ __global__ void __launch_bounds__(256) cell_len_kernel(const __grid_constant__ T
   if (lane == 0 && any_to && P.timeout_flag) atomicExch(P.timeout_flag, 1);
 }
 
+// ------------------------------------------------------------ Cash-Karp lengths-only tracer
+// The decision traces of the refinement passes (qsl_refine_spec.pass_stepper
+// QSL_PASS_CASH_KARP): the paper's Cash-Karp stepper across cells (Sec.
+// "Integration methods") on the position only, one lane per line direction,
+// with the step control, error norm and face landing of trace_kernel. A stage
+// takes its derivative from the trilinear polynomials of the cell its point
+// lies in; those coefficients stay in registers while the following stages
+// fall in the same cell (a step at the passes' step cap spans a few cells), so
+// only a stage that enters another cell loads corners.
+template <class R>
+struct CkCell {
+  int ci[3];    // lower vertex of the cached cell (absolute)
+  R a[3][8];    // its polynomials (len_coeffs)
+};
+
+// Stage derivative in cell units at the local-frame point ic + t.
+template <class R, class V>
+__device__ __forceinline__ void ck_len_rhs(const V* fv, const int* n, int64_t sy, int64_t sz, bool raw,
+                                           const R* ih, const int* ic, const R* t, CkCell<R>& C, R* k) {
+  int ci[3];
+  R uu[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R lim = R(n[a]);
+    const R fl = floor(fmin(fmax(t[a], -lim), lim));
+    int i = ic[a] + (int)fl;
+    i = min(max(i, 0), n[a] - 2);
+    uu[a] = t[a] - R(i - ic[a]);
+    ci[a] = i;
+  }
+  if (ci[0] != C.ci[0] || ci[1] != C.ci[1] || ci[2] != C.ci[2]) {
+    const V* p = fv + ((int64_t)ci[2] * sz + (int64_t)ci[1] * sy + ci[0]);
+    V q[8];
+    q[0] = ldg4(p);
+    q[1] = ldg4(p + 1);
+    q[2] = ldg4(p + sy);
+    q[3] = ldg4(p + sy + 1);
+    q[4] = ldg4(p + sz);
+    q[5] = ldg4(p + sz + 1);
+    q[6] = ldg4(p + sz + sy);
+    q[7] = ldg4(p + sz + sy + 1);
+    len_coeffs<R, V>(q, raw, ih, C.a);
+    C.ci[0] = ci[0];
+    C.ci[1] = ci[1];
+    C.ci[2] = ci[2];
+  }
+  len_rhs<R>(C.a, raw, ih, uu, k);
+}
+
+// One Cash-Karp step of signed size hh from the local-frame point ic + y.
+template <class R, class V>
+__device__ __forceinline__ void ck_len_step(const V* fv, const int* n, int64_t sy, int64_t sz, bool raw,
+                                            const R* ih, const int* ic, const R* y, R hh, CkCell<R>& C, R* dy,
+                                            R* yerr) {
+  R k1[3], k2[3], k3[3], k4[3], k5[3], k6[3], t[3];
+  ck_len_rhs<R, V>(fv, n, sy, sz, raw, ih, ic, y, C, k1);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t[i] = fma(hh, R(A21) * k1[i], y[i]);
+  ck_len_rhs<R, V>(fv, n, sy, sz, raw, ih, ic, t, C, k2);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t[i] = fma(hh, R(A31) * k1[i] + R(A32) * k2[i], y[i]);
+  ck_len_rhs<R, V>(fv, n, sy, sz, raw, ih, ic, t, C, k3);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t[i] = fma(hh, R(A41) * k1[i] + R(A42) * k2[i] + R(A43) * k3[i], y[i]);
+  ck_len_rhs<R, V>(fv, n, sy, sz, raw, ih, ic, t, C, k4);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    t[i] = fma(hh, R(A51) * k1[i] + R(A52) * k2[i] + R(A53) * k3[i] + R(A54) * k4[i], y[i]);
+  ck_len_rhs<R, V>(fv, n, sy, sz, raw, ih, ic, t, C, k5);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    t[i] = fma(hh, R(A61) * k1[i] + R(A62) * k2[i] + R(A63) * k3[i] + R(A64) * k4[i] + R(A65) * k5[i], y[i]);
+  ck_len_rhs<R, V>(fv, n, sy, sz, raw, ih, ic, t, C, k6);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    dy[i] = hh * (R(B1) * k1[i] + R(B3) * k3[i] + R(B4) * k4[i] + R(B6) * k6[i]);
+    yerr[i] = hh * (R(E1) * k1[i] + R(E3) * k3[i] + R(E4) * k4[i] + R(E5) * k5[i] + R(E6) * k6[i]);
+  }
+}
+
+// face_g (local frame) for a face id known only at run time: the axis
+// components are picked by selects, so that the arrays stay in registers.
+template <class R>
+__device__ __forceinline__ R face_gs(const R* lo, const R* hi, const int* ic, int f, const R* y, const R* d) {
+  const int a = f >> 1;
+  const bool up = (f & 1) != 0;
+  R bound = up ? sel3(a, hi[0], hi[1], hi[2]) : sel3(a, lo[0], lo[1], lo[2]);
+  bound -= R(sel3(a, ic[0], ic[1], ic[2]));
+  const R r = bound - sel3(a, y[0], y[1], y[2]);
+  const R dd = d ? sel3(a, d[0], d[1], d[2]) : R(0);
+  return up ? (dd - r) : (r - dd);
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Asks L1 for the corner rows of the cell holding the local-frame point
+// ic + t (clamped to the grid like a stage's cell, so the address is valid).
+template <class R, class V>
+__device__ __forceinline__ void ck_prefetch_cell(const V* fv, const int* n, int64_t sy, int64_t sz, const int* ic,
+                                                 const R* t) {
+  int cj[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R lim = R(n[a]);
+    const R fl = floor(fmin(fmax(t[a], -lim), lim));
+    cj[a] = min(max(ic[a] + (int)fl, 0), n[a] - 2);
+  }
+  const V* p = fv + ((int64_t)cj[2] * sz + (int64_t)cj[1] * sy + cj[0]);
+  prefetch_l1(p);
+  prefetch_l1(p + 1);
+  prefetch_l1(p + sy);
+  prefetch_l1(p + sy + 1);
+  prefetch_l1(p + sz);
+  prefetch_l1(p + sz + 1);
+  prefetch_l1(p + sz + sy);
+  prefetch_l1(p + sz + sy + 1);
+}
+
+// One line direction of the Cash-Karp lengths-only tracer, start to end, by
+// one lane (trace_kernel's steps for NC = 3 in the local frame). After each
+// accepted step the cells at a third, two thirds and the end of the next step
+// (predicted along this step's increment) are requested from L1, so that the
+// stages entering them find their corners there instead of waiting for L2.
+template <class R>
+__device__ __forceinline__ void ck_len_line(const TraceParams<R>& P, int64_t unit, unsigned long long* c_stage,
+                                            unsigned long long* c_acc, unsigned long long* c_rej,
+                                            unsigned long long* c_land, bool* timed_out,
+                                            unsigned long long t_start) {
+  typedef typename V4<R>::type V;
+  int64_t g;
+  double xd[3];
+  const Item<R>* E = resolve_seed(P, unit >> 1, &g, xd);
+  const R sgn = (unit & 1) ? R(-1) : R(1);
+  const V* const fv = E->F.v;
+  const bool raw = E->F.raw != 0;
+  const int n[3] = {E->F.n[0], E->F.n[1], E->F.n[2]};
+  const int64_t sy = n[0], sz = (int64_t)n[0] * n[1];
+  const R ih[3] = {R(E->F.inv_h[0]), R(E->F.inv_h[1]), R(E->F.inv_h[2])};
+  const R hh3[3] = {R(1) / ih[0], R(1) / ih[1], R(1) / ih[2]};
+  const R org[3] = {R(E->F.org[0]), R(E->F.org[1]), R(E->F.org[2])};
+  const R dlo[3] = {E->lo[0], E->lo[1], E->lo[2]}, dhi[3] = {E->hi[0], E->hi[1], E->hi[2]};
+  const R max_len = E->max_len, h_max = E->h_max, h_min = E->h_min, land_tol = E->land_tol;
+  const R tol_abs = P.tol_abs, tol_rel = P.tol_rel;
+  const long long max_steps = P.max_steps;
+  int ic[3];
+  R y[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    double fa = (xd[ax] - E->org_d[ax]) * E->inv_h_d[ax];
+    double fl = floor(fmin(fmax(fa, 0.0), (double)(n[ax] - 2)));
+    ic[ax] = (int)fl;
+    y[ax] = (R)(fa - fl);
+  }
+  int status = ST_RUNNING, lface = NO_FACE;
+  {
+    bool outside = false;
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+      if (face_g<R, true>(dlo, dhi, ic, f, y, (const R*)nullptr) > R(0)) outside = true;
+    if (outside || !isfinite(xd[0]) || !isfinite(xd[1]) || !isfinite(xd[2])) {
+      status = QSL_LINE_OUTSIDE;
+    } else {
+      Interp<R> I0;
+      interp<R, R, false, false, true, false>(E->F, y[0], y[1], y[2], I0, ic);
+      R m0 = sqrt(I0.b[0] * I0.b[0] + I0.b[1] * I0.b[1] + I0.b[2] * I0.b[2]);
+      if (!(m0 > R(0))) {
+        status = QSL_LINE_NULL;
+      } else {
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          if (status == ST_RUNNING && face_g<R, true>(dlo, dhi, ic, f, y, (const R*)nullptr) == R(0)) {
+            R bn = I0.b[f >> 1] * sgn;
+            R outw = (f & 1) ? bn : -bn;
+            if (outw > R(0)) {
+              status = QSL_LINE_OK;
+              lface = f;
+            }
+          }
+        }
+      }
+    }
+  }
+  if (status != ST_RUNNING) {
+    write_end<R, 3, true>(P, E, unit, y, ic, R(0), lface, status, 0);
+    return;
+  }
+  CkCell<R> C;
+  C.ci[0] = C.ci[1] = C.ci[2] = -1;
+  R mu = 0, muc = 0, h = E->h_init, hs = 0;
+  int steps = 0, phase = 0;
+  bool capped = false;
+  R la = 0, lb = 0, lga = 0, lgb = 0, lhm = 0, yh[3] = {0, 0, 0};
+  int lside = 0, lit = 0, lround = 0;
+  for (;;) {
+    if (P.timeout_ns && ((steps & 63) == 63)) {
+      if (globaltimer() - t_start > P.timeout_ns) *timed_out = true;
+    }
+    if (*timed_out) status = QSL_LINE_TIMEOUT;
+    hs = lhm;
+    if (status == ST_RUNNING && phase == 0) {
+      if (steps >= max_steps) status = QSL_LINE_MAXSTEPS;
+      R room = max_len - mu;
+      if (status == ST_RUNNING && !(room > R(0))) status = QSL_LINE_MAXLEN;
+      hs = fmin(h, h_max);
+      capped = false;
+      if (room <= hs) {
+        hs = room;
+        capped = true;
+      }
+    }
+    if (status != ST_RUNNING) break;
+    R dy[3], yerr[3];
+    ck_len_step<R, V>(fv, n, sy, sz, raw, ih, ic, y, sgn * hs, C, dy, yerr);
+    *c_stage += 6;
+    steps += 1;
+    if (phase == 0) {
+      R err = 0;
+      bool finite = true;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        R yn = y[i] + dy[i];
+        if (!isfinite(yn)) finite = false;
+        // position error in domain units, scaled by |x| in domain units
+        R base = org[i] + R(ic[i]) * hh3[i];
+        R e = fabs(yerr[i]) * hh3[i];
+        R ya = fabs(base + y[i] * hh3[i]);
+        R yb = fabs(base + yn * hh3[i]);
+        R sc = tol_abs + tol_rel * fmax(ya, yb);
+        err = fmax(err, cdiv(e, sc));
+      }
+      if (!finite) {
+        status = QSL_LINE_NONFINITE;
+      } else if (err > R(1)) {
+        *c_rej += 1;
+        h = hs * fmax(R(0.2), R(0.9) * cpow(err, R(-0.25)));
+        if (h < h_min) status = QSL_LINE_STALL;
+      } else {
+        *c_acc += 1;
+        bool inside = true;
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+          if (face_g<R, true>(dlo, dhi, ic, f, y, dy) > R(0)) inside = false;
+        if (inside) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) y[i] += dy[i];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            R fl = floor(y[a]);
+            int ni = min(max(ic[a] + (int)fl, 0), n[a] - 2);
+            y[a] -= R(ni - ic[a]);
+            ic[a] = ni;
+          }
+          R t1 = hs - muc, t2 = mu + t1;
+          muc = (t2 - mu) - t1;
+          mu = t2;
+          if (capped) status = QSL_LINE_MAXLEN;
+          else h = hs * ((err == R(0)) ? R(5) : fmin(R(5), R(0.9) * cpow(err, R(-0.2))));
+          const R sc = fmin(h, h_max) / hs;
+#pragma unroll
+          for (int q = 1; q <= 3; ++q) {
+            const R c = R(q) * R(1.0 / 3.0) * sc;
+            const R tq[3] = {fma(c, dy[0], y[0]), fma(c, dy[1], y[1]), fma(c, dy[2], y[2])};
+            ck_prefetch_cell<R, V>(fv, n, sy, sz, ic, tq);
+          }
+        } else {
+          phase = 1;
+          yh[0] = dy[0];
+          yh[1] = dy[1];
+          yh[2] = dy[2];
+          lface = chord_face<R, true>(dlo, dhi, ic, y, yh);
+          la = 0;
+          lb = hs;
+          lga = face_gs<R>(dlo, dhi, ic, lface, y, (const R*)nullptr);
+          lgb = face_gs<R>(dlo, dhi, ic, lface, y, yh);
+          lside = 0;
+          lit = 0;
+          lround = 0;
+          lhm = la + (lb - la) * lga / (lga - lgb);
+          if (!(lga < R(0))) {
+            lside = 2;
+            lhm = R(0.5) * lb;
+          }
+        }
+      }
+    } else {
+      *c_land += 1;
+      lit += 1;
+      R gm = face_gs<R>(dlo, dhi, ic, lface, y, dy);
+      R dn = fabs(lface >> 1 == 0 ? dy[0] : (lface >> 1 == 1 ? dy[1] : dy[2]));
+      R gtol = fmax(land_tol, R(4) * eps_of<R>() * dn);
+      if (lside == 2 && lit < 60 && isfinite(gm)) {
+        if (gm < R(0)) {
+          la = lhm;
+          lga = gm;
+          lside = 0;
+          lhm = la + (lb - la) * lga / (lga - lgb);
+        } else {
+          lb = lhm;
+          lgb = gm;
+          lhm = R(0.5) * lhm;
+        }
+      } else if (fabs(gm) <= gtol || lit >= 60 || !isfinite(gm) || !(lb - la > eps_of<R>() * lb)) {
+        R worst = R(-1);
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+          if (f != lface) worst = fmax(worst, face_g<R, true>(dlo, dhi, ic, f, y, dy));
+        if (worst > gtol && lround < 8) {
+          lround += 1;
+          yh[0] = dy[0];
+          yh[1] = dy[1];
+          yh[2] = dy[2];
+          R hi_h = lhm;
+          lface = chord_face<R, true>(dlo, dhi, ic, y, yh);
+          la = 0;
+          lb = hi_h;
+          lga = face_gs<R>(dlo, dhi, ic, lface, y, (const R*)nullptr);
+          lgb = face_gs<R>(dlo, dhi, ic, lface, y, yh);
+          lside = 0;
+          lit = 0;
+          lhm = la + (lb - la) * lga / (lga - lgb);
+          if (!(lga < R(0))) {
+            lside = 2;
+            lhm = R(0.5) * lb;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) y[i] += dy[i];
+          R t1 = lhm - muc, t2 = mu + t1;
+          muc = (t2 - mu) - t1;
+          mu = t2;
+          status = QSL_LINE_OK;
+        }
+      } else {
+        if (gm > R(0)) {
+          lb = lhm;
+          lgb = gm;
+          if (lside == 1) lga *= R(0.5);
+          lside = 1;
+        } else {
+          la = lhm;
+          lga = gm;
+          if (lside == -1) lgb *= R(0.5);
+          lside = -1;
+        }
+        lhm = la + (lb - la) * lga / (lga - lgb);
+      }
+    }
+    if (status != ST_RUNNING) break;
+  }
+  write_end<R, 3, true>(P, E, unit, y, ic, mu, lface, status, steps);
+}
+
+// The Cash-Karp lengths-only kernel: units spread over the warps as in
+// cell_len_kernel, each lane runs its line to the end.
+template <class R>
+__global__ void __maxnreg__(168) ck_len_kernel(const __grid_constant__ TraceParams<R> P) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int64_t total = P.n_units;
+  if (P.n_seeds_dev) {
+    int64_t c = 2 * (*P.n_seeds_dev);
+    total = c < total ? c : total;
+  }
+  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  unsigned long long c_stage = 0, c_acc = 0, c_rej = 0, c_land = 0, c_lines = 0;
+  bool timed_out = false;
+  const unsigned long long t_start = P.timeout_ns ? globaltimer() : 0ull;
+  for (int64_t unit = w + (int64_t)lane * W; unit < total; unit += 32 * W) {
+    c_lines += (unit & 1) == 0;
+    ck_len_line<R>(P, unit, &c_stage, &c_acc, &c_rej, &c_land, &timed_out, t_start);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c_stage += __shfl_down_sync(FULL, c_stage, o);
+    c_acc += __shfl_down_sync(FULL, c_acc, o);
+    c_rej += __shfl_down_sync(FULL, c_rej, o);
+    c_land += __shfl_down_sync(FULL, c_land, o);
+    c_lines += __shfl_down_sync(FULL, c_lines, o);
+  }
+  unsigned any_to = __ballot_sync(FULL, timed_out);
+  if (lane == 0 && P.stats) {
+    atomicAdd(&P.stats->stage_evals, c_stage);
+    atomicAdd(&P.stats->accepted, c_acc);
+    atomicAdd(&P.stats->rejected, c_rej);
+    atomicAdd(&P.stats->landing, c_land);
+    atomicAdd(&P.stats->lines, c_lines);
+    if (any_to) atomicAdd(&P.stats->timeouts, 1ull);
+  }
+  if (lane == 0 && any_to && P.timeout_flag) atomicExch(P.timeout_flag, 1);
+}
+
 // ------------------------------------------------------------ assembly (FP64)
 __device__ __forceinline__ double dot3(const double* a, const double* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
@@ -2838,6 +3233,19 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
     const int bps_len = shape.blocks_per_sm < res_len ? shape.blocks_per_sm : res_len;
     len_kernel = 2 * n_seeds <= (int64_t)32 * shape.warps_per_block * (bps_len > 0 ? bps_len : 1) * sms;
   }
+  // lengths only with the Cash-Karp stepper on a uniform, trilinear, Cartesian
+  // grid in FP32 (the refinement passes' decision traces): the one-lane kernel
+  // with the cell polynomials cached across stages, when every lane of the
+  // resident grid takes at most one line direction
+  bool ck_len = false;
+  if (loc && NC == 3 && sizeof(R) == 4 && cfg.integrator == QSL_RKCK54 && cfg.geom != QSL_GEOM_SPHERICAL &&
+      cfg.interp_order <= 1) {
+    int res_ck = 0;
+    QSL_CHECK_CUDA(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&res_ck, ck_len_kernel<R>, 32 * shape.warps_per_block, 0));
+    const int bps_ck = shape.blocks_per_sm < res_ck ? shape.blocks_per_sm : res_ck;
+    ck_len = 2 * n_seeds <= (int64_t)32 * shape.warps_per_block * (bps_ck > 0 ? bps_ck : 1) * sms;
+  }
   bool coop = false;
   if (use_cell && !len_kernel) {
     if (shape.line_lanes == 3) {
@@ -2852,7 +3260,9 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
   }
   size_t smem = (use_cell && !coop && !len_kernel) ? (size_t)24 * threads * sizeof(R) : 0;
   int resident = 0;
-  if (len_kernel)
+  if (ck_len)
+    QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, ck_len_kernel<R>, threads, 0));
+  else if (len_kernel)
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_len_kernel<R>, threads, 0));
   else if (coop)
     QSL_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cell_coop_kernel<R, NC>, threads, 0));
@@ -2883,7 +3293,10 @@ int launch_trace(const Item<R>& item0, const Item<R>* items_dev, int n_items, bo
   if (blocks < 1) blocks = 1;
   if (ev) QSL_CHECK_CUDA(cudaEventRecord(ev[0], stream));
   if (n_seeds > 0) {
-    if (len_kernel) {
+    if (ck_len) {
+      ck_len_kernel<R><<<blocks, threads, 0, stream>>>(P);
+      qsl::count_launch();
+    } else if (len_kernel) {
       cell_len_kernel<R><<<blocks, threads, 0, stream>>>(P);
       qsl::count_launch();
     } else if (coop) {

@@ -364,14 +364,15 @@ def test_cash_karp_decision_lengths_match_oracle(qsl, oracle_mod, mode, tol):
     assert rep["labels_checked"] > 550
 
 
-@pytest.mark.parametrize("integ,lanes", [(0, 0), (2, 1), (2, 3)])
-def test_watchdog_expires_and_handle_stays_usable(qsl, oracle_mod, integ, lanes):
+@pytest.mark.parametrize("integ,lanes,len_only", [(0, 0, 0), (2, 1, 0), (2, 3, 0), (0, 0, 1), (2, 1, 1)])
+def test_watchdog_expires_and_handle_stays_usable(qsl, oracle_mod, integ, lanes, len_only):
     """The device watchdog (qsl_opts.timeout_s): with a limit of one
     microsecond every tracer kernel stops its lines after its next check (every
     64 loop iterations), lines still running end with QSL_LINE_TIMEOUT,
     qsl_last_stats reports QSL_ETIMEOUT, and the next call on the same field
     handle runs to completion. Nothing waits on anything: the kernels only
-    return early."""
+    return early. Lengths only (len_only): the one-lane Cash-Karp and
+    cell-wise kernels of the refinement passes."""
     ch = inputs.random_charges(4, 2)
     gf = inputs.charge_field(ch, 64, dtype=torch.float32)
     F = _gpu_field(qsl, gf, 0)
@@ -379,7 +380,7 @@ def test_watchdog_expires_and_handle_stays_usable(qsl, oracle_mod, integ, lanes)
     seeds[:, 2] = 0.0
     sd = torch.as_tensor(seeds).cuda()
     o = qsl.qsl_opts_default(tol_abs=1e-9, tol_rel=1e-9, integrator=integ, line_lanes=lanes, retrace_q=0.0,
-                             timeout_s=1e-6)
+                             timeout_s=1e-6, length_only=len_only)
     rec = qsl.lines_to_numpy(qsl.qsl_trace_seeds(F, sd, o))
     with pytest.raises(qsl.QslError) as e:
         qsl.qsl_last_stats()
