@@ -48,9 +48,9 @@ FIELD_SEED = 2
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the
 # current kernels (summaries under profiles/); None until captured. Coarse:
 # one full-size launch, 435.2 MB read + 105.9 MB written. Passes: the average
-# over one refined map's 27 launches, 29.0 MB read + 0.17 MB written.
+# over one refined map's 27 launches, 28.4 MB read + 0.16 MB written.
 TRAFFIC_COARSE_BYTES = 541.0e6
-TRAFFIC_PASS_BYTES = None
+TRAFFIC_PASS_BYTES = 28.5e6
 FLOP_PER_STAGE = {"ck": 246.0, "cell": 227.0}
 # length-only stage evaluation: the cell-wise kernels (trilinear values of 3
 # components 63, position scaling 3, the 3-component share of the stage
@@ -1008,7 +1008,10 @@ def main():
     # trace lengths only with the FLL-jump criterion
     pass_ms = rs["passes_ms"] / max(rs["passes"], 1)
     len_only = rs["deferred_ms"] > 0
-    if len_only and PASS_STEPPER == 0:
+    # the Cash-Karp decision traces read a cell's corners at every stage (the
+    # kernel's cell cache skips repeats): one 8-vertex gather per stage
+    ck_pass = len_only and PASS_STEPPER == 0
+    if ck_pass:
         pass_flop, pass_kernel = FLOP_PER_STAGE_LEN["ck"], "trace_kernel<float,3> (Cash-Karp decision traces, "
     elif len_only:
         pass_flop, pass_kernel = FLOP_PER_STAGE_LEN["cell"], "cell_len_kernel<float> ("
@@ -1025,7 +1028,8 @@ def main():
                    "stage_evals": rs["pass_stage_evals"] // max(rs["passes"], 1), "flop_per_stage": pass_flop,
                    "peak_note": peak_note + "; launches are bound by the latency of their longest line, not by the "
                                             "pipe",
-                   "gather": gather((rs["pass_landings"] + 2 * rs["pass_lines"]) / max(rs["passes"], 1), pass_ms)}
+                   "gather": gather((rs["pass_stage_evals"] if ck_pass else rs["pass_landings"] + 2 * rs["pass_lines"])
+                                    / max(rs["passes"], 1), pass_ms)}
     passes_dominate = rs["passes_ms"] > rs["coarse_ms"]
     step_breakdown = {"device_ms": rs["total_ms"], "coarse_trace_ms": rs["coarse_ms"],
                       "pass_trace_ms": rs["passes_ms"], "deferred_trace_ms": rs["deferred_ms"],
