@@ -113,7 +113,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (fixed tolerance and shape)")
     ap.add_argument("--config", default="refine2d",
-                    choices=["refine2d", "hyperbolic", "volume", "batch64", "learned", "qcrit", "euler"],
+                    choices=["refine2d", "hyperbolic", "volume", "batch64", "learned", "qcrit", "euler", "spherical",
+                             "interp"],
                     help="refine2d: 1024^2 map refined to 4096^2 (default); volume: 512x512x256 Q/FLL/FLEDGE volume "
                          "of an 8-charge field on 384^3")
     ap.add_argument("--shape", default=None,
@@ -285,13 +286,13 @@ def oracle_sample_rate(gf_cpu, seeds, tol, budget_s=15.0, seed=99):
     return done / t_used, done, cores, t_used
 
 
-def oracle_rate_on(gf, seeds, tol, mode=0, budget_s=10.0, seed=99):
+def oracle_rate_on(gf, seeds, tol, mode=0, budget_s=10.0, seed=99, order=1, geometry=0):
     """cpu_baseline of a bench mode: the FP64 oracle on seeded subsamples of
     `seeds` of the field gf (GridField, any device) at tolerance `tol`."""
     from paper_1609_00724_gb300 import inputs
     import oracle
     g = inputs.to_numpy64(gf)
-    F = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=mode)
+    F = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=mode, order=order, geometry=geometry)
     cores = os.cpu_count() or 1
     o = oracle.default_opts(tol_abs=tol, tol_rel=tol, nthreads=cores)
     done, t_used, m, k = 0, 0.0, 64 * cores, seed
@@ -661,6 +662,143 @@ def run_euler(args, qsl, torch, dev, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def map_parity(oracle, Fo, seeds, idx, q, L, fc, cell, lo, hi, opts_ref):
+    """Sampled pixels of a GPU map against the FP64 oracle (tol 1e-11): end
+    faces, Q (Q < 1e6, same faces) and L relative to max(L, one cell)."""
+    ref = oracle.trace_seeds(Fo, seeds[idx], opts_ref)
+    qg, lg = q.cpu().numpy()[idx], L.cpu().numpy()[idx]
+    fg = fc.cpu().numpy().reshape(-1, 2)[idx]
+    same = (fg[:, 0] == ref["face_f"]) & (fg[:, 1] == ref["face_b"])
+    ok = same & np.isfinite(ref["q_perp"]) & (ref["q_perp"] < 1e6)
+    qe = np.abs(qg[ok] / ref["q_perp"][ok] - 1)
+    le = np.abs(lg[same] - ref["L"][same]) / np.maximum(ref["L"][same], cell)
+    return {"n": int(len(idx)), "faces_equal": float(same.mean()), "q_checked": int(ok.sum()),
+            "q_max_rel": float(qe.max()) if qe.size else None, "l_max_rel": float(le.max()) if le.size else None}
+
+
+def map_line(args, qsl, world, metric, workload, name_q, best_ms, N, st, flop, parity, cpu, extra):
+    a = st["stage_evals"] * flop / (best_ms / 1000.0) / 1e12
+    return {"metric": metric, "value": N / (best_ms / 1000.0), "unit": UNIT, "n_gpus": world, "steps": 3,
+            "warmup": 1, "ms_per_step": best_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": dict({"workload": workload}, **extra),
+            "roofline": {"bound": "alu", "achieved": a, "peak": PEAK["fp32"], "unit": "TFLOP/s",
+                         "frac": a / PEAK["fp32"], "traffic": None, "kernel": name_q, "kernel_ms": best_ms,
+                         "stage_evals": st["stage_evals"], "flop_per_stage": flop,
+                         "peak_note": "of measured: FP32 FMA microbenchmark in this run"},
+            "parity": parity, "cpu_baseline": cpu}
+
+
+def run_spherical(args, qsl, torch, dev, rank, world, local):
+    """Spherical geometry (Eq. fl_sph, Eq. dev_sph): a 6-charge potential field
+    on a wedge (longitude and latitude +-0.4 and +-0.3 rad, radius 1 to 1.5;
+    256 x 192 x 128 vertices), the spherical slice at r = 1 (the footpoints on
+    the inner sphere) as a 1024 x 768 map, traced by the Cash-Karp kernel in
+    FP32 with FP64 assembly at tol 1e-7: Q-points/s and errors against the
+    FP64 oracle in spherical geometry on 200 seeded pixels."""
+    import oracle
+    from paper_1609_00724_gb300 import inputs
+    ch = inputs.random_wedge_charges(6, replica_seed(7, rank))
+    n = (256, 192, 128)
+    gf = inputs.spherical_charge_field(ch, n, device=dev, slab=8)
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
+    qsl.qsl_set_geometry(F, qsl.QSL_GEOM_SPHERICAL)
+    nu, nv = 1024, 768
+    N = nu * nv
+    w = inputs.WEDGE
+    c, u, v = (0.0, 0.0, 1.0), (w[0][1] - w[0][0], 0, 0), (0, w[1][1] - w[1][0], 0)
+    q, L = torch.empty(N, device=dev), torch.empty(N, device=dev)
+    fc = torch.empty(2 * N, dtype=torch.uint8, device=dev)
+    tol = args.tol if args.tol is not None else 1e-7
+    o = qsl.qsl_opts_default(tol_abs=tol, tol_rel=tol, integrator=qsl.QSL_RKCK54)
+    best = None
+    for _ in range(4):
+        qsl.qsl_q_map_2d(F, c, u, v, nu, nv, o, q=q, length=L, faces=fc)
+        st = qsl.qsl_last_stats()
+        best = st["kernel_ms"] if best is None else min(best, st["kernel_ms"])
+    torch.cuda.synchronize()
+    parity, cpu = None, None
+    if rank == 0:
+        g = inputs.to_numpy64(gf)
+        Fo = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0, geometry=1)
+        seeds = oracle.plane_seeds(list(c), list(u), list(v), nu, nv)
+        cell = float(min(np.min(np.diff(a)) for a in (g.xc, g.yc, g.zc)))
+        parity = map_parity(oracle, Fo, seeds, inputs.subsample(N, 200, 7), q, L, fc, cell,
+                            [a[0] for a in w], [a[1] for a in w],
+                            oracle.default_opts(tol_abs=1e-11, tol_rel=1e-11, nthreads=os.cpu_count()))
+        if not args.no_cpu_baseline:
+            cpu = oracle_rate_on(gf, seeds, tol, geometry=1)
+    line = map_line(args, qsl, world, "Q-points/s (spherical slice map, Cash-Karp)",
+                    "6-charge potential field on a spherical wedge, 256x192x128 vertices, r = 1 slice %dx%d" % (nu, nv),
+                    "trace_kernel<float,9,spherical>", best, N, st, FLOP_PER_STAGE["ck"] + 16.0, parity, cpu,
+                    {"tol": tol, "integrator": "ck", "geometry": "spherical"})
+    line["kernel_ms_per_map"] = best
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# trilinear value and gradient of 3 components plus |B| (99 FLOP, as in the
+# tangent stage count) against the separable K^3 stencils of the
+# triquadratic (K = 3) and tricubic (K = 4) kernels: per vertex one weight
+# product, 4 value FMAs, 3 gradient weights and 9 gradient FMAs (30 FLOP)
+INTERP_FLOP = {1: 99.0, 2: 27 * 30.0, 3: 64 * 30.0}
+
+
+def run_interp(args, qsl, torch, dev, rank, world, local):
+    """Interpolation orders (Sec. "Interpolation schemes"): the bench field's
+    1024^2 z = 0 map traced by the Cash-Karp kernel with trilinear,
+    triquadratic and tricubic interpolation at tol 1e-7: map time, stage
+    evaluations and each order's errors against the FP64 oracle with the same
+    interpolation on 200 seeded pixels."""
+    import oracle
+    from paper_1609_00724_gb300 import inputs
+    c = args.coarse
+    gf = make_field(replica_seed(FIELD_SEED, rank), dev, args.grid)
+    F = qsl.qsl_load_field(gf.bx, gf.by, gf.bz, gf.xc, gf.yc, gf.zc, qsl.QSL_PAPER_NORMALIZE_FIRST)
+    N = c * c
+    q, L = torch.empty(N, device=dev), torch.empty(N, device=dev)
+    fc = torch.empty(2 * N, dtype=torch.uint8, device=dev)
+    tol = args.tol if args.tol is not None else 1e-7
+    g = inputs.to_numpy64(make_field(replica_seed(FIELD_SEED, rank), "cpu", args.grid)) if rank == 0 else None
+    seeds = oracle.plane_seeds([0, 0, 0], [2, 0, 0], [0, 2, 0], c, c)
+    res = {}
+    for order in (1, 2, 3):
+        o = qsl.qsl_opts_default(tol_abs=tol, tol_rel=tol, integrator=qsl.QSL_RKCK54, interp_order=order)
+        best = None
+        for _ in range(3):
+            qsl.qsl_q_map_2d(F, (0, 0, 0), (2, 0, 0), (0, 2, 0), c, c, o, q=q, length=L, faces=fc)
+            st = qsl.qsl_last_stats()
+            best = st["kernel_ms"] if best is None else min(best, st["kernel_ms"])
+        torch.cuda.synchronize()
+        flop = FLOP_PER_STAGE["ck"] - INTERP_FLOP[1] + INTERP_FLOP[order]
+        a = st["stage_evals"] * flop / (best / 1000.0) / 1e12
+        r = {"map_ms": best, "q_points_per_s": N / (best / 1000.0), "stage_evals": st["stage_evals"],
+             "flop_per_stage": flop, "tflops": a, "frac": a / PEAK["fp32"]}
+        if rank == 0:
+            Fo = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0, order=order)
+            cell = float(min(np.min(np.diff(x)) for x in (g.xc, g.yc, g.zc)))
+            r["parity"] = map_parity(oracle, Fo, seeds, inputs.subsample(N, 200, 7), q, L, fc, cell, (-1, -1, 0),
+                                     (1, 1, 1), oracle.default_opts(tol_abs=1e-11, tol_rel=1e-11,
+                                                                    nthreads=os.cpu_count()))
+            if order == 3 and not args.no_cpu_baseline:
+                r["cpu_baseline"] = oracle_rate_on(gf, seeds, tol, order=3)
+        res[order] = r
+    top = res[3]
+    line = {"metric": "Q-points/s (1024^2 z=0 map, Cash-Karp, tricubic interpolation; other orders alongside)",
+            "value": top["q_points_per_s"], "unit": UNIT, "n_gpus": world, "steps": 3, "warmup": 0,
+            "ms_per_step": top["map_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "4-charge potential field %d^3 FP32, %d^2 z=0 Q map" % (args.grid, c),
+                       "tol": tol, "integrator": "ck"},
+            "roofline": {"bound": "alu", "achieved": top["tflops"], "peak": PEAK["fp32"], "unit": "TFLOP/s",
+                         "frac": top["frac"], "traffic": None, "kernel": "trace_kernel<float,9,higher-order>",
+                         "kernel_ms": top["map_ms"], "stage_evals": top["stage_evals"],
+                         "flop_per_stage": top["flop_per_stage"],
+                         "peak_note": "of measured: FP32 FMA microbenchmark in this run"},
+            "cpu_baseline": top.get("cpu_baseline"), "orders": res}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_qcrit(args, qsl, torch, dev, rank, world, local):
     """Refinement criteria compared (Sec. "Adaptive refinements"): the FLL jump
     (tau 0.05) against a Q threshold (Q > 100), both refining the 1024^2 z = 0
@@ -870,9 +1008,9 @@ def main():
         RUN["shape"] = tuple(int(v) for v in args.shape.split(","))
     if args.hmax:
         RUN["h_max"] = args.hmax
-    if args.config in ("hyperbolic", "volume", "batch64", "learned", "qcrit", "euler"):
+    if args.config != "refine2d":
         {"hyperbolic": run_hyperbolic, "volume": run_volume, "batch64": run_batch, "learned": run_learned,
-         "qcrit": run_qcrit, "euler": run_euler}[args.config](
+         "qcrit": run_qcrit, "euler": run_euler, "spherical": run_spherical, "interp": run_interp}[args.config](
             args, qsl, torch, dev, rank, world, local)
         if world > 1:
             torch.distributed.destroy_process_group()

@@ -173,6 +173,20 @@ int default_shape(const qsl_opts* o, int tangent, int precision, LaunchShape* s)
 }
 
 // ------------------------------------------------------------ field packing
+// 1 / sqrt(s) in FP64 without an FP64 square root or division (the pack is
+// bound by the FP64 rate): Newton-Raphson iteration for the reciprocal square
+// root, x <- x (3 - s x^2) / 2, started from the FP32 estimate; each step
+// doubles the correct bits (about 23 -> 46 -> 92), so two reach FP64
+// precision. s outside the FP32 normal range takes sqrt and a division; 0
+// gives 0.
+__device__ __forceinline__ double rsqrt_fp64(double s) {
+  if (!(s > 1e-30 && s < 1e30)) return s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  double x = (double)rsqrtf((float)s);
+  x = x * fma(-0.5 * s, x * x, 1.5);
+  x = x * fma(-0.5 * s, x * x, 1.5);
+  return x;
+}
+
 template <class T>
 __global__ void pack_kernel(const T* bx, const T* by, const T* bz, size_t n, int raw, float4* v32, double4_32a* v64,
                             int* bad) {
@@ -182,8 +196,9 @@ __global__ void pack_kernel(const T* bx, const T* by, const T* bz, size_t n, int
       atomicExch(bad, 1);
       B[0] = B[1] = B[2] = 0;
     }
-    double m = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
-    const double rm = m > 0 ? 1.0 / m : 0.0;  // one FP64 division per vertex
+    const double s2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const double rm = rsqrt_fp64(s2);  // 1 / |B|, 0 for B = 0
+    const double m = s2 * rm;
     double o[3];
     for (int a = 0; a < 3; ++a) o[a] = raw ? B[a] : B[a] * rm;
     v32[i] = make_float4((float)o[0], (float)o[1], (float)o[2], (float)m);

@@ -169,12 +169,13 @@ __device__ __forceinline__ int ho_taps(int order, int c, R u, int n, int* idx, R
 }
 
 // Value (4 stored components) and local-coordinate gradient of the
-// higher-order interpolant: separable sums over the K^3 stencil vertices.
-template <class R, class S, bool GRAD>
-__device__ void ho_sum(const FieldView<S>& F, const int* ci, const R* uu, R* val4, R (*d)[3]) {
+// higher-order interpolant: separable sums over the K^3 stencil vertices, K
+// known at compile time so that the taps and the sums stay in registers.
+template <class R, class S, bool GRAD, int K>
+__device__ __forceinline__ void ho_sum_k(const FieldView<S>& F, const int* ci, const R* uu, R* val4, R (*d)[3]) {
   int ix[4], iy[4], iz[4];
   R wx[4], wy[4], wz[4], gx[4], gy[4], gz[4];
-  const int K = ho_taps<R>(F.order, ci[0], uu[0], F.n[0], ix, wx, gx);
+  ho_taps<R>(F.order, ci[0], uu[0], F.n[0], ix, wx, gx);
   ho_taps<R>(F.order, ci[1], uu[1], F.n[1], iy, wy, gy);
   ho_taps<R>(F.order, ci[2], uu[2], F.n[2], iz, wz, gz);
   typedef typename V4<S>::type V;
@@ -184,10 +185,13 @@ __device__ void ho_sum(const FieldView<S>& F, const int* ci, const R* uu, R* val
     val4[c] = R(0);
     if (GRAD && c < 3) d[c][0] = d[c][1] = d[c][2] = R(0);
   }
+#pragma unroll 1
   for (int kz = 0; kz < K; ++kz) {
+#pragma unroll
     for (int ky = 0; ky < K; ++ky) {
       const size_t row = (size_t)iz[kz] * sz + (size_t)iy[ky] * sy;
       const R wyz = wy[ky] * wz[kz], gyz = gy[ky] * wz[kz], wgz = wy[ky] * gz[kz];
+#pragma unroll
       for (int kx = 0; kx < K; ++kx) {
         const V q = ldg4(F.v + row + ix[kx]);
         const R f = wx[kx] * wyz;
@@ -206,6 +210,14 @@ __device__ void ho_sum(const FieldView<S>& F, const int* ci, const R* uu, R* val
       }
     }
   }
+}
+
+template <class R, class S, bool GRAD>
+__device__ __forceinline__ void ho_sum(const FieldView<S>& F, const int* ci, const R* uu, R* val4, R (*d)[3]) {
+  if (F.order == 3)
+    ho_sum_k<R, S, GRAD, 4>(F, ci, uu, val4, d);
+  else
+    ho_sum_k<R, S, GRAD, 3>(F, ci, uu, val4, d);
 }
 
 // Interpolated b, grad b and |B| at a point. Storage type S (float/double),

@@ -7,6 +7,8 @@ inputs that the CUDA library and the FP64 oracle both consume:
   a closed form), sampled on a uniform grid;
 * potential fields of sub-photospheric point charges, B = sum_i q_i (x - x_i) /
   |x - x_i|^3, evaluated in FP64 at the grid vertices and then cast;
+* the same charge fields on a spherical wedge (axes longitude, latitude,
+  radius; components along the local unit vectors), for spherical geometry;
 * random seed points.
 
 The paper's own workloads (the Titov-Demoulin flux rope and an NLFFF model of
@@ -96,6 +98,58 @@ def charge_field(charges, n, box=BOX, dtype=torch.float32, device="cpu", slab=16
         for a in range(3):
             out[a][z0:z0 + slab] = acc[a].to(dtype)
     return GridField(out[0], out[1], out[2], xc, yc, zc)
+
+
+WEDGE = ((-0.4, 0.4), (-0.3, 0.3), (1.0, 1.5))  # longitude, latitude (radians), radius
+
+
+def random_wedge_charges(count, seed, wedge=WEDGE, strength=(0.5, 1.5), depth=(0.03, 0.1)):
+    """`count` charges below the wedge's inner sphere, alternating signs,
+    |q| ~ U(strength), depth below r = wedge inner radius ~ U(depth), longitude
+    and latitude ~ U over the inner half of the wedge; Cartesian positions."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ph = rng.uniform(0.5 * wedge[0][0], 0.5 * wedge[0][1], size=count)
+    th = rng.uniform(0.5 * wedge[1][0], 0.5 * wedge[1][1], size=count)
+    rr = wedge[2][0] - rng.uniform(depth[0], depth[1], size=count)
+    mag = rng.uniform(strength[0], strength[1], size=count)
+    sign = np.where(np.arange(count) % 2 == 0, 1.0, -1.0)
+    pos = np.column_stack([rr * np.cos(th) * np.cos(ph), rr * np.cos(th) * np.sin(ph), rr * np.sin(th)])
+    return Charges(pos=pos, q=sign * mag)
+
+
+def spherical_charge_field(charges, n, wedge=WEDGE, dtype=torch.float32, device="cpu", slab=16):
+    """Potential field of Cartesian point charges on a spherical wedge grid:
+    n = (n_phi, n_theta, n_r) uniform vertices over `wedge`; the field at each
+    vertex is evaluated in FP64 and returned as its components along the local
+    unit vectors (phi^, theta^, r^), as torch tensors [n_r, n_theta, n_phi] of
+    `dtype`; the GridField's axes are the longitudes, latitudes and radii."""
+    ax = [np.linspace(lo, hi, k) for (lo, hi), k in zip(wedge, n)]
+    dev = torch.device(device)
+    P = torch.as_tensor(ax[0], dtype=torch.float64, device=dev)
+    T = torch.as_tensor(ax[1], dtype=torch.float64, device=dev)
+    Rs = torch.as_tensor(ax[2], dtype=torch.float64, device=dev)
+    out = [torch.empty((n[2], n[1], n[0]), dtype=dtype, device=dev) for _ in range(3)]
+    pos = torch.as_tensor(charges.pos, dtype=torch.float64, device=dev)
+    q = torch.as_tensor(charges.q, dtype=torch.float64, device=dev)
+    for r0 in range(0, n[2], slab):
+        rr, tt, pp = torch.meshgrid(Rs[r0:r0 + slab], T, P, indexing="ij")
+        ct, st, cp, sp = torch.cos(tt), torch.sin(tt), torch.cos(pp), torch.sin(pp)
+        x, y, z = rr * ct * cp, rr * ct * sp, rr * st
+        acc = [torch.zeros_like(x) for _ in range(3)]
+        for i in range(pos.shape[0]):
+            dx, dy, dz = x - pos[i, 0], y - pos[i, 1], z - pos[i, 2]
+            d2 = dx * dx + dy * dy + dz * dz
+            w = q[i] / (d2 * torch.sqrt(d2))
+            acc[0] += w * dx
+            acc[1] += w * dy
+            acc[2] += w * dz
+        bx, by, bz = acc
+        b_phi = -sp * bx + cp * by
+        b_th = -st * cp * bx - st * sp * by + ct * bz
+        b_r = ct * cp * bx + ct * sp * by + st * bz
+        for a, v in enumerate((b_phi, b_th, b_r)):
+            out[a][r0:r0 + slab] = v.to(dtype)
+    return GridField(out[0], out[1], out[2], ax[0], ax[1], ax[2])
 
 
 def to_numpy64(gf):
