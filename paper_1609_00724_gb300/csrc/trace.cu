@@ -518,6 +518,19 @@ __device__ __forceinline__ R face_g(const R* lo, const R* hi, const int* ic, int
   return (f & 1) ? (dd - r) : (r - dd);
 }
 
+// face_g for a face id known only at run time: the axis components are
+// picked by selects, so that the arrays stay in registers.
+template <class R, bool LOC>
+__device__ __forceinline__ R face_gs(const R* lo, const R* hi, const int* ic, int f, const R* y, const R* d) {
+  const int a = f >> 1;
+  const bool up = (f & 1) != 0;
+  R bound = up ? (a == 0 ? hi[0] : (a == 1 ? hi[1] : hi[2])) : (a == 0 ? lo[0] : (a == 1 ? lo[1] : lo[2]));
+  if (LOC) bound -= R(a == 0 ? ic[0] : (a == 1 ? ic[1] : ic[2]));
+  const R r = bound - (a == 0 ? y[0] : (a == 1 ? y[1] : y[2]));
+  const R dd = d ? (a == 0 ? d[0] : (a == 1 ? d[1] : d[2])) : R(0);
+  return up ? (dd - r) : (r - dd);
+}
+
 // Exit face along the chord y -> y + d: the smallest crossing fraction,
 // lowest face id on ties.
 template <class R, bool LOC>
@@ -844,8 +857,8 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
             lface = chord_face<R, LOC>(E->lo, E->hi, ic, y, yh);
             la = 0;
             lb = hs;
-            lga = face_g<R, LOC>(E->lo, E->hi, ic, lface, y, (const R*)nullptr);
-            lgb = face_g<R, LOC>(E->lo, E->hi, ic, lface, y, yh);
+            lga = face_gs<R, LOC>(E->lo, E->hi, ic, lface, y, (const R*)nullptr);
+            lgb = face_gs<R, LOC>(E->lo, E->hi, ic, lface, y, yh);
             lside = 0;
             lit = 0;
             lround = 0;
@@ -861,7 +874,7 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
       } else {
         c_land += 1;
         lit += 1;
-        R gm = face_g<R, LOC>(E->lo, E->hi, ic, lface, y, dy);
+        R gm = face_gs<R, LOC>(E->lo, E->hi, ic, lface, y, dy);
         // converged when within the landing tolerance or at the resolution of
         // the step increment along the face normal
         R dn = fabs(lface >> 1 == 0 ? dy[0] : (lface >> 1 == 1 ? dy[1] : dy[2]));
@@ -893,8 +906,8 @@ __global__ void __launch_bounds__(256) trace_kernel(const __grid_constant__ Trac
             lface = chord_face<R, LOC>(E->lo, E->hi, ic, y, yh);
             la = 0;
             lb = hi_h;
-            lga = face_g<R, LOC>(E->lo, E->hi, ic, lface, y, (const R*)nullptr);
-            lgb = face_g<R, LOC>(E->lo, E->hi, ic, lface, y, yh);
+            lga = face_gs<R, LOC>(E->lo, E->hi, ic, lface, y, (const R*)nullptr);
+            lgb = face_gs<R, LOC>(E->lo, E->hi, ic, lface, y, yh);
             lside = 0;
             lit = 0;
             lhm = la + (lb - la) * lga / (lga - lgb);
@@ -2641,19 +2654,6 @@ __device__ __forceinline__ void ck_len_step(const V* fv, const int* n, int64_t s
   }
 }
 
-// face_g (local frame) for a face id known only at run time: the axis
-// components are picked by selects, so that the arrays stay in registers.
-template <class R>
-__device__ __forceinline__ R face_gs(const R* lo, const R* hi, const int* ic, int f, const R* y, const R* d) {
-  const int a = f >> 1;
-  const bool up = (f & 1) != 0;
-  R bound = up ? sel3(a, hi[0], hi[1], hi[2]) : sel3(a, lo[0], lo[1], lo[2]);
-  bound -= R(sel3(a, ic[0], ic[1], ic[2]));
-  const R r = bound - sel3(a, y[0], y[1], y[2]);
-  const R dd = d ? sel3(a, d[0], d[1], d[2]) : R(0);
-  return up ? (dd - r) : (r - dd);
-}
-
 __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
@@ -2835,8 +2835,8 @@ __device__ __forceinline__ void ck_len_line(const TraceParams<R>& P, int64_t uni
           lface = chord_face<R, true>(dlo, dhi, ic, y, yh);
           la = 0;
           lb = hs;
-          lga = face_gs<R>(dlo, dhi, ic, lface, y, (const R*)nullptr);
-          lgb = face_gs<R>(dlo, dhi, ic, lface, y, yh);
+          lga = face_gs<R, true>(dlo, dhi, ic, lface, y, (const R*)nullptr);
+          lgb = face_gs<R, true>(dlo, dhi, ic, lface, y, yh);
           lside = 0;
           lit = 0;
           lround = 0;
@@ -2850,7 +2850,7 @@ __device__ __forceinline__ void ck_len_line(const TraceParams<R>& P, int64_t uni
     } else {
       *c_land += 1;
       lit += 1;
-      R gm = face_gs<R>(dlo, dhi, ic, lface, y, dy);
+      R gm = face_gs<R, true>(dlo, dhi, ic, lface, y, dy);
       R dn = fabs(lface >> 1 == 0 ? dy[0] : (lface >> 1 == 1 ? dy[1] : dy[2]));
       R gtol = fmax(land_tol, R(4) * eps_of<R>() * dn);
       if (lside == 2 && lit < 60 && isfinite(gm)) {
@@ -2878,8 +2878,8 @@ __device__ __forceinline__ void ck_len_line(const TraceParams<R>& P, int64_t uni
           lface = chord_face<R, true>(dlo, dhi, ic, y, yh);
           la = 0;
           lb = hi_h;
-          lga = face_gs<R>(dlo, dhi, ic, lface, y, (const R*)nullptr);
-          lgb = face_gs<R>(dlo, dhi, ic, lface, y, yh);
+          lga = face_gs<R, true>(dlo, dhi, ic, lface, y, (const R*)nullptr);
+          lgb = face_gs<R, true>(dlo, dhi, ic, lface, y, yh);
           lside = 0;
           lit = 0;
           lhm = la + (lb - la) * lga / (lga - lgb);
