@@ -173,20 +173,6 @@ int default_shape(const qsl_opts* o, int tangent, int precision, LaunchShape* s)
 }
 
 // ------------------------------------------------------------ field packing
-// 1 / sqrt(s) in FP64 without an FP64 square root or division (the pack is
-// bound by the FP64 rate): Newton-Raphson iteration for the reciprocal square
-// root, x <- x (3 - s x^2) / 2, started from the FP32 estimate; each step
-// doubles the correct bits (about 23 -> 46 -> 92), so two reach FP64
-// precision. s outside the FP32 normal range takes sqrt and a division; 0
-// gives 0.
-__device__ __forceinline__ double rsqrt_fp64(double s) {
-  if (!(s > 1e-30 && s < 1e30)) return s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-  double x = (double)rsqrtf((float)s);
-  x = x * fma(-0.5 * s, x * x, 1.5);
-  x = x * fma(-0.5 * s, x * x, 1.5);
-  return x;
-}
-
 template <class T>
 __global__ void pack_kernel(const T* bx, const T* by, const T* bz, size_t n, int raw, float4* v32, double4_32a* v64,
                             int* bad) {

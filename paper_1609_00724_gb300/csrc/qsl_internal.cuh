@@ -62,6 +62,30 @@ __host__ __device__ __forceinline__ void sph_scale(R theta, R r, R* m) {
   m[2] = R(1);
 }
 
+// FP64 reciprocal square root and reciprocal without an FP64 square root or
+// division (GB300's FP64 rate makes those the cost of the packing and the
+// assembly kernels): Newton-Raphson iteration, x <- x (3 - s x^2) / 2 for
+// 1 / sqrt(s) and x <- x (2 - s x) for 1 / s, started from the FP32 estimate;
+// each step doubles the correct bits (about 23 -> 46 -> 92), so two reach FP64
+// precision (within an ulp or two of the rounded result). Arguments outside
+// the FP32 normal range take the FP64 operations; rsqrt_fp64(0) is 0.
+__device__ __forceinline__ double rsqrt_fp64(double s) {
+  if (!(s > 1e-30 && s < 1e30)) return s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  double x = (double)rsqrtf((float)s);
+  x = x * fma(-0.5 * s, x * x, 1.5);
+  x = x * fma(-0.5 * s, x * x, 1.5);
+  return x;
+}
+
+__device__ __forceinline__ double rcp_fp64(double s) {
+  const double a = fabs(s);
+  if (!(a > 1e-30 && a < 1e30)) return 1.0 / s;
+  double x = (double)__frcp_rn((float)s);
+  x = x * fma(-s, x, 2.0);
+  x = x * fma(-s, x, 2.0);
+  return x;
+}
+
 }  // namespace qsl
 
 struct qsl_field {

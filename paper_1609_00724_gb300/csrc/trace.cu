@@ -2966,6 +2966,35 @@ struct EndTerms {
   bool foot_ok;
 };
 
+// B at a point for the assembly (|B| and the direction the deviations are
+// projected against). FP32 field on a uniform grid: the cell and the in-cell
+// fractions are found in FP64 (exact), the interpolation itself runs in FP32
+// on the FP32 vertex values (relative error about 1e-7) and is widened; the
+// deviation norms, the determinant and Q are then assembled in FP64. FP64
+// fields and rectilinear grids interpolate in FP64.
+template <class S>
+__device__ __forceinline__ void interp_end(const FieldView<S>& F, const double* x, Interp<double>& I) {
+  if (sizeof(S) == 4 && F.uniform) {
+    int ic[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double fa = (x[a] - (double)F.org[a]) * (double)F.inv_h[a];
+      const double fl = floor(fmin(fmax(fa, 0.0), (double)(F.n[a] - 2)));
+      ic[a] = (int)fl;
+      f[a] = (float)(fa - fl);
+    }
+    Interp<float> J;
+    interp<float, S, false, true, true, true>(F, f[0], f[1], f[2], J, ic);
+    I.b[0] = J.b[0];
+    I.b[1] = J.b[1];
+    I.b[2] = J.b[2];
+    I.m = J.m;
+  } else {
+    interp<double, S, false, true>(F, x[0], x[1], x[2], I);
+  }
+}
+
 template <class S>
 __device__ void end_terms(const FieldView<S>& F, const double* x, const double* d1_in, const double* d2_in,
                           int face, bool have_face, EndTerms& r) {
@@ -2976,10 +3005,10 @@ __device__ void end_terms(const FieldView<S>& F, const double* x, const double* 
   const double d1[3] = {d1_in[0] * sf[0], d1_in[1] * sf[1], d1_in[2] * sf[2]};
   const double d2[3] = {d2_in[0] * sf[0], d2_in[1] * sf[1], d2_in[2] * sf[2]};
   Interp<double> I;
-  interp<double, S, false, true>(F, x[0], x[1], x[2], I);
+  interp_end<S>(F, x, I);
   r.bmag = I.m;
-  double m = sqrt(dot3(I.b, I.b));
-  const double rm = 1.0 / m;  // one FP64 division per end
+  const double b2 = dot3(I.b, I.b);
+  const double rm = b2 > 0.0 ? rsqrt_fp64(b2) : 1.0 / sqrt(b2);  // a null end gives NaN directions, as 1 / 0
   double u[3] = {I.b[0] * rm, I.b[1] * rm, I.b[2] * rm};
   // Sec. "Squashing factor calculation": dx_perp = dx - b (b.dx), b normalised
   double ud1 = dot3(u, d1), ud2 = dot3(u, d2);
@@ -2992,14 +3021,15 @@ __device__ void end_terms(const FieldView<S>& F, const double* x, const double* 
   r.B = dot3(bp, bp);
   r.C = dot3(ap, bp);
   double cr[3] = {ap[1] * bp[2] - ap[2] * bp[1], ap[2] * bp[0] - ap[0] * bp[2], ap[0] * bp[1] - ap[1] * bp[0]};
-  r.cross = sqrt(dot3(cr, cr));
+  const double c2 = dot3(cr, cr);
+  r.cross = c2 * rsqrt_fp64(c2);
   r.foot_ok = false;
   r.Af = r.Bf = r.Cf = r.bn = __longlong_as_double(0x7ff8000000000000ll);
   if (have_face && face != NO_FACE) {
     int a = face >> 1;
     if (u[a] != 0.0) {
       double af[3], bf[3];
-      const double ru = 1.0 / u[a];
+      const double ru = rcp_fp64(u[a]);
       const double s1 = d1[a] * ru, s2 = d2[a] * ru;
       for (int i = 0; i < 3; ++i) {
         af[i] = d1[i] - u[i] * s1;
@@ -3039,7 +3069,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(const __grid_constant__ A
     if (sf != QSL_LINE_OUTSIDE) L = (double)ef.mu + (double)eb.mu;
     if (sf != QSL_LINE_OUTSIDE && sf != QSL_LINE_NULL) {
       Interp<double> I0;
-      interp<double, R, false, true>(FV, x0[0], x0[1], x0[2], I0);
+      interp_end<R>(FV, x0, I0);
       b0 = I0.m;
     }
     bool okf = (sf == QSL_LINE_OK || sf == QSL_LINE_MAXLEN);
@@ -3061,9 +3091,10 @@ __global__ void __launch_bounds__(128) assemble_kernel(const __grid_constant__ A
       bf = tf.bmag;
       bb = tb.bmag;
       double br = tf.A * tb.B + tb.A * tf.B - 2.0 * tb.C * tf.C;
-      const double rb0 = 1.0 / b0, rb02 = rb0 * rb0;
+      const double rb0 = rcp_fp64(b0), rb02 = rb0 * rb0;
       q_perp = bf * bb * rb02 * br;  // Eq. finalQ
-      q_det = br / sqrt((tf.A * tf.B - tf.C * tf.C) * (tb.A * tb.B - tb.C * tb.C));
+      const double gd = (tf.A * tf.B - tf.C * tf.C) * (tb.A * tb.B - tb.C * tb.C);
+      q_det = gd > 0.0 ? br * rsqrt_fp64(gd) : br / sqrt(gd);
       ff = bf * rb0 * tf.cross - 1.0;
       fb = bb * rb0 * tb.cross - 1.0;
       if (tf.foot_ok && tb.foot_ok) {
