@@ -475,6 +475,14 @@ int qsl_set_geometry(qsl_field* field, int geometry);
  * respect to nothing: blocks still in use by queued work stay allocated. */
 int qsl_trim_pool(void);
 
+/* Check of the library's FP64 Newton-Raphson reciprocal square root and
+ * reciprocal (used by the field pack and the Q assembly; no paper
+ * counterpart) against CUDA's 1 / sqrt(x) and 1 / x: x are n host values;
+ * max_ulp_out (host, 2 doubles) receives the largest difference of each, in
+ * units in the last place of CUDA's result, over the finite positive inputs.
+ * Synchronous (default stream). QSL_EINVAL for n < 1 or NULL pointers. */
+int qsl_check_fp64_newton(const double* x, int64_t n, double* max_ulp_out);
+
 /* Kernels of this library launched by this process since the library was
  * loaded (all threads). Radix sorts and scans inside qsl_refine run CUB
  * kernels, which are not counted. */

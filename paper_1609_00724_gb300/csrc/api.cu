@@ -173,6 +173,21 @@ int default_shape(const qsl_opts* o, int tangent, int precision, LaunchShape* s)
 }
 
 // ------------------------------------------------------------ field packing
+// Largest differences of rsqrt_fp64 / rcp_fp64 from 1 / sqrt(x) and 1 / x, in
+// ulps of the latter, over the finite positive inputs (bit patterns of
+// non-negative doubles order like their values, so atomicMax on them works).
+__global__ void newton_check_kernel(const double* x, int64_t n, double* max_ulp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    if (!(v > 0.0) || !isfinite(v)) continue;
+    const double r1 = 1.0 / sqrt(v), r2 = 1.0 / v;
+    const double u1 = fabs(rsqrt_fp64(v) - r1) / (nextafter(r1, INFINITY) - r1);
+    const double u2 = fabs(rcp_fp64(v) - r2) / (nextafter(r2, INFINITY) - r2);
+    atomicMax((unsigned long long*)&max_ulp[0], (unsigned long long)__double_as_longlong(u1));
+    atomicMax((unsigned long long*)&max_ulp[1], (unsigned long long)__double_as_longlong(u2));
+  }
+}
+
 template <class T>
 __global__ void pack_kernel(const T* bx, const T* by, const T* bz, size_t n, int raw, float4* v32, double4_32a* v64,
                             int* bad) {
@@ -567,6 +582,24 @@ int qsl_set_geometry(qsl_field* f, int geometry) {
   f->cell = fmin(fmin(f->glo[2] * cmin * f->h[0], f->glo[2] * f->h[1]), f->h[2]);
   f->cell_q = hmin;
   f->geom = QSL_GEOM_SPHERICAL;
+  return QSL_OK;
+}
+
+int qsl_check_fp64_newton(const double* x, int64_t n, double* max_ulp_out) {
+  if (n < 1 || !x || !max_ulp_out) QSL_FAIL(QSL_EINVAL, "need n >= 1 and non-NULL pointers");
+  double *dx = nullptr, *dm = nullptr;
+  QSL_CHECK_CUDA(cudaMalloc((void**)&dx, sizeof(double) * n));
+  QSL_CHECK_CUDA(cudaMalloc((void**)&dm, sizeof(double) * 2));
+  QSL_CHECK_CUDA(cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice));
+  QSL_CHECK_CUDA(cudaMemset(dm, 0, sizeof(double) * 2));
+  const int blocks = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  newton_check_kernel<<<blocks, 256>>>(dx, n, dm);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(max_ulp_out, dm, sizeof(double) * 2, cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(dm);
+  if (e != cudaSuccess) QSL_FAIL(QSL_ECUDA, "%s", cudaGetErrorString(e));
   return QSL_OK;
 }
 

@@ -114,6 +114,7 @@ def lib():
     L = C.CDLL(LIB_PATH)
     vp, i32, i64, dp = C.c_void_p, C.c_int, C.c_int64, C.c_void_p
     L.qsl_last_error.restype = C.c_char_p
+    L.qsl_check_fp64_newton.argtypes = [vp, i64, vp]
     L.qsl_opts_default.argtypes = [C.POINTER(qsl_opts)]
     L.qsl_load_field.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, dp, dp, dp, i32, vp, C.POINTER(vp)]
     L.qsl_free_field.argtypes = [vp]
@@ -463,6 +464,15 @@ def qsl_set_geometry(field, geometry):
     """Sets the field's geometry (QSL_GEOM_CARTESIAN or QSL_GEOM_SPHERICAL)."""
     _check(lib().qsl_set_geometry(field.handle, int(geometry)))
     return field
+
+
+def qsl_check_fp64_newton(x):
+    """Largest differences (ulps) of the library's FP64 Newton-Raphson
+    reciprocal square root and reciprocal from CUDA's, over host values x."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(2)
+    _check(lib().qsl_check_fp64_newton(_ptr(x), x.size, _ptr(out)))
+    return {"rsqrt_ulp": float(out[0]), "rcp_ulp": float(out[1])}
 
 
 def qsl_trim_pool():

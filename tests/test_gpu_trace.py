@@ -399,3 +399,17 @@ def test_watchdog_expires_and_handle_stays_usable(qsl, oracle_mod, integ, lanes,
     assert done.sum() > 0
     assert np.array_equal(rec["face_f"][done], rec2["face_f"][done])
     assert np.allclose(rec["length"][done], rec2["length"][done], rtol=1e-6)
+
+
+def test_fp64_newton_reciprocals_match_cuda(qsl):
+    """The FP64 Newton-Raphson reciprocal square root and reciprocal of the
+    field pack and the Q assembly against CUDA's 1 / sqrt(x) and 1 / x, over
+    values log-uniform on 1e-35..1e35 (both sides of the FP32 range, where the
+    FP64 operations take over) and powers of two and their neighbours."""
+    rng = np.random.default_rng(5)
+    x = 10.0 ** rng.uniform(-35, 35, 200000)
+    p2 = 2.0 ** np.arange(-99, 100)
+    x = np.concatenate([x, p2, np.nextafter(p2, 0), np.nextafter(p2, np.inf), [1.0, 3.0, 0.5]])
+    r = qsl.qsl_check_fp64_newton(x)
+    print("max ulps:", r)
+    assert r["rsqrt_ulp"] <= 2.0 and r["rcp_ulp"] <= 2.0
