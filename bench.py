@@ -859,10 +859,11 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
     128 volume refined two orders (1024 x 1024 x 512 effective). Compared:
     wall time of the plain criterion with FP64 everywhere (and with FP32
     tracing) against the learned proposal (CNN on the coarse z-slices, mask
-    dilated by one cell, every effective cell of a proposed coarse cell traced
-    in one launch) with FP32 tracing and the plain criterion as fallback, run
-    for a few iterations and to convergence; recall of the plain FP64 run's
-    QSL pixels."""
+    dilated by one cell, the effective cells of a proposed coarse cell traced
+    in one launch: all of them, or every other one per axis, which is one per
+    output cell) with FP32 tracing and the plain criterion as fallback, run for
+    a few iterations and to convergence; recall of the plain FP64 run's QSL
+    pixels."""
     from paper_1609_00724_gb300 import inputs, learned
     n_vol = int(os.environ.get("QSL_LEARNED_VOLUMES", "160"))
     fb_iters = int(os.environ.get("QSL_LEARNED_FALLBACK_ITERS", "2"))
@@ -918,17 +919,18 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
 
     ql_keep = {}
 
-    def learned_run(max_iters):
+    def learned_run(max_iters, stride=1):
         s2 = learned.Samples(cap, dev)
 
         def go():
             s2.refine(F, learned.volume_spec(coarse, 2, TAU, max_iters=0), o32)
             L, Q, _ = learned.coarse_grids(s2, 3, spec.max_order, 2, coarse[::-1])
-            budget = max(0, int(0.9 * (cap - s2.count) / 64))
+            budget = max(0, int(0.9 * (cap - s2.count) / (4 // stride) ** 3))
             mask = learned.propose(net, learned.features_slices(L, Q), thr, dilate=True)
             if int(mask.sum().item()) > budget:
                 mask = learned.propose(net, learned.features_slices(L, Q), thr, budget=budget // 27, dilate=True)
-            r = s2.refine(F, learned.volume_spec(coarse, 2, TAU, proposal=mask, max_iters=max_iters), o32)
+            r = s2.refine(F, learned.volume_spec(coarse, 2, TAU, proposal=mask, max_iters=max_iters,
+                                                 proposal_stride=stride), o32)
             return r, int(mask.sum().item())
 
         dt, ((n_l, it_l, tr_l, rc_l), ncells) = timed(go)
@@ -936,18 +938,21 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
         pos = torch.searchsorted(lk, plain_keys).clamp(max=n_l - 1)
         sample_recall = float((lk[pos] == plain_keys).float().mean().item())
         ql = learned.converted_q(s2, 3, spec.max_order, ext, out_order)
-        ql_keep["b" if max_iters == fb_iters else "f"] = ql
+        ql_keep[(max_iters, stride)] = ql
         qsl_pix = torch.nan_to_num(ql.reshape(-1)[qsl_cells], nan=0.0) >= 100.0
         old_pix = torch.nan_to_num(qp, nan=0.0) >= 100.0
         old_recall = float(((torch.nan_to_num(ql, nan=0.0) >= 100.0) & old_pix).sum().item() /
                            max(1, int(old_pix.sum().item())))
         return {"seconds": dt, "samples": n_l, "iters": it_l, "rc": rc_l, "proposed_cells": ncells,
                 "proposed_frac": ncells / float(np.prod(coarse)), "fallback_max_iters": max_iters,
+                "proposal_stride": stride,
                 "qsl_pixel_recall": float(qsl_pix.float().mean().item()), "sample_recall": sample_recall,
                 "converted_qsl_recall": old_recall}
 
-    res["learned_fp32_bounded"] = learned_run(fb_iters)
-    res["learned_fp32_full"] = learned_run(64)
+    runs = {"learned_fp32_bounded": (fb_iters, 1), "learned_fp32_full": (64, 1),
+            "learned_fp32_stride2_bounded": (fb_iters, 2), "learned_fp32_stride2_full": (64, 2)}
+    for k, (mi, stv) in runs.items():
+        res[k] = learned_run(mi, stv)
     dense = None
     if os.environ.get("QSL_LEARNED_DENSE") == "1":
         # a dense map of every effective cell (FP32), max-pooled to the output
@@ -960,11 +965,11 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
         truth = torch.nn.functional.max_pool3d(qd, 2).reshape(-1) >= 100.0
         del qd
         dense = {"seconds": dt_d, "qsl_cells": int(truth.sum().item())}
-        for k, qmap in (("plain_fp64", qp), ("learned_fp32_bounded", ql_keep["b"]), ("learned_fp32_full", ql_keep["f"])):
+        for k, qmap in [("plain_fp64", qp)] + [(k, ql_keep[v]) for k, v in runs.items()]:
             got = torch.nan_to_num(qmap, nan=0.0).reshape(-1) >= 100.0
             tp = int((got & truth).sum().item())
             dense[k] = {"recall": tp / max(1, dense["qsl_cells"]), "precision": tp / max(1, int(got.sum().item()))}
-    meets = [k for k in ("learned_fp32_bounded", "learned_fp32_full") if res[k]["qsl_pixel_recall"] >= 0.99]
+    meets = [k for k in runs if res[k]["qsl_pixel_recall"] >= 0.99]
     best = min(meets, key=lambda k: res[k]["seconds"]) if meets else "learned_fp32_full"
     line = {"metric": "refined-map wall time: learned proposal + FP32 vs plain FP64 at >= 99% QSL-pixel recall",
             "value": res["plain_fp64"]["seconds"] / res[best]["seconds"], "unit": "x speed-up",

@@ -214,13 +214,17 @@ typedef struct qsl_refine_spec {
   int32_t extent[3];     /* effective lattice extent per axis, <= 2^p, multiple of 2^(p-p0); 0: 2^p */
   int32_t shift;         /* 1: shifted-curve pass after each refinement pass                */
   int32_t out_order;     /* converter output order (<= p); 0: p                             */
-  int32_t pad;
+  int32_t proposal_stride; /* with a proposal: the effective cells of a proposed coarse cell
+                              that are sampled, every stride-th per axis at offset stride / 2
+                              (stride 2 with out_order = p - 1: one sample per output cell);
+                              0 or 1: every effective cell; a power of two <= 2^(p - p0)  */
   double center[3], u[3], v[3]; /* planar slice, as in qsl_q_map_2d                     */
   double lo[3], hi[3];          /* volume box                                             */
   double tau;                   /* refine a pair when |L_i - L_i+1| > tau; tau < 0: every pair */
   const uint8_t* proposal;      /* optional (device or host per `mem`): one byte per coarse
-                                   cell, x fastest; nonzero cells are sampled at every
-                                   effective cell before the first iteration          */
+                                   cell, x fastest; nonzero cells are sampled (at the
+                                   effective cells proposal_stride selects) before the
+                                   first iteration                                     */
   int32_t criterion;            /* QSL_REFINE_FLL_JUMP (0): |L_i - L_i+1| > tau (the paper's);
                                    QSL_REFINE_Q_THRESHOLD (1): a pair is refined when either
                                    sample's Q (opts.q_form) is finite and > q_threshold, the

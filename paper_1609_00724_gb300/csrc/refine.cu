@@ -121,21 +121,23 @@ __global__ void coarse_keys_kernel(int64_t n, int nd, int bits, int R, int nc0, 
   }
 }
 
-// Proposal: every effective cell of the flagged coarse cells that is not
-// already a sample (binary search in the sorted keys). One thread per
-// (flagged cell, sub-cell).
+// Proposal: the effective cells of the flagged coarse cells at stride `st`
+// (offset st / 2) that are not already samples (binary search in the sorted
+// keys). One thread per (flagged cell, sub-cell).
 __global__ void proposal_keys_kernel(const int64_t* __restrict__ cells, const int64_t* ncells_dev, int nd, int bits,
-                                     int R, int nc0, int nc1, const uint64_t* __restrict__ have, int64_t n_have,
-                                     uint64_t* keys, int64_t* count) {
+                                     int R, int st, int nc0, int nc1, const uint64_t* __restrict__ have,
+                                     int64_t n_have, uint64_t* keys, int64_t* count) {
   int64_t ncells = *ncells_dev;
+  const int Rs = R / st;
   int64_t per = 1;
-  for (int a = 0; a < nd; ++a) per *= R;
+  for (int a = 0; a < nd; ++a) per *= Rs;
   int64_t total = ncells * per;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     int64_t cell = cells[t / per], sub = t % per;
     int64_t i = cell % nc0, rem = cell / nc0;
     int64_t j = rem % nc1, k = rem / nc1;
-    int64_t s0 = sub % R, s1 = (sub / R) % R, s2 = nd == 3 ? sub / (R * R) : 0;
+    int64_t s0 = (sub % Rs) * st + st / 2, s1 = ((sub / Rs) % Rs) * st + st / 2,
+            s2 = nd == 3 ? (sub / (Rs * Rs)) * st + st / 2 : 0;
     uint32_t c[3] = {(uint32_t)(i * R + s0), (uint32_t)(j * R + s1), (uint32_t)(k * R + s2)};
     uint64_t key = hilbert_key_dev(c, nd, bits);
     int64_t lo = 0, hi = n_have;  // already a sample?
@@ -874,8 +876,9 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
     QSL_CHECK_CUDA(cudaMemcpyAsync(cnt_h, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     QSL_CHECK_CUDA(cudaStreamSynchronize(s));
     int64_t ncells = *cnt_h;
+    const int pst = sp->proposal_stride > 1 ? sp->proposal_stride : 1;
     int64_t per = 1;
-    for (int a = 0; a < nd; ++a) per *= R;
+    for (int a = 0; a < nd; ++a) per *= R / pst;
     int64_t want = ncells * per;
     if (want > cap - n) {
       set_error("capacity too small for the proposal (up to %lld more samples)", (long long)want);
@@ -886,7 +889,7 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
       if ((rc = sc.alloc(&ncd, 1))) return rc;
       QSL_CHECK_CUDA(cudaMemcpyAsync(ncd, cnt, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
       QSL_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t), s));
-      proposal_keys_kernel<<<grid_for(want), 256, 0, s>>>(cells, ncd, nd, p, R, nc[0], nc[1], cur.key, n,
+      proposal_keys_kernel<<<grid_for(want), 256, 0, s>>>(cells, ncd, nd, p, R, pst, nc[0], nc[1], cur.key, n,
                                                             cur.key + n, cnt);
       qsl::count_launch();
       QSL_CHECK_CUDA(cudaGetLastError());
@@ -1199,6 +1202,14 @@ int qsl_refine(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o,
   if (sp->criterion != QSL_REFINE_FLL_JUMP && sp->criterion != QSL_REFINE_Q_THRESHOLD) {
     set_error("criterion must be QSL_REFINE_FLL_JUMP or QSL_REFINE_Q_THRESHOLD");
     return QSL_EINVAL;
+  }
+  {
+    const int pst = sp->proposal_stride;
+    const int Rr = 1 << (sp->max_order - sp->coarse_order);
+    if (pst < 0 || pst > Rr || (pst > 1 && (pst & (pst - 1)))) {
+      set_error("proposal_stride must be 0, 1 or a power of two <= 2^(max_order - coarse_order)");
+      return QSL_EINVAL;
+    }
   }
   if (sp->pass_stepper < QSL_PASS_CASH_KARP || sp->pass_stepper > QSL_PASS_FULL ||
       !(sp->pass_h_max >= 0.0 && sp->pass_h_max < 1e6)) {

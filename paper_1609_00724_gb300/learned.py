@@ -40,18 +40,20 @@ def init_params(seed):
     return p
 
 
-def plane_spec(coarse, levels, tau, shift=1, max_iters=64, proposal=None):
+def plane_spec(coarse, levels, tau, shift=1, max_iters=64, proposal=None, proposal_stride=1):
     p0 = int(round(math.log2(coarse)))
     return qsl.refine_spec(ndim=2, coarse_order=p0, max_order=p0 + levels, center=(0, 0, 0), u=(2, 0, 0),
-                           v=(0, 2, 0), tau=tau, shift=shift, max_iters=max_iters, proposal=proposal)
+                           v=(0, 2, 0), tau=tau, shift=shift, max_iters=max_iters, proposal=proposal,
+                           proposal_stride=proposal_stride)
 
 
-def volume_spec(coarse_xyz, levels, tau, lo=(-1, -1, 0), hi=(1, 1, 1), max_iters=64, proposal=None):
+def volume_spec(coarse_xyz, levels, tau, lo=(-1, -1, 0), hi=(1, 1, 1), max_iters=64, proposal=None,
+                proposal_stride=1):
     R = 1 << levels
     p0 = int(round(math.log2(max(coarse_xyz))))
     ext = [c * R for c in coarse_xyz]
     return qsl.refine_spec(ndim=3, coarse_order=p0, max_order=p0 + levels, extent=ext, lo=lo, hi=hi, tau=tau,
-                           max_iters=max_iters, proposal=proposal)
+                           max_iters=max_iters, proposal=proposal, proposal_stride=proposal_stride)
 
 
 class Samples:

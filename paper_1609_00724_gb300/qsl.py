@@ -68,7 +68,8 @@ class qsl_refine_stats(C.Structure):
 class qsl_refine_spec(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("coarse_order", C.c_int32), ("max_order", C.c_int32),
                 ("max_iters", C.c_int32), ("extent", C.c_int32 * 3), ("shift", C.c_int32),
-                ("out_order", C.c_int32), ("pad", C.c_int32), ("center", C.c_double * 3), ("u", C.c_double * 3),
+                ("out_order", C.c_int32), ("proposal_stride", C.c_int32), ("center", C.c_double * 3),
+                ("u", C.c_double * 3),
                 ("v", C.c_double * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("tau", C.c_double),
                 ("proposal", C.c_void_p), ("criterion", C.c_int32), ("pass_stepper", C.c_int32),
                 ("q_threshold", C.c_double), ("pass_h_max", C.c_double)]

@@ -325,10 +325,12 @@ def test_refine_sample_set_matches_oracle(qsl, oracle_mod, ndim, integrator, ste
     assert np.array_equal(lg.cpu().numpy()[flat], b["L"].cpu().numpy()[:n])
 
 
-def test_refine_proposal_traces_every_cell_of_flagged_coarse_cells(qsl, oracle_mod):
+@pytest.mark.parametrize("stride", [1, 2])
+def test_refine_proposal_traces_every_cell_of_flagged_coarse_cells(qsl, oracle_mod, stride):
     """Proposal step (one byte per coarse cell, x fastest) with no refinement
-    iteration after it: the sample set is the coarse samples plus every
-    effective cell of the flagged coarse cells, key for key (keys from the
+    iteration after it: the sample set is the coarse samples plus the
+    effective cells of the flagged coarse cells at the proposal stride (every
+    cell; every other cell per axis at offset 1), key for key (keys from the
     oracle's Hilbert curve), and the lines traced there match the oracle."""
     from gpu_helpers import compare_lines
     F, Fo = _fields(qsl, oracle_mod, n=40, seed=3)
@@ -339,7 +341,7 @@ def test_refine_proposal_traces_every_cell_of_flagged_coarse_cells(qsl, oracle_m
     kw = dict(ndim=2, coarse_order=p0, max_order=p, center=(0, 0, 0), u=(2, 0, 0), v=(0, 2, 0), tau=0.05,
               max_iters=0)
     mask_dev = torch.as_tensor(mask).cuda()
-    sp = qsl.refine_spec(proposal=mask_dev, **kw)
+    sp = qsl.refine_spec(proposal=mask_dev, proposal_stride=stride, **kw)
     cap = (nc * R) ** 2
     b = _alloc(cap)
     o = qsl.qsl_opts_default(tol_abs=GPU_TOL, tol_rel=GPU_TOL)
@@ -349,12 +351,11 @@ def test_refine_proposal_traces_every_cell_of_flagged_coarse_cells(qsl, oracle_m
     want = set()
     for j in range(nc):
         for i in range(nc):
+            want.add(oracle_mod.hilbert_key((i * R + R // 2, j * R + R // 2), 2, p))
             if mask[i + nc * j]:
-                for bb in range(R):
-                    for aa in range(R):
+                for bb in range(stride // 2, R, stride):
+                    for aa in range(stride // 2, R, stride):
                         want.add(oracle_mod.hilbert_key((i * R + aa, j * R + bb), 2, p))
-            else:
-                want.add(oracle_mod.hilbert_key((i * R + R // 2, j * R + R // 2), 2, p))
     assert n == len(want) and list(keys) == sorted(want)
     # the lines: a seeded sample of the samples against the oracle
     idx = np.sort(np.random.default_rng(12).choice(n, 80, replace=False))
