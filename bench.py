@@ -263,6 +263,45 @@ def alloc(torch, coarse, device):
             "sg": torch.empty((eff, eff), dtype=torch.float32, device=device), "eff": eff}
 
 
+WINDOW = 32  # coarse cells per side of one refinement window of the oracle baseline
+
+
+def oracle_window_refine(oracle, Fo, tol, coarse, rng, nthreads):
+    """The oracle's whole refinement (coarse pass, FLL-jump passes with their
+    decision traces, tangent-space values) on one window of WINDOW x WINDOW
+    coarse cells of the z = 0 map, at a seeded position, with the map's cell
+    sizes (coarse spacing 2 / coarse, refined 2^(P - P0) times). Returns the
+    samples it produced and the seconds it took."""
+    nw = coarse // WINDOW
+    i0, j0 = (int(v) for v in rng.integers(0, nw, size=2))
+    w = 2.0 * WINDOW / coarse
+    cx, cy = -1.0 + (i0 + 0.5) * w, -1.0 + (j0 + 0.5) * w
+    p0 = int(np.log2(WINDOW))
+    sp = oracle.refine_spec(ndim=2, coarse_order=p0, max_order=p0 + (P - P0), center=(cx, cy, 0.0), u=(w, 0, 0),
+                            v=(0, w, 0), tau=TAU, shift=1, max_iters=64, pass_h_max=PASS_H_MAX)
+    o = oracle.default_opts(tol_abs=tol, tol_rel=tol, nthreads=nthreads)
+    t0 = time.perf_counter()
+    r = oracle.refine(Fo, sp, o)
+    return len(r["key"]), time.perf_counter() - t0
+
+
+def oracle_refine_rate(gf_cpu, tol, coarse, budget_s=12.0, seed=99):
+    """cpu_baseline of the refined map: the oracle's own refinement on seeded
+    windows of the map (no input from the GPU run) until about budget_s
+    seconds. Returns (samples/s, samples, windows, cores, seconds)."""
+    import oracle
+    from paper_1609_00724_gb300 import inputs
+    g = inputs.to_numpy64(gf_cpu)
+    Fo = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
+    cores = os.cpu_count() or 1
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n, t, k = 0, 0.0, 0
+    while t < budget_s:
+        m, dt = oracle_window_refine(oracle, Fo, tol, coarse, rng, cores)
+        n, t, k = n + m, t + dt, k + 1
+    return n / t, n, k, cores, t
+
+
 def oracle_sample_rate(gf_cpu, seeds, tol, budget_s=15.0, seed=99):
     """The FP64 oracle, as it stands, on seeded subsamples of `seeds` (S x 3)
     at tolerance `tol`, on all host cores, until about budget_s seconds of
@@ -400,21 +439,21 @@ def run_reference(args, rank, world):
     gf = make_field(FIELD_SEED, "cpu", args.grid)
     g = inputs.to_numpy64(gf)
     F = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
-    seeds = oracle.plane_seeds([0, 0, 0], [2, 0, 0], [0, 2, 0], args.coarse, args.coarse)
     cores = os.cpu_count() or 1
-    o = oracle.default_opts(tol_abs=TUNED_TOL, tol_rel=TUNED_TOL, nthreads=cores)
-    per_step = 256 * cores  # 4 of the oracle's 64-seed work chunks per thread
-    for w in range(args.warmup):
-        oracle.trace_seeds(F, seeds[inputs.subsample(len(seeds), per_step, 1000 + w)], o)
-    t = 0.0
-    for s in range(args.steps):
-        idx = inputs.subsample(len(seeds), per_step, 2000 + s)
-        t0 = time.perf_counter()
-        oracle.trace_seeds(F, seeds[idx], o)
-        t += time.perf_counter() - t0
-    value = per_step * args.steps / t
-    sample = ("%d seeded coarse-map seeds per step of the 1024^2 z=0 map, tol %g (the tolerance the GPU arm's "
-              "autotuner picks on this workload)" % (per_step, TUNED_TOL))
+    per_step = 8  # refinement windows per step
+    rng = np.random.Generator(np.random.PCG64(1000))
+    for _ in range(args.warmup):
+        oracle_window_refine(oracle, F, TUNED_TOL, args.coarse, rng, cores)
+    rng = np.random.Generator(np.random.PCG64(2000))
+    t, n = 0.0, 0
+    for _ in range(args.steps):
+        for _ in range(per_step):
+            m, dt = oracle_window_refine(oracle, F, TUNED_TOL, args.coarse, rng, cores)
+            n, t = n + m, t + dt
+    value = n / t
+    sample = ("the oracle's refinement of %d seeded %dx%d-coarse-cell windows per step of the 1024^2 z=0 map at its "
+              "cell sizes (%d samples in all), tol %g (the tolerance the GPU arm's autotuner picks on this workload)"
+              % (per_step, WINDOW, WINDOW, n, TUNED_TOL))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -1224,13 +1263,12 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         gf_cpu = make_field(field_seed, "cpu", args.grid)
         n_s = int(info.get("samples") or 0)
-        seeds_all = sample_positions(qsl, bufs["key"][:n_s].cpu().numpy().view(np.uint64), args.coarse)
-        rate, nseeds, cores, secs = oracle_sample_rate(gf_cpu, seeds_all, RUN["tol"])
+        rate, nsm, nwin, cores, secs = oracle_refine_rate(gf_cpu, RUN["tol"], args.coarse)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "%d line traces in growing batches, each a seeded subsample of the GPU step's "
-                                          "%d refined-map samples (coarse and refined in proportion), tol %g (the "
-                                          "autotuned GPU tolerance), %.1f s"
-                                          % (nseeds, n_s, RUN["tol"], secs)}
+                                "sample": "the oracle's refinement (coarse pass, FLL-jump passes, tangent-space "
+                                          "values) of %d seeded %dx%d-coarse-cell windows of the map at its cell "
+                                          "sizes, %d samples, tol %g (the autotuned GPU tolerance), %.1f s"
+                                          % (nwin, WINDOW, WINDOW, nsm, RUN["tol"], secs)}
         line["parity"] = parity_sample(qsl, gf, gf_cpu, args.coarse)
         line["parity_refined"] = refined_parity(bufs, n_s, gf_cpu, args.coarse)
     if rank == 0:
