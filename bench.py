@@ -440,7 +440,7 @@ def run_reference(args, rank, world):
     g = inputs.to_numpy64(gf)
     F = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
     cores = os.cpu_count() or 1
-    per_step = 8  # refinement windows per step
+    per_step = 24  # refinement windows per step
     rng = np.random.Generator(np.random.PCG64(1000))
     for _ in range(args.warmup):
         oracle_window_refine(oracle, F, TUNED_TOL, args.coarse, rng, cores)
