@@ -302,29 +302,6 @@ def oracle_refine_rate(gf_cpu, tol, coarse, budget_s=12.0, seed=99):
     return n / t, n, k, cores, t
 
 
-def oracle_sample_rate(gf_cpu, seeds, tol, budget_s=15.0, seed=99):
-    """The FP64 oracle, as it stands, on seeded subsamples of `seeds` (S x 3)
-    at tolerance `tol`, on all host cores, until about budget_s seconds of
-    tracing. Returns (Q-points/s, seeds traced, cores, seconds)."""
-    import oracle
-    from paper_1609_00724_gb300 import inputs
-    g = inputs.to_numpy64(gf_cpu)
-    F = oracle.Field(g.bx, g.by, g.bz, g.xc, g.yc, g.zc, mode=0)
-    cores = os.cpu_count() or 1
-    o = oracle.default_opts(tol_abs=tol, tol_rel=tol, nthreads=cores)
-    done, t_used, m = 0, 0.0, 64 * cores
-    rng_seed = seed
-    while t_used < budget_s and done < len(seeds):
-        idx = inputs.subsample(len(seeds), min(m, len(seeds)), rng_seed)
-        t0 = time.perf_counter()
-        oracle.trace_seeds(F, seeds[idx], o)
-        t_used += time.perf_counter() - t0
-        done += len(idx)
-        rng_seed += 1
-        m = min(4 * m, max(64, int(m * budget_s / max(t_used, 1e-3))))
-    return done / t_used, done, cores, t_used
-
-
 def oracle_rate_on(gf, seeds, tol, mode=0, budget_s=10.0, seed=99, order=1, geometry=0):
     """cpu_baseline of a bench mode: the FP64 oracle on seeded subsamples of
     `seeds` of the field gf (GridField, any device) at tolerance `tol`."""

@@ -388,7 +388,7 @@ int qsl_mask_dilate(const uint8_t* in, int nz, int ny, int nx, uint8_t* out, voi
  *  - the step cap: the requested h_max, or 4 smallest spacings when that also
  *    meets the bounds;
  *  - the fastest launch shape (warps per block 2/4/8, blocks per SM at most
- *    2 or as many as fit, refill threshold 1/8) and step cap at that
+ *    2 or as many as fit, refill threshold 1, 4, 8 or 16) and step cap at that
  *    tolerance, timed with CUDA events on `stream` on the sample repeated
  *    until one launch holds at least 16 x 384 line directions per SM (a
  *    throughput measurement; the sample's own launch is often as long as its

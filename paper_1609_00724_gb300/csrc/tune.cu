@@ -187,7 +187,7 @@ extern "C" int qsl_autotune(const qsl_field* f, const double* seeds, int64_t S, 
   qsl_line* shape_out = reps > 1 ? dt.p : d.p;
   const int wpb[] = {2, 4, 8};
   const int bps[] = {32, 2};
-  const int refill[] = {1, 8};
+  const int refill[] = {1, 4, 8, 16};
   double best = 1e30;
   int bw = 4, bb = 32, br = 1;
   double bh = opts->h_max;
