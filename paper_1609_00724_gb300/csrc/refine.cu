@@ -487,6 +487,75 @@ __global__ void __launch_bounds__(256) convert_tiled_kernel(const uint64_t* __re
   }
 }
 
+// Both grids of a refinement, Q (log10 interpolation) and L (linear), in one
+// pass over the curve keys: convert_tiled_kernel's staging, Hilbert decodes
+// and binary searches shared by the two value arrays, each resolved by the
+// same rule.
+__global__ void __launch_bounds__(256) convert_tiled_qL_kernel(const uint64_t* __restrict__ keys,
+                                                               const float* __restrict__ qv,
+                                                               const float* __restrict__ lv, int64_t n, int nd,
+                                                               int bits, int e0, int e1, int e2, uint64_t nkeys,
+                                                               const int64_t* __restrict__ start, float* qout,
+                                                               float* lout) {
+  __shared__ uint64_t sk[CS];
+  __shared__ float sq[CS];
+  __shared__ float sL[CS];
+  __shared__ double sl[CS];
+  __shared__ double sinv[CS];
+  for (uint64_t c0 = (uint64_t)blockIdx.x * CK; c0 < nkeys; c0 += (uint64_t)gridDim.x * CK) {
+    const uint64_t c1 = c0 + CK < nkeys ? c0 + CK : nkeys;
+    const uint64_t ci = c0 / CK;
+    int64_t a = start[ci], b = start[ci + 1];
+    if (a > 0) a -= 1;  // predecessor of the chunk
+    if (b < n) b += 1;  // successor of the chunk
+    const int cnt = (int)(b - a);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      sk[i] = keys[a + i];
+      sq[i] = qv[a + i];
+      sL[i] = lv[a + i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      sl[i] = log10((double)sq[i]);
+      if (i + 1 < cnt) sinv[i] = 1.0 / (double)(sk[i + 1] - sk[i]);
+    }
+    __syncthreads();
+    for (uint64_t k = c0 + threadIdx.x; k < c1; k += blockDim.x) {
+      uint32_t c[3] = {0, 0, 0};
+      hilbert_coords_dev(k, nd, bits, c);
+      if ((int)c[0] >= e0 || (int)c[1] >= e1 || (nd == 3 && (int)c[2] >= e2)) continue;
+      float rq = __int_as_float(0x7fc00000), rl = rq;
+      if (cnt > 0) {
+        int lo = 0, hi = cnt;  // j: last staged sample with key <= k
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (sk[mid] <= k) lo = mid + 1;
+          else hi = mid;
+        }
+        const int j = lo - 1;
+        if (j >= 0 && sk[j] == k) {
+          rq = sq[j];
+          rl = sL[j];
+        } else if (j + 1 >= cnt) {
+          rq = sq[j];  // after the last sample
+          rl = sL[j];
+        } else if (j < 0) {
+          rq = sq[0];  // before the first sample
+          rl = sL[0];
+        } else {
+          const double t = (double)(k - sk[j]) * sinv[j];
+          rq = pow10_of((1 - t) * sl[j] + t * sl[j + 1]);
+          rl = (float)((1 - t) * (double)sL[j] + t * (double)sL[j + 1]);
+        }
+      }
+      const int64_t o = (int64_t)c[0] + (int64_t)e0 * ((int64_t)c[1] + (int64_t)e1 * (int64_t)c[2]);
+      qout[o] = rq;
+      lout[o] = rl;
+    }
+    __syncthreads();
+  }
+}
+
 int grid_for(int64_t n) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -1022,8 +1091,28 @@ int refine_body(const qsl_field* f, const qsl_refine_spec* sp, const qsl_opts* o
   smp->iters = it;
   smp->traced = (int32_t)(traced & 0x7fffffff);
   int out_order = sp->out_order > 0 ? sp->out_order : p;
-  if (q_grid && (rc = convert_device(user.key, user.q, n, nd, p, ext, out_order, 1, q_grid, s))) return rc;
-  if (l_grid && (rc = convert_device(user.key, user.L, n, nd, p, ext, out_order, 0, l_grid, s))) return rc;
+  if (q_grid && l_grid && out_order == p && n > 0) {
+    // both grids in one pass over the curve keys
+    int eo[3] = {1, 1, 1};
+    for (int a = 0; a < nd; ++a) eo[a] = ext[a];
+    const uint64_t nkeys = 1ull << (nd * p);
+    const uint64_t chunks = (nkeys + CK - 1) / CK;
+    int64_t* start = nullptr;
+    if ((rc = sc.alloc(&start, chunks + 1))) return rc;
+    chunk_bounds_kernel<<<grid_for((int64_t)chunks + 1), 256, 0, s>>>(user.key, n, chunks, start);
+    qsl::count_launch();
+    int dev = 0, sms = 0;
+    QSL_CHECK_CUDA(cudaGetDevice(&dev));
+    QSL_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = chunks < (uint64_t)sms * 8 ? (int)chunks : sms * 8;
+    convert_tiled_qL_kernel<<<blocks, 256, 0, s>>>(user.key, user.q, user.L, n, nd, p, eo[0], eo[1], eo[2], nkeys,
+                                                   start, q_grid, l_grid);
+    qsl::count_launch();
+    QSL_CHECK_CUDA(cudaGetLastError());
+  } else {
+    if (q_grid && (rc = convert_device(user.key, user.q, n, nd, p, ext, out_order, 1, q_grid, s))) return rc;
+    if (l_grid && (rc = convert_device(user.key, user.L, n, nd, p, ext, out_order, 0, l_grid, s))) return rc;
+  }
   if (cap_hit) {
     set_error("sample capacity %lld reached", (long long)cap);
     return QSL_ECAPACITY;

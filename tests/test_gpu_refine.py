@@ -323,6 +323,14 @@ def test_refine_sample_set_matches_oracle(qsl, oracle_mod, ndim, integrator, ste
     if ndim == 3:
         flat += ext[0] * ext[1] * c[:, 2].astype(np.int64)
     assert np.array_equal(lg.cpu().numpy()[flat], b["L"].cpu().numpy()[:n])
+    # both grids (converted in one pass) equal qsl_convert of each sample array
+    for vals, grid, log_interp in ((b["q"], qg, 1), (b["L"], lg, 0)):
+        want = torch.full_like(grid, float("nan"))
+        qsl.qsl_convert(b["key"][:n], vals[:n], ndim, sp.max_order, ext, sp.max_order, log_interp, want)
+        w, gg = want.cpu().numpy(), grid.cpu().numpy()
+        m = int(np.prod(ext))
+        assert np.array_equal(np.isnan(w[:m]), np.isnan(gg[:m])) and np.array_equal(w[:m][~np.isnan(w[:m])],
+                                                                                      gg[:m][~np.isnan(gg[:m])])
 
 
 @pytest.mark.parametrize("stride", [1, 2])
