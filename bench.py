@@ -941,6 +941,15 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
         def go():
             s2.refine(F, learned.volume_spec(coarse, 2, TAU, max_iters=0), o32)
             L, Q, _ = learned.coarse_grids(s2, 3, spec.max_order, 2, coarse[::-1])
+            if stride == "mixed":
+                # the cells the network flags at every effective cell, the
+                # ring the dilation adds at every other one per axis
+                Xf = learned.features_slices(L, Q)
+                core = learned.propose(net, Xf, thr, dilate=False)
+                ring = (learned.propose(net, Xf, thr, dilate=True).bool() & ~core.bool()).to(torch.uint8)
+                s2.refine(F, learned.volume_spec(coarse, 2, TAU, proposal=ring, max_iters=0, proposal_stride=2), o32)
+                r = s2.refine(F, learned.volume_spec(coarse, 2, TAU, proposal=core, max_iters=max_iters), o32)
+                return r, int(core.sum().item()) + int(ring.sum().item())
             budget = max(0, int(0.9 * (cap - s2.count) / (4 // stride) ** 3))
             mask = learned.propose(net, learned.features_slices(L, Q), thr, dilate=True)
             if int(mask.sum().item()) > budget:
@@ -966,7 +975,8 @@ def run_learned(args, qsl, torch, dev, rank, world, local):
                 "converted_qsl_recall": old_recall}
 
     runs = {"learned_fp32_bounded": (fb_iters, 1), "learned_fp32_full": (64, 1),
-            "learned_fp32_stride2_bounded": (fb_iters, 2), "learned_fp32_stride2_full": (64, 2)}
+            "learned_fp32_stride2_bounded": (fb_iters, 2), "learned_fp32_stride2_full": (64, 2),
+            "learned_fp32_mixed_bounded": (fb_iters, "mixed"), "learned_fp32_mixed_full": (64, "mixed")}
     for k, (mi, stv) in runs.items():
         res[k] = learned_run(mi, stv)
     dense = None
