@@ -187,10 +187,14 @@ __device__ __forceinline__ void ho_sum_k(const FieldView<S>& F, const int* ci, c
   }
 #pragma unroll 1
   for (int kz = 0; kz < K; ++kz) {
+    // the z tap of this pass by selects (a rolled loop would index the arrays in local memory)
+    const int izk = kz == 0 ? iz[0] : (kz == 1 ? iz[1] : (kz == 2 ? iz[2] : iz[3]));
+    const R wzk = kz == 0 ? wz[0] : (kz == 1 ? wz[1] : (kz == 2 ? wz[2] : wz[3]));
+    const R gzk = kz == 0 ? gz[0] : (kz == 1 ? gz[1] : (kz == 2 ? gz[2] : gz[3]));
 #pragma unroll
     for (int ky = 0; ky < K; ++ky) {
-      const size_t row = (size_t)iz[kz] * sz + (size_t)iy[ky] * sy;
-      const R wyz = wy[ky] * wz[kz], gyz = gy[ky] * wz[kz], wgz = wy[ky] * gz[kz];
+      const size_t row = (size_t)izk * sz + (size_t)iy[ky] * sy;
+      const R wyz = wy[ky] * wzk, gyz = gy[ky] * wzk, wgz = wy[ky] * gzk;
 #pragma unroll
       for (int kx = 0; kx < K; ++kx) {
         const V q = ldg4(F.v + row + ix[kx]);
